@@ -1,0 +1,391 @@
+"""Benchmark of the wall-RPY rigid-multiblob hot path on GB300.
+
+Workload: 4,369 L-shaped boomerangs x 15 blobs = 65,535 blobs above a no-slip
+wall (box scaled to the 128-boomerang / 40 x 40 um density), synthetic and
+seeded.  One bench step is one pass of the whole hot path over it:
+  * one Trapezoidal-Slip time step (Algorithm 2): blob geometry, body-block
+    preconditioner, GMRES RFD solve, RFD drift D^F / D^S, preconditioned
+    Lanczos M^{1/2} W, predictor and corrector GMRES solves -- FP32 pair
+    arithmetic, FP64 Krylov vectors;
+  * one batched FP32 wall-RPY matvec with k = 16 right-hand sides.
+value = pair interactions per second over the timed steps (n^2 per pair-kernel
+launch, summed over every launch inside the step), whole job over all ranks.
+
+--impl reference times the CPU oracle (the plain FP64 program the tests check
+against) on the host cores on a bounded sample of the same workload.
+"""
+import argparse
+import ctypes as C
+import json
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "wall-RPY matvec pairs/s + steps/s, FP32 multi-RHS vs FP64 plain, rel err <=1e-5"
+UNIT = "pairs/s"
+NB, NPER = 4369, 15
+N = NB * NPER
+K_RHS = 16
+F_GEOM = 116                 # algorithmic flops of one pair block (FMA = 2), see the design doc
+FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+
+
+def f_pair(k):
+    return F_GEOM + 18 * k
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-oracle", action="store_true", help="skip the oracle accuracy / CPU legs")
+    return ap.parse_args()
+
+
+def workload(seed=1):
+    from paper_1709_02410_gb300 import synth
+    return synth.boomerang_suspension(NB, 40.0 * np.sqrt(NB / 128), seed)
+
+
+# ---------------------------------------------------------------------------
+# clocks during the timed region
+
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        rows = []
+        for line in open(self.f.name):
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                rows.append(parts)
+        os.unlink(self.f.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------
+# our arm
+
+def run_ours(args, rank, world, local):
+    import torch
+    import paper_1709_02410_gb300 as P
+    from paper_1709_02410_gb300 import _native, synth
+    from paper_1709_02410_gb300._native import Forces, StepParams
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    s = workload(seed=1 + rank)
+    T = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
+    h = P.Handle(synth.ETA, s.a, synth.KT)
+    lib = h.lib
+    shape, q0, th0 = T(s.shape), T(s.q), T(s.theta)
+    q, th = q0.clone(), th0.clone()
+    F16 = T(synth.gaussian(100 + rank, (K_RHS, 3, N), np.float32), torch.float32)
+    U16 = torch.empty_like(F16)
+    # gravity m_e g per blob (Sec. 4.1: m_e = 1.57e-11 mg, g = 9.81e6 um/s^2), blob-wall Yukawa
+    forces = Forces(1.57e-11 * 9.81e6, 0.096, 0.162, 0.1, (0.0, 0.0, 0.0))
+    Lp = 14 * 1.05 * s.a          # arm length: 7 spacings of 2.1 a
+
+    def sp(i):
+        return StepParams(0.01, 1e-3, Lp, 1e-6, 1e-4, 200, 50, 80, P.F32, 2024 + rank, i)
+
+    stats_log = []
+
+    def step(i):
+        r = h.blobs_from_bodies(shape, q, th)
+        st, status = h.step_ts(shape, q, th, forces, sp(i))
+        stats_log.append(st)
+        h.mobility_apply(r, F16, out=U16)
+
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+
+    def barrier():
+        if world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for i in range(args.warmup):
+        step(i)
+    barrier()
+    lib.rpbd_profile_read(h.h, 1, 1, C.byref(C.c_double()), C.byref(C.c_longlong()), C.byref(C.c_double()), 1)
+    lib.rpbd_profile_enable(h.h, 1)
+    stats_log.clear()
+    clocks = Clocks(local)
+    clocks.start()
+    launches0 = lib.rpbd_launch_count()
+    barrier()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        ev[i][0].record()
+        step(args.warmup + i)
+        ev[i][1].record()
+    barrier()
+    wall = time.perf_counter() - wall0
+    launches = lib.rpbd_launch_count() - launches0
+    clk = clocks.stop()
+    lib.rpbd_profile_enable(h.h, 0)
+    ms_steps = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(ms_steps) / 1e3
+    # per-variant pair-kernel time from the library's own events
+    prof = {}
+    for dt, name in ((1, "f32"), (0, "f64")):
+        for k in (1, 2, 4, 8, 16):
+            ms, nl, pr = C.c_double(), C.c_longlong(), C.c_double()
+            lib.rpbd_profile_read(h.h, dt, k, C.byref(ms), C.byref(nl), C.byref(pr), 0)
+            if nl.value:
+                prof[f"{name}_k{k}"] = dict(ms=ms.value, launches=nl.value, pairs=pr.value)
+    pairs_local = sum(v["pairs"] for v in prof.values())
+
+    # whole job: max time over ranks, pairs summed over ranks
+    t_max, pairs_total = t_local, pairs_local
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        pp = torch.tensor([pairs_local], device=dev, dtype=torch.float64)
+        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
+        t_max, pairs_total = float(tt.item()), float(pp.item())
+    value = pairs_total / t_max
+
+    # ---- end-to-end through the public API with host buffers (same steps)
+    qh = torch.empty_like(q0, device="cpu").pin_memory()
+    thh = torch.empty_like(th0, device="cpu").pin_memory()
+    Fh = F16.cpu().pin_memory()
+    Uh = torch.empty_like(Fh).pin_memory()
+    qh.copy_(q0.cpu())
+    thh.copy_(th0.cpu())
+    lib.rpbd_profile_read(h.h, 1, 1, C.byref(C.c_double()), C.byref(C.c_longlong()), C.byref(C.c_double()), 1)
+    lib.rpbd_profile_enable(h.h, 1)
+    barrier()
+    e0 = time.perf_counter()
+    for i in range(args.steps):
+        q.copy_(qh, non_blocking=True)
+        th.copy_(thh, non_blocking=True)
+        F16.copy_(Fh, non_blocking=True)
+        step(1000 + i)
+        qh.copy_(q, non_blocking=True)
+        thh.copy_(th, non_blocking=True)
+        Uh.copy_(U16, non_blocking=True)
+        torch.cuda.synchronize()
+    barrier()
+    e2e_t = time.perf_counter() - e0
+    lib.rpbd_profile_enable(h.h, 0)
+    e2e_pairs = 0.0
+    for dt in (1, 0):
+        for k in (1, 2, 4, 8, 16):
+            ms, nl, pr = C.c_double(), C.c_longlong(), C.c_double()
+            lib.rpbd_profile_read(h.h, dt, k, C.byref(ms), C.byref(nl), C.byref(pr), 0)
+            e2e_pairs += pr.value
+    lib.rpbd_profile_read(h.h, 1, 1, C.byref(C.c_double()), C.byref(C.c_longlong()), C.byref(C.c_double()), 1)
+    h2d = q0.numel() * 8 + th0.numel() * 8 + F16.numel() * 4
+    d2h = h2d
+    if world > 1:
+        import torch.distributed as dist
+        tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        pp = torch.tensor([e2e_pairs], device=dev, dtype=torch.float64)
+        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
+        e2e_t, e2e_pairs = float(tt.item()), float(pp.item())
+
+    # ---- separate measurements (outside the timed steps): k = 16 FP32 batch and
+    # the plain FP64 single-RHS kernel, each alone, and their accuracy
+    r = h.blobs_from_bodies(shape, q0, th0)
+    extra = {}
+
+    def time_launch(fn, reps):
+        fn()
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        tot = 0.0
+        for _ in range(reps):
+            flush.zero_()
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize()
+            tot += a.elapsed_time(b)
+        return tot / reps / 1e3
+
+    t16 = time_launch(lambda: h.mobility_apply(r, F16, out=U16), 3)
+    F1 = T(synth.gaussian(200, (3, N)))
+    U1 = torch.empty_like(F1)
+    t64 = time_launch(lambda: h.mobility_apply(r, F1, out=U1), 1)
+    F1f = F1.float()
+    U1f = torch.empty_like(F1f)
+    t32k1 = time_launch(lambda: h.mobility_apply(r, F1f, out=U1f), 3)
+    extra["f32_k16"] = dict(s_per_launch=t16, pairs_per_s=N * N / t16, matvecs_per_s=K_RHS / t16,
+                            tflops=N * N * f_pair(16) / t16 / 1e12)
+    extra["f32_k1"] = dict(s_per_launch=t32k1, pairs_per_s=N * N / t32k1, tflops=N * N * f_pair(1) / t32k1 / 1e12)
+    extra["f64_k1"] = dict(s_per_launch=t64, pairs_per_s=N * N / t64)
+    extra["speedup_f32_k16_vs_f64_k1_per_rhs"] = (t64 * K_RHS) / t16
+    extra["speedup_f32_k1_vs_f64_k1"] = t64 / t32k1
+
+    out = None
+    if rank == 0:
+        # dominant pair-kernel variant of the step -> roofline
+        dom = max(prof.items(), key=lambda kv: kv[1]["ms"]) if prof else None
+        roof = None
+        if dom:
+            name, d = dom
+            k = int(name.split("_k")[1])
+            avg = d["ms"] / d["launches"] / 1e3
+            flops = d["pairs"] / d["launches"] * f_pair(k)
+            ach = flops / avg / 1e12
+            roof = {"bound": "alu", "kernel": f"pair_kernel<{name}>", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                    "flops_per_pair": f_pair(k), "avg_launch_ms": avg * 1e3,
+                    "share_of_step": d["ms"] / (t_local * 1e3)}
+        # accuracy vs the FP64 oracle on sampled rows (outside the timed region)
+        acc = {}
+        if not args.no_oracle:
+            from oracle import mobility as om
+            from oracle import rigid
+            ro = rigid.blob_positions(s.q, s.theta, s.shape)
+            prm = om.Params(synth.ETA, s.a)
+            rows = np.random.default_rng(5).choice(N, 32, replace=False)
+            Fo = F16.cpu().numpy().astype(np.float64)
+            Uo = om.apply(ro, Fo, prm, rows=rows)
+            Ug = U16.cpu().numpy()[:, :, rows].astype(np.float64)
+            acc["f32_k16_rel_err_vs_oracle"] = float(np.linalg.norm(Ug - Uo) / np.linalg.norm(Uo))
+            U1o = om.apply(ro, F1.cpu().numpy(), prm, rows=rows)
+            acc["f64_k1_rel_err_vs_oracle"] = float(np.linalg.norm(U1.cpu().numpy()[:, rows] - U1o)
+                                                    / np.linalg.norm(U1o))
+            acc["rows_sampled"] = len(rows)
+            # CPU baseline: the oracle as it stands, bounded sample (rows x all sources, k = 16)
+            nrows = 512
+            rows_b = np.arange(nrows)
+            t0 = time.perf_counter()
+            om.apply(ro, Fo, prm, rows=rows_b)
+            tc = time.perf_counter() - t0
+            cpu = {"value": nrows * N / tc, "unit": UNIT, "cores": om.num_threads(), "kind": "oracle",
+                   "sample": f"{nrows} target rows x {N} sources, k = 16, FP64 ({tc:.1f} s)"}
+        else:
+            cpu = None
+        iters = [[x["iterations"] for x in st] for st in stats_log]
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic (seeded boomerang suspension, forces N(0,1))",
+            "config": {"workload": "boomerangs_65535: 4369 L-bodies x 15 blobs, T-S step + k=16 FP32 batch",
+                       "n_blobs": N, "n_bodies": NB, "k_rhs": K_RHS, "gmres_tol": 1e-6, "lanczos_tol": 1e-4,
+                       "rfd_delta": 1e-3, "l2": "flushed (256 MB write) before every timed step",
+                       "parallelism": f"replicas x{world}"},
+            "steps_per_s": args.steps / t_max * world,
+            "e2e": {"value": e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches),
+            "roofline": roof,
+            "cpu_baseline": cpu,
+            "clocks": clk,
+            "pair_kernels_in_step": prof,
+            "solver_iterations_per_step": iters,
+            "matvec": extra,
+            "accuracy": acc,
+            "wall_s_timed": wall,
+        }
+    return out
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the CPU oracle, bounded sample of the same workload
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return None
+    from oracle import mobility as om
+    from oracle import rigid
+    from paper_1709_02410_gb300 import synth
+    s = workload(1)
+    ro = rigid.blob_positions(s.q, s.theta, s.shape)
+    prm = om.Params(synth.ETA, s.a)
+    F = synth.gaussian(100, (K_RHS, 3, N), np.float32).astype(np.float64)
+    nrows = 32
+
+    def step(i):
+        rows = np.arange(i * nrows, (i + 1) * nrows) % N
+        om.apply(ro, F, prm, rows=rows)
+
+    for i in range(args.warmup):
+        step(i)
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        step(args.warmup + i)
+    t = time.perf_counter() - t0
+    v = args.steps * nrows * N / t
+    return {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": {"workload": "boomerangs_65535 (oracle: k=16 FP64 matvec rows)", "n_blobs": N},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": om.num_threads(), "kind": "oracle",
+                             "sample": f"{nrows} target rows x {N} sources x k=16 per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        out = run_reference(args, rank, world)
+    else:
+        import __graft_entry__
+        __graft_entry__.build()
+        if world > 1:
+            import torch
+            import torch.distributed as dist
+            torch.cuda.set_device(local)
+            dist.init_process_group("nccl")
+        out = run_ours(args, rank, world, local)
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+    if out is not None and rank == 0:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,229 @@
+/*
+ * rpbd.h -- C ABI of the GB300 library for rigid-multiblob Brownian dynamics
+ * above a no-slip wall (Sprinkle, Balboa Usabiaga, Patankar, Donev, "Large
+ * Scale Brownian Dynamics of Confined Suspensions of Rigid Particles").
+ *
+ * Conventions (all entry points):
+ *  - Every array argument is a DEVICE pointer owned by the caller, unless
+ *    the comment says "host".  The library never frees caller memory.
+ *  - Blob positions are SoA: r[0..n) = x, r[n..2n) = y, r[2n..3n) = z (FP64).
+ *  - Blob vectors (forces, velocities) are [k][3][n]: RHS-major, then
+ *    component, then blob.
+ *  - Bodies: nb bodies of one shape with nper blobs each; blob i of body p is
+ *    index p * nper + i.  Body vectors are [nb][6] rows (u, omega) or
+ *    (f, tau); tracking points q [nb][3]; unit quaternions theta [nb][4] as
+ *    (s, p_x, p_y, p_z).
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *    Kernel-only calls are asynchronous on that stream.  Calls that run a
+ *    Krylov iteration (Lanczos, GMRES, steps) read a residual back to the
+ *    host once per iteration and return only when done.
+ *  - Return value: RPBD_OK (0) or a negative status; rpbd_last_error(h)
+ *    gives a message.  Inputs with NaN/Inf positions give RPBD_BAD_INPUT.
+ *  - The handle owns a device workspace that grows on demand
+ *    (cudaMalloc); rpbd_reserve() sizes it ahead of time.  A handle is used
+ *    by one host thread at a time.
+ *  - Units are the caller's; the paper's workloads use um, s, mg.
+ */
+#ifndef RPBD_H
+#define RPBD_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RPBD_OK 0
+#define RPBD_BAD_ARG (-1)
+#define RPBD_BAD_INPUT (-2)
+#define RPBD_CUDA (-3)
+#define RPBD_NOT_CONVERGED (-4)
+#define RPBD_TIMEOUT (-5)
+#define RPBD_NO_MEM (-6)
+
+/* arithmetic of the pair kernels */
+#define RPBD_F64 0 /* FP64 pair math, FP64 accumulation */
+#define RPBD_F32 1 /* FP32 pair math, FP32 tile partials summed in FP64 */
+
+typedef struct rpbd_handle rpbd_handle;
+
+/* Physical parameters (Sec. 2.1, Sec. 4). */
+typedef struct rpbd_params {
+    double eta;   /* fluid viscosity */
+    double a;     /* blob hydrodynamic radius */
+    double kT;    /* thermal energy k_B T */
+    int wall;     /* 1: no-slip wall at z = 0 (Rotne-Prager-Blake); 0: unbounded RPY */
+    double s_min; /* floor of the wall-overlap scale s_i = clamp(z_i/a, s_min, 1) */
+} rpbd_params;
+
+/* Per-call solver statistics (host struct, filled before return). */
+typedef struct rpbd_stats {
+    int iterations;  /* Krylov iterations */
+    int matvecs;     /* applications of M */
+    double residual; /* GMRES: relative residual; Lanczos: last relative change */
+    int status;      /* RPBD_OK or RPBD_NOT_CONVERGED */
+} rpbd_stats;
+
+/* Deterministic forces for the time steps (Sec. 4): per-blob gravity -weight z^,
+ * blob-wall Yukawa repulsion gamma exp(-h/b)/h evaluated at h = max(z, h_floor),
+ * and a constant torque on every body. */
+typedef struct rpbd_forces {
+    double weight;
+    double wall_gamma;
+    double wall_b;
+    double h_floor;
+    double torque[3];
+} rpbd_forces;
+
+/* Time-step controls (Algorithms 1 and 2). */
+typedef struct rpbd_step_params {
+    double dt;          /* time step */
+    double delta;       /* RFD displacement parameter */
+    double Lp;          /* body length scale L_p of the RFD (same for all bodies) */
+    double tol_gmres;   /* relative residual of every saddle solve */
+    double tol_lanczos; /* relative change stop test of Lanczos */
+    int max_iter_gmres;
+    int restart;        /* GMRES(m) restart length */
+    int max_iter_lanczos;
+    int dtype;          /* RPBD_F32 or RPBD_F64 pair arithmetic */
+    uint64_t seed;      /* Philox key */
+    uint32_t step;      /* step counter (Philox counter word 1) */
+} rpbd_step_params;
+
+/* ---- handle ------------------------------------------------------------ */
+
+/* Create a handle bound to the current CUDA device.  *h receives it. */
+int rpbd_create(rpbd_handle** h, const rpbd_params* p);
+int rpbd_destroy(rpbd_handle* h);
+/* Pre-size the workspace for n blobs, nb bodies of nper blobs, k right-hand
+ * sides and a Krylov basis of `basis` vectors (0 for none). */
+int rpbd_reserve(rpbd_handle* h, int64_t n, int64_t nb, int nper, int k, int basis);
+const char* rpbd_last_error(const rpbd_handle* h);
+const char* rpbd_status_string(int status);
+
+/* ---- a1: blob geometry (Sec. 2.1 multiblob model, App. B.1) ------------ */
+
+/* r_i = q_p + R(theta_p) shape_i for every blob; shape [nper][3] (device). */
+int rpbd_blobs_from_bodies(rpbd_handle* h, int64_t nb, int nper, const double* shape,
+                           const double* q, const double* theta, double* r, void* stream);
+
+/* ---- a2: wall-RPY matvec (Sec. 2.1; the dense GPU sum of Sec. 2.1/4.2) -- */
+
+/* U = M(r) F for k right-hand sides (1 <= k <= 16; k in {1,2,4,8,16} hit
+ * specialised kernels, other k run as the next larger one).  F and U are
+ * [k][3][n] of type double (dtype RPBD_F64) or float (RPBD_F32).
+ * M_ij = s_i s_j [M_RPY(r~_i - r~_j) + M_wall(r~_i, r~_j)], r~ = (x, y, max(z, a)). */
+int rpbd_mobility_apply(rpbd_handle* h, int64_t n, const double* r, const void* F, void* U,
+                        int k, int dtype, void* stream);
+
+/* Same, FP64 blob vectors in and out with the pair arithmetic chosen by
+ * dtype (the mixed mode the Krylov solvers use). */
+int rpbd_mobility_apply_mixed(rpbd_handle* h, int64_t n, const double* r, const double* F,
+                              double* U, int k, int dtype, void* stream);
+
+/* ---- a7: adjoint and divergence ---------------------------------------- */
+
+/* grad[3][n] = d(u^T M(r) F)/dr, FP64; u, F [3][n].  The derivative of the
+ * matvec of Sec. 2.1 with respect to the blob positions. */
+int rpbd_mobility_adjoint(rpbd_handle* h, int64_t n, const double* r, const double* u,
+                          const double* F, double* grad, void* stream);
+
+/* div[3][n] = sum_j d_{r_j} . M_ij (the quantity the RFD of Sec. 3 estimates
+ * with B = M), FP64. */
+int rpbd_mobility_divergence(rpbd_handle* h, int64_t n, const double* r, double* div,
+                             void* stream);
+
+/* ---- rigid operators (eq. K and force/torque balance, Sec. 2.1) -------- */
+
+/* out[3][n] = K U: u_p + omega_p x (r_i - q_p). */
+int rpbd_K_apply(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q,
+                 const double* U, double* out, void* stream);
+/* out[nb][6] = K^T lam: (sum_i lam_i, sum_i (r_i - q_p) x lam_i). */
+int rpbd_KT_apply(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q,
+                  const double* lam, double* out, void* stream);
+
+/* ---- a3: body-block-diagonal preconditioner (Sec. 2.2) ----------------- */
+
+/* Build, for every body p, the dense M(pp) of its blobs alone (wall
+ * included), its Cholesky factor L_p, L_p^-1, M(pp)^-1 and
+ * N_p = (K_p^T M(pp)^-1 K_p)^-1 in FP64.  Kept in the handle until the next
+ * build. */
+int rpbd_precond_build(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q,
+                       void* stream);
+/* Apply a stored factor to a blob vector [3][n]: mode 0: out = L x;
+ * 1: out = L^-1 x; 2: out = L^-T x; 3: out = M~^-1 x. */
+int rpbd_precond_apply(rpbd_handle* h, int mode, const double* x, double* out, void* stream);
+
+/* ---- a4: preconditioned Lanczos M^{1/2} W (Sec. 2.2) ------------------- */
+
+/* out[3][n] ~ L f(L^-1 M L^-T) W with f = sqrt, by Lanczos with full
+ * reorthogonalisation from v_1 = W/|W|; stops when |y_m - y_{m-1}|/|y_m| < tol.
+ * use_precond = 0 runs on M itself (L = I).  W, out: [3][n] FP64. */
+int rpbd_lanczos_sqrt_apply(rpbd_handle* h, int64_t n, const double* r, const double* W,
+                            double* out, double tol, int max_iter, int dtype, int use_precond,
+                            rpbd_stats* stats, void* stream);
+
+/* ---- a5: GMRES saddle-point mobility solve (eq. saddle, Sec. 2.1) ------ */
+
+/* Solve [M -K; -K^T 0][lambda; U] = [-slip; -FT] by right-preconditioned
+ * restarted GMRES with the body-block preconditioner built on the same r, q
+ * (built here when build_precond != 0).  slip [3][n] or NULL (zero); FT
+ * [nb][6] or NULL (zero); lambda [3][n] and U [nb][6] outputs.  Stops on
+ * the relative residual |b - A x|/|b| <= tol. */
+int rpbd_gmres_rigid_solve(rpbd_handle* h, int64_t nb, int nper, const double* r,
+                           const double* q, const double* slip, const double* FT,
+                           double* lambda, double* U, double tol, int max_iter, int restart,
+                           int dtype, int build_precond, rpbd_stats* stats, void* stream);
+
+/* ---- a6: random finite difference drift (Sec. 3, eq. RFDcenter) -------- */
+
+/* drift[3][n] = (1/delta) [M(r + delta/2 W) - M(r - delta/2 W)] W; its mean
+ * over W ~ N(0, I) is div M + O(delta^2). */
+int rpbd_rfd_drift(rpbd_handle* h, int64_t n, const double* r, const double* W, double delta,
+                   double* drift, int dtype, void* stream);
+
+/* ---- random numbers ---------------------------------------------------- */
+
+/* out[e] for e < n: standard normals from Philox4x32-10 (Salmon et al.,
+ * SC'11) keyed by seed, counter (e/4, step, sid, 0), Box-Muller on word pairs. */
+int rpbd_philox_normals(rpbd_handle* h, uint64_t seed, uint32_t step, uint32_t sid, int64_t n,
+                        double* out, void* stream);
+
+/* ---- a8: time steps ----------------------------------------------------- */
+
+/* One Trapezoidal-Slip step (Algorithm 2) or Euler-Maruyama-Traction step
+ * (Algorithm 1) of nb bodies: q [nb][3] and theta [nb][4] are updated in
+ * place; shape [nper][3].  Random vectors are drawn with
+ * rpbd_philox_normals(seed, step, sid): T-S uses sid 0 for W^s [3][n] and
+ * sid 1 for W [3][n]; EM-T uses sid 2 for (W^f, W^tau) as [nb][6] rows and
+ * sid 1 for W.  stats (host) receives, in order: T-S: RFD solve, Lanczos,
+ * predictor solve, corrector solve; EM-T: RFD solve, Lanczos, solve. */
+int rpbd_step_ts(rpbd_handle* h, int64_t nb, int nper, const double* shape, double* q,
+                 double* theta, const rpbd_forces* forces, const rpbd_step_params* sp,
+                 rpbd_stats* stats /* host, 4 entries */, void* stream);
+int rpbd_step_emt(rpbd_handle* h, int64_t nb, int nper, const double* shape, double* q,
+                  double* theta, const rpbd_forces* forces, const rpbd_step_params* sp,
+                  rpbd_stats* stats /* host, 3 entries */, void* stream);
+
+/* Blob forces [3][n] of the force model (gravity + wall repulsion) at r. */
+int rpbd_blob_forces(rpbd_handle* h, int64_t n, const double* r, const rpbd_forces* forces,
+                     double* f, void* stream);
+
+/* ---- instrumentation ----------------------------------------------------- */
+
+/* Number of kernels this library has launched since it was loaded. */
+long long rpbd_launch_count(void);
+/* on != 0: bracket every pair-kernel launch of h with CUDA events on its
+ * stream (used to time the kernel inside a larger step). */
+int rpbd_profile_enable(rpbd_handle* h, int on);
+/* Sum of the recorded pair-kernel durations for (dtype, k-variant), their
+ * launch count and pairs (n^2 per launch); synchronises the device.  reset
+ * != 0 drops every record afterwards. */
+int rpbd_profile_read(rpbd_handle* h, int dtype, int k, double* ms, long long* launches, double* pairs,
+                      int reset);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RPBD_H */

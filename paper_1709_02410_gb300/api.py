@@ -1,0 +1,199 @@
+"""Torch-facing binding of the C ABI (argument marshalling only).
+
+Tensors must be contiguous CUDA tensors on the handle's device; positions
+are [3, n] float64 (SoA), blob vectors [k, 3, n] or [3, n], body vectors
+[nb, 6], q [nb, 3], theta [nb, 4].  Calls run on torch's current stream.
+"""
+import ctypes as C
+
+import torch
+
+from . import _native
+from ._native import F32, F64, Forces, Params, Stats, StepParams
+
+
+class RpbdError(RuntimeError):
+    pass
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise RpbdError("expected a CUDA tensor")
+    if not t.is_contiguous():
+        raise RpbdError("expected a contiguous tensor")
+    return C.c_void_p(t.data_ptr())
+
+
+def _stream():
+    return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+
+def _need(t, dtype, shape=None, name="tensor"):
+    if t.dtype != dtype:
+        raise RpbdError(f"{name}: expected {dtype}, got {t.dtype}")
+    if shape is not None and tuple(t.shape) != tuple(shape):
+        raise RpbdError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+
+
+class Handle:
+    """Owns an rpbd_handle (device workspace + physical parameters)."""
+
+    def __init__(self, eta, a, kT=0.0, wall=True, s_min=1e-3):
+        self.lib = _native.load()
+        self.params = Params(eta, a, kT, int(bool(wall)), s_min)
+        h = C.c_void_p()
+        st = self.lib.rpbd_create(C.byref(h), C.byref(self.params))
+        if st != 0:
+            raise RpbdError(f"rpbd_create failed: {_native.STATUS.get(st, st)}")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rpbd_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, what):
+        if st != 0:
+            msg = self.lib.rpbd_last_error(self.h).decode(errors="replace")
+            raise RpbdError(f"{what}: {_native.STATUS.get(st, st)}: {msg}")
+        return st
+
+    # ---- a1
+    def blobs_from_bodies(self, shape, q, theta, out=None):
+        nb, nper = q.shape[0], shape.shape[0]
+        out = torch.empty((3, nb * nper), dtype=torch.float64, device=q.device) if out is None else out
+        for t, n in ((shape, "shape"), (q, "q"), (theta, "theta")):
+            _need(t, torch.float64, name=n)
+        self._check(self.lib.rpbd_blobs_from_bodies(self.h, nb, nper, _ptr(shape), _ptr(q), _ptr(theta),
+                                                    _ptr(out), _stream()), "blobs_from_bodies")
+        return out
+
+    # ---- a2
+    def mobility_apply(self, r, F, dtype=None, out=None):
+        """U = M(r) F.  F [k,3,n] or [3,n]; float64 -> FP64 kernel, float32 ->
+        FP32 kernel.  dtype=F32 with float64 F runs FP32 pairs on FP64 vectors."""
+        n = r.shape[1]
+        _need(r, torch.float64, (3, n), "r")
+        squeeze = F.dim() == 2
+        k = 1 if squeeze else F.shape[0]
+        out = torch.empty_like(F) if out is None else out
+        if dtype is None:
+            dt = F64 if F.dtype == torch.float64 else F32
+            fn = self.lib.rpbd_mobility_apply
+        else:
+            dt = dtype
+            if F.dtype != torch.float64:
+                raise RpbdError("mixed mode needs float64 vectors")
+            fn = self.lib.rpbd_mobility_apply_mixed
+        self._check(fn(self.h, n, _ptr(r), _ptr(F), _ptr(out), k, dt, _stream()), "mobility_apply")
+        return out
+
+    # ---- a7
+    def mobility_adjoint(self, r, u, F, out=None):
+        n = r.shape[1]
+        out = torch.empty((3, n), dtype=torch.float64, device=r.device) if out is None else out
+        self._check(self.lib.rpbd_mobility_adjoint(self.h, n, _ptr(r), _ptr(u), _ptr(F), _ptr(out), _stream()),
+                    "mobility_adjoint")
+        return out
+
+    def mobility_divergence(self, r, out=None):
+        n = r.shape[1]
+        out = torch.empty((3, n), dtype=torch.float64, device=r.device) if out is None else out
+        self._check(self.lib.rpbd_mobility_divergence(self.h, n, _ptr(r), _ptr(out), _stream()),
+                    "mobility_divergence")
+        return out
+
+    # ---- rigid
+    def K_apply(self, nper, r, q, U, out=None):
+        nb = q.shape[0]
+        out = torch.empty((3, nb * nper), dtype=torch.float64, device=r.device) if out is None else out
+        self._check(self.lib.rpbd_K_apply(self.h, nb, nper, _ptr(r), _ptr(q), _ptr(U), _ptr(out), _stream()),
+                    "K_apply")
+        return out
+
+    def KT_apply(self, nper, r, q, lam, out=None):
+        nb = q.shape[0]
+        out = torch.empty((nb, 6), dtype=torch.float64, device=r.device) if out is None else out
+        self._check(self.lib.rpbd_KT_apply(self.h, nb, nper, _ptr(r), _ptr(q), _ptr(lam), _ptr(out), _stream()),
+                    "KT_apply")
+        return out
+
+    # ---- a3
+    def precond_build(self, nper, r, q):
+        self._check(self.lib.rpbd_precond_build(self.h, q.shape[0], nper, _ptr(r), _ptr(q), _stream()),
+                    "precond_build")
+
+    def precond_apply(self, mode, x, out=None):
+        out = torch.empty_like(x) if out is None else out
+        self._check(self.lib.rpbd_precond_apply(self.h, mode, _ptr(x), _ptr(out), _stream()), "precond_apply")
+        return out
+
+    # ---- a4
+    def lanczos_sqrt_apply(self, r, W, tol, max_iter=100, dtype=F64, use_precond=True, out=None):
+        n = r.shape[1]
+        out = torch.empty_like(W) if out is None else out
+        st = Stats()
+        s = self.lib.rpbd_lanczos_sqrt_apply(self.h, n, _ptr(r), _ptr(W), _ptr(out), tol, max_iter, dtype,
+                                             int(bool(use_precond)), C.byref(st), _stream())
+        if s not in (0, -4):
+            self._check(s, "lanczos_sqrt_apply")
+        return out, st.as_dict()
+
+    # ---- a5
+    def gmres_rigid_solve(self, nper, r, q, slip=None, FT=None, tol=1e-6, max_iter=200, restart=50, dtype=F64,
+                          build_precond=True):
+        nb = q.shape[0]
+        n = nb * nper
+        lam = torch.empty((3, n), dtype=torch.float64, device=r.device)
+        U = torch.empty((nb, 6), dtype=torch.float64, device=r.device)
+        st = Stats()
+        s = self.lib.rpbd_gmres_rigid_solve(self.h, nb, nper, _ptr(r), _ptr(q), _ptr(slip), _ptr(FT), _ptr(lam),
+                                            _ptr(U), tol, max_iter, restart, dtype, int(bool(build_precond)),
+                                            C.byref(st), _stream())
+        if s not in (0, -4):
+            self._check(s, "gmres_rigid_solve")
+        return lam, U, st.as_dict()
+
+    # ---- a6
+    def rfd_drift(self, r, W, delta, dtype=F64, out=None):
+        n = r.shape[1]
+        out = torch.empty_like(W) if out is None else out
+        self._check(self.lib.rpbd_rfd_drift(self.h, n, _ptr(r), _ptr(W), delta, _ptr(out), dtype, _stream()),
+                    "rfd_drift")
+        return out
+
+    # ---- random numbers
+    def philox_normals(self, n, seed, step, sid, device="cuda"):
+        out = torch.empty(n, dtype=torch.float64, device=device)
+        self._check(self.lib.rpbd_philox_normals(self.h, seed, step, sid, n, _ptr(out), _stream()),
+                    "philox_normals")
+        return out
+
+    # ---- a8
+    def _step(self, fn, nstats, shape, q, theta, forces: Forces, sp: StepParams):
+        st = (Stats * nstats)()
+        s = fn(self.h, q.shape[0], shape.shape[0], _ptr(shape), _ptr(q), _ptr(theta), C.byref(forces),
+               C.byref(sp), st, _stream())
+        if s not in (0, -4):
+            self._check(s, "step")
+        return [x.as_dict() for x in st], s
+
+    def step_ts(self, shape, q, theta, forces, sp):
+        return self._step(self.lib.rpbd_step_ts, 4, shape, q, theta, forces, sp)
+
+    def step_emt(self, shape, q, theta, forces, sp):
+        return self._step(self.lib.rpbd_step_emt, 3, shape, q, theta, forces, sp)
+
+    def blob_forces(self, r, forces: Forces, out=None):
+        out = torch.empty_like(r) if out is None else out
+        self._check(self.lib.rpbd_blob_forces(self.h, r.shape[1], _ptr(r), C.byref(forces), _ptr(out), _stream()),
+                    "blob_forces")
+        return out

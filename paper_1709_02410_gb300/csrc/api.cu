@@ -1,0 +1,256 @@
+// C ABI entry points: argument checks, workspace, dispatch.
+#include <cuda_runtime.h>
+
+#include <cstdio>
+#include <cstring>
+#include <atomic>
+#include <new>
+
+#include "rpbd_internal.cuh"
+
+namespace rpbd {
+
+static std::atomic<long long> g_launches{0};
+
+void count_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+static cudaEvent_t pool_event(rpbd_handle* h)
+{
+    if (!h->ev_pool.empty()) {
+        cudaEvent_t e = h->ev_pool.back();
+        h->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+void prof_begin(rpbd_handle* h, cudaStream_t st)
+{
+    ProfRec r{pool_event(h), pool_event(h), 0, 0, 0.0};
+    cudaEventRecord(r.a, st);
+    h->prof.push_back(r);
+}
+
+void prof_end(rpbd_handle* h, cudaStream_t st, int dtype, int k, double pairs)
+{
+    ProfRec& r = h->prof.back();
+    cudaEventRecord(r.b, st);
+    r.dtype = dtype;
+    r.k = k;
+    r.pairs = pairs;
+}
+
+int set_error(rpbd_handle* h, int code, const std::string& msg)
+{
+    if (h) h->err = msg;
+    return code;
+}
+
+int ensure(rpbd_handle* h, Buf b, size_t bytes, void** out)
+{
+    if (bytes == 0) bytes = 16;
+    if (h->cap[b] < bytes) {
+        if (h->buf[b]) {
+            cudaError_t e = cudaFree(h->buf[b]);
+            h->buf[b] = nullptr;
+            h->cap[b] = 0;
+            if (e != cudaSuccess) return set_error(h, RPBD_CUDA, std::string("cudaFree: ") + cudaGetErrorString(e));
+        }
+        size_t want = bytes + bytes / 8;  // headroom for slowly growing sizes
+        cudaError_t e = cudaMalloc(&h->buf[b], want);
+        if (e != cudaSuccess) {
+            h->buf[b] = nullptr;
+            return set_error(h, RPBD_NO_MEM, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+        }
+        h->cap[b] = want;
+    }
+    *out = h->buf[b];
+    return RPBD_OK;
+}
+
+}  // namespace rpbd
+
+using namespace rpbd;
+
+static cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+extern "C" {
+
+const char* rpbd_status_string(int status)
+{
+    switch (status) {
+    case RPBD_OK: return "ok";
+    case RPBD_BAD_ARG: return "bad argument";
+    case RPBD_BAD_INPUT: return "bad input (non-finite values)";
+    case RPBD_CUDA: return "CUDA error";
+    case RPBD_NOT_CONVERGED: return "iteration did not converge";
+    case RPBD_TIMEOUT: return "device wait timed out";
+    case RPBD_NO_MEM: return "out of device memory";
+    default: return "unknown status";
+    }
+}
+
+const char* rpbd_last_error(const rpbd_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+int rpbd_create(rpbd_handle** out, const rpbd_params* p)
+{
+    if (!out || !p) return RPBD_BAD_ARG;
+    *out = nullptr;
+    if (!(p->eta > 0) || !(p->a > 0) || !(p->kT >= 0) || !(p->s_min > 0) || p->s_min > 1) return RPBD_BAD_ARG;
+    rpbd_handle* h = new (std::nothrow) rpbd_handle();
+    if (!h) return RPBD_NO_MEM;
+    h->p = *p;
+    if (cudaGetDevice(&h->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&h->sm_count, cudaDevAttrMultiProcessorCount, h->device) != cudaSuccess) {
+        delete h;
+        return RPBD_CUDA;
+    }
+    if (cudaMalloc(&h->dev_flag, sizeof(int)) != cudaSuccess || cudaMemset(h->dev_flag, 0, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&h->host_small, 4096 * sizeof(double)) != cudaSuccess) {
+        if (h->dev_flag) cudaFree(h->dev_flag);
+        delete h;
+        return RPBD_CUDA;
+    }
+    *out = h;
+    return RPBD_OK;
+}
+
+int rpbd_destroy(rpbd_handle* h)
+{
+    if (!h) return RPBD_OK;
+    for (auto& r : h->prof) {
+        cudaEventDestroy(r.a);
+        cudaEventDestroy(r.b);
+    }
+    for (auto e : h->ev_pool) cudaEventDestroy(e);
+    for (int b = 0; b < BUF_COUNT; ++b)
+        if (h->buf[b]) cudaFree(h->buf[b]);
+    if (h->dev_flag) cudaFree(h->dev_flag);
+    if (h->host_small) cudaFreeHost(h->host_small);
+    delete h;
+    return RPBD_OK;
+}
+
+int rpbd_reserve(rpbd_handle* h, int64_t n, int64_t nb, int nper, int k, int basis)
+{
+    if (!h || n < 0 || nb < 0 || k < 0 || basis < 0) return RPBD_BAD_ARG;
+    void* p;
+    const int64_t n_pad = (n + 255) / 256 * 256;
+    const int kk = k < 1 ? 1 : k;
+    RPBD_TRY(ensure(h, BUF_PACK, (size_t)n_pad * (8 + 3 * kk + 4) * sizeof(double), &p));
+    RPBD_TRY(ensure(h, BUF_SCALE, (size_t)n_pad * sizeof(double), &p));
+    if (basis > 0) {
+        const int64_t len = 3 * n + 6 * nb;
+        RPBD_TRY(ensure(h, BUF_KRYLOV, (size_t)(basis + 1) * len * sizeof(double), &p));
+    }
+    (void)nper;
+    return RPBD_OK;
+}
+
+long long rpbd_launch_count(void) { return g_launches.load(); }
+
+int rpbd_profile_enable(rpbd_handle* h, int on)
+{
+    if (!h) return RPBD_BAD_ARG;
+    h->profile = on != 0;
+    return RPBD_OK;
+}
+
+int rpbd_profile_read(rpbd_handle* h, int dtype, int k, double* ms, long long* launches, double* pairs, int reset)
+{
+    if (!h || !ms || !launches || !pairs) return RPBD_BAD_ARG;
+    *ms = 0.0;
+    *launches = 0;
+    *pairs = 0.0;
+    RPBD_CU(h, cudaDeviceSynchronize());
+    std::vector<ProfRec> keep;
+    for (auto& r : h->prof) {
+        if (r.dtype == dtype && r.k == k) {
+            float t = 0.0f;
+            RPBD_CU(h, cudaEventElapsedTime(&t, r.a, r.b));
+            *ms += t;
+            *launches += 1;
+            *pairs += r.pairs;
+        }
+        if (reset) {
+            h->ev_pool.push_back(r.a);
+            h->ev_pool.push_back(r.b);
+        } else {
+            keep.push_back(r);
+        }
+    }
+    h->prof.swap(keep);
+    return RPBD_OK;
+}
+
+int rpbd_blobs_from_bodies(rpbd_handle* h, int64_t nb, int nper, const double* shape, const double* q,
+                           const double* theta, double* r, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (nb < 0 || nper <= 0 || !shape || !q || !theta || !r)
+        return set_error(h, RPBD_BAD_ARG, "blobs_from_bodies: bad arguments");
+    launch_blobs(nb, nper, shape, q, theta, r, S(stream));
+    RPBD_LAUNCH_CHECK(h);
+    return RPBD_OK;
+}
+
+int rpbd_mobility_apply(rpbd_handle* h, int64_t n, const double* r, const void* F, void* U, int k, int dtype,
+                        void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (n < 0) return set_error(h, RPBD_BAD_ARG, "n < 0");
+    return mobility_apply_impl(h, n, r, F, U, k, dtype, false, S(stream));
+}
+
+int rpbd_mobility_apply_mixed(rpbd_handle* h, int64_t n, const double* r, const double* F, double* U, int k,
+                              int dtype, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (n < 0) return set_error(h, RPBD_BAD_ARG, "n < 0");
+    return mobility_apply_impl(h, n, r, F, U, k, dtype, true, S(stream));
+}
+
+int rpbd_K_apply(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* U,
+                 double* out, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (nb < 0 || nper <= 0 || !r || !q || !U || !out) return set_error(h, RPBD_BAD_ARG, "K_apply: bad arguments");
+    launch_K(nb, nper, r, q, U, out, S(stream));
+    RPBD_LAUNCH_CHECK(h);
+    return RPBD_OK;
+}
+
+int rpbd_KT_apply(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* lam,
+                  double* out, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (nb < 0 || nper <= 0 || !r || !q || !lam || !out)
+        return set_error(h, RPBD_BAD_ARG, "KT_apply: bad arguments");
+    launch_KT(nb, nper, r, q, lam, out, S(stream));
+    RPBD_LAUNCH_CHECK(h);
+    return RPBD_OK;
+}
+
+int rpbd_philox_normals(rpbd_handle* h, uint64_t seed, uint32_t step, uint32_t sid, int64_t n, double* out,
+                        void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (n < 0 || (n > 0 && !out)) return set_error(h, RPBD_BAD_ARG, "philox_normals: bad arguments");
+    if (n / 4 >= (int64_t)0xffffffffLL) return set_error(h, RPBD_BAD_ARG, "philox_normals: n too large");
+    launch_normals(seed, step, sid, n, out, S(stream));
+    RPBD_LAUNCH_CHECK(h);
+    return RPBD_OK;
+}
+
+int rpbd_blob_forces(rpbd_handle* h, int64_t n, const double* r, const rpbd_forces* f, double* out, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (n < 0 || !r || !f || !out) return set_error(h, RPBD_BAD_ARG, "blob_forces: bad arguments");
+    launch_blob_forces(n, r, *f, out, S(stream));
+    RPBD_LAUNCH_CHECK(h);
+    return RPBD_OK;
+}
+
+}  // extern "C"

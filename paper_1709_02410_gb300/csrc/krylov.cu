@@ -1,0 +1,585 @@
+// Krylov solvers of the hot path, FP64 vectors on the device:
+//
+//  Lanczos M^{1/2} W (Sec. 2.2): Lanczos on G = L^-1 M L^-T (L the block
+//    Cholesky preconditioner) from v_1 = W/|W| with full (classical, twice)
+//    reorthogonalisation; f(G) W ~ |W| V_m T_m^{1/2} e_1, T_m^{1/2} e_1 from a
+//    one-warp cyclic Jacobi eigendecomposition of the tridiagonal T_m; stop
+//    when |y_m - y_{m-1}| / |y_m| < tol (evaluated in the small space, V is
+//    orthonormal); output L y_m.
+//  GMRES (Sec. 2.1, eq. saddle): right-preconditioned restarted GMRES(m) on
+//    [M -K; -K^T 0] with the exact body-block solve of Sec. 2.2 as
+//    preconditioner; Arnoldi by classical Gram-Schmidt applied twice, Givens
+//    rotations and the Hessenberg least-squares solve in a device kernel.
+//
+// The host drives the iteration and reads one FP64 scalar per iteration (the
+// residual estimate or the Lanczos change) to decide whether to stop; every
+// arithmetic step runs in the kernels below.
+#include <cuda_runtime.h>
+
+#include <cmath>
+
+#include "rpbd_internal.cuh"
+
+namespace rpbd {
+
+constexpr int DOT_BLOCKS = 256;
+constexpr int LANCZOS_MAX = 80;
+
+// ---------------------------------------------------------------------------
+// vector kernels
+
+// partial[i * gridDim.x + bx] = sum over the block's slice of V_i . w
+__global__ void multidot_kernel(int64_t n, const double* __restrict__ V, int64_t ld, const double* __restrict__ w,
+                                double* __restrict__ partial)
+{
+    const int i = blockIdx.y;
+    const double* v = V + (int64_t)i * ld;
+    double s = 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        s += v[e] * w[e];
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) partial[(int64_t)i * gridDim.x + blockIdx.x] = s;
+    }
+}
+
+// out[i] (+)= sum_b partial[i * nb + b]; one block per i
+__global__ void reduce_partials_kernel(int nblocks, const double* __restrict__ partial, double* __restrict__ out,
+                                       int accumulate)
+{
+    const int i = blockIdx.x;
+    double s = 0.0;
+    for (int b = threadIdx.x; b < nblocks; b += blockDim.x) s += partial[(int64_t)i * nblocks + b];
+    __shared__ double red[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        s = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+        if (threadIdx.x == 0) out[i] = accumulate ? out[i] + s : s;
+    }
+}
+
+// w -= sum_i h[i] V_i
+__global__ void multiaxpy_kernel(int64_t n, const double* __restrict__ V, int64_t ld, int nv,
+                                 const double* __restrict__ h, double* __restrict__ w)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double s = w[e];
+        for (int i = 0; i < nv; ++i) s -= h[i] * V[(int64_t)i * ld + e];
+        w[e] = s;
+    }
+}
+
+// out = scale * sum_i y[i] V_i   (scale = *scale_dev when scale_dev != NULL)
+__global__ void lincomb_kernel(int64_t n, const double* __restrict__ V, int64_t ld, int nv,
+                               const double* __restrict__ y, double scale, const double* __restrict__ scale_dev,
+                               double* __restrict__ out)
+{
+    const double sc = scale_dev ? scale * scale_dev[0] : scale;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x) {
+        double s = 0.0;
+        for (int i = 0; i < nv; ++i) s += y[i] * V[(int64_t)i * ld + e];
+        out[e] = sc * s;
+    }
+}
+
+// out = x / sqrt(*nrm2)  (or 0 when the norm vanishes)
+__global__ void normalize_kernel(int64_t n, const double* __restrict__ x, const double* __restrict__ nrm2,
+                                 double* __restrict__ out)
+{
+    const double nv = sqrt(nrm2[0]);
+    const double inv = nv > 0.0 ? 1.0 / nv : 0.0;
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        out[e] = x[e] * inv;
+}
+
+__global__ void add_kernel(int64_t n, const double* __restrict__ x, double* __restrict__ y)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        y[e] += x[e];
+}
+
+// saddle operator pieces: lamout -= K U ; Uout = -K^T lam (done with launch_KT then negate)
+__global__ void K_sub_kernel(int64_t nb, int nper, const double* __restrict__ r, const double* __restrict__ q,
+                             const double* __restrict__ U, double* __restrict__ out)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t n = nb * nper;
+    if (i >= n) return;
+    const int64_t p = i / nper;
+    const double d0 = r[i] - q[3 * p], d1 = r[n + i] - q[3 * p + 1], d2 = r[2 * n + i] - q[3 * p + 2];
+    const double* u = U + 6 * p;
+    out[i] -= u[0] + (u[4] * d2 - u[5] * d1);
+    out[n + i] -= u[1] + (u[5] * d0 - u[3] * d2);
+    out[2 * n + i] -= u[2] + (u[3] * d1 - u[4] * d0);
+}
+
+__global__ void negate_kernel(int64_t n, double* __restrict__ x)
+{
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+        x[e] = -x[e];
+}
+
+static unsigned vgrid(int64_t n)
+{
+    int64_t g = (n + 255) / 256;
+    if (g > 152 * 8) g = 152 * 8;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+// h[0..nv) = V^T w (accumulate != 0: h += V^T w)
+static int multidot(rpbd_handle* h, int64_t n, const double* V, int64_t ld, int nv, const double* w, double* out,
+                    int accumulate, double* partial, cudaStream_t st)
+{
+    multidot_kernel<<<dim3(DOT_BLOCKS, nv), 256, 0, st>>>(n, V, ld, w, partial); count_launch();
+    reduce_partials_kernel<<<nv, 256, 0, st>>>(DOT_BLOCKS, partial, out, accumulate); count_launch();
+    RPBD_LAUNCH_CHECK(h);
+    return RPBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// small GMRES kernels (one thread)
+
+// H column j from hcol[0..j] and hcol[j+1] = |w|^2; rotations; residual estimate
+__global__ void gmres_column_kernel(int j, int mdim, const double* __restrict__ hcol, double* __restrict__ H,
+                                    double* __restrict__ cs, double* __restrict__ sn, double* __restrict__ g,
+                                    const double* __restrict__ bnorm, double* __restrict__ res)
+{
+    double* col = H + (int64_t)j * (mdim + 1);
+    for (int i = 0; i <= j; ++i) col[i] = hcol[i];
+    col[j + 1] = sqrt(hcol[j + 1]);
+    for (int i = 0; i < j; ++i) {
+        const double t = cs[i] * col[i] + sn[i] * col[i + 1];
+        col[i + 1] = -sn[i] * col[i] + cs[i] * col[i + 1];
+        col[i] = t;
+    }
+    const double den = hypot(col[j], col[j + 1]);
+    if (den > 0.0) {
+        cs[j] = col[j] / den;
+        sn[j] = col[j + 1] / den;
+    } else {
+        cs[j] = 1.0;
+        sn[j] = 0.0;
+    }
+    col[j] = den;
+    col[j + 1] = 0.0;
+    g[j + 1] = -sn[j] * g[j];
+    g[j] = cs[j] * g[j];
+    res[0] = fabs(g[j + 1]) / bnorm[0];
+}
+
+// y = H(0:k,0:k)^-1 g(0:k), upper triangular back substitution
+__global__ void gmres_backsolve_kernel(int k, int mdim, const double* __restrict__ H, const double* __restrict__ g,
+                                       double* __restrict__ y)
+{
+    for (int i = k - 1; i >= 0; --i) {
+        double s = g[i];
+        for (int c = i + 1; c < k; ++c) s -= H[(int64_t)c * (mdim + 1) + i] * y[c];
+        const double d = H[(int64_t)i * (mdim + 1) + i];
+        y[i] = d != 0.0 ? s / d : 0.0;
+    }
+}
+
+// g = [sqrt(nrm2), 0, ...]; bnorm (when first) = sqrt(nrm2); res = sqrt(nrm2)/bnorm
+__global__ void gmres_start_kernel(int mdim, const double* __restrict__ nrm2, double* __restrict__ g,
+                                   double* __restrict__ bnorm, int first, double* __restrict__ res)
+{
+    const double b = sqrt(nrm2[0]);
+    for (int i = 0; i <= mdim; ++i) g[i] = 0.0;
+    g[0] = b;
+    if (first) bnorm[0] = b;
+    res[0] = bnorm[0] > 0.0 ? b / bnorm[0] : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// Lanczos small kernels
+
+// alpha/beta bookkeeping: alpha[m] = h[m] (after both passes), beta[m] = |w|
+__global__ void lanczos_coef_kernel(int m, const double* __restrict__ h, const double* __restrict__ nrm2,
+                                    double* __restrict__ alpha, double* __restrict__ beta)
+{
+    alpha[m] = h[m];
+    beta[m] = sqrt(nrm2[0]);
+}
+
+// One warp: eigendecomposition of the (m+1) x (m+1) tridiagonal T by cyclic
+// Jacobi, c = T^{1/2} e_1, change = |c - [c_prev; 0]| / |c|.
+__global__ void lanczos_sqrt_kernel(int m1, const double* __restrict__ alpha, const double* __restrict__ beta,
+                                    double* __restrict__ c, double* __restrict__ c_prev, double* __restrict__ change)
+{
+    extern __shared__ double sm[];
+    double* A = sm;            // m1 x m1 row-major
+    double* Q = sm + m1 * m1;  // eigenvectors, columns
+    const int lane = threadIdx.x;
+    for (int e = lane; e < m1 * m1; e += 32) {
+        const int i = e / m1, j = e % m1;
+        double v = 0.0;
+        if (i == j) v = alpha[i];
+        else if (j == i + 1) v = beta[i];
+        else if (i == j + 1) v = beta[j];
+        A[e] = v;
+        Q[e] = (i == j) ? 1.0 : 0.0;
+    }
+    __syncwarp();
+    double fro = 0.0;
+    for (int e = lane; e < m1 * m1; e += 32) fro += A[e] * A[e];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
+    for (int sweep = 0; sweep < 60; ++sweep) {
+        double off = 0.0;
+        for (int e = lane; e < m1 * m1; e += 32) {
+            const int i = e / m1, j = e % m1;
+            if (i != j) off += A[e] * A[e];
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
+        if (off <= 1e-32 * fro) break;
+        for (int p = 0; p < m1 - 1; ++p)
+            for (int qq = p + 1; qq < m1; ++qq) {
+                const double apq = A[p * m1 + qq];
+                const double app = A[p * m1 + p], aqq = A[qq * m1 + qq];
+                if (!(fabs(apq) > 1e-300) || fabs(apq) < 1e-19 * sqrt(fabs(app * aqq))) continue;
+                const double tau = (aqq - app) / (2.0 * apq);
+                const double t = tau != 0.0 ? copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau)) : 1.0;
+                const double cc = 1.0 / sqrt(1.0 + t * t), s = t * cc;
+                __syncwarp();
+                for (int k = lane; k < m1; k += 32) {
+                    if (k != p && k != qq) {
+                        const double akp = A[k * m1 + p], akq = A[k * m1 + qq];
+                        const double np = cc * akp - s * akq, nq = s * akp + cc * akq;
+                        A[k * m1 + p] = np;
+                        A[p * m1 + k] = np;
+                        A[k * m1 + qq] = nq;
+                        A[qq * m1 + k] = nq;
+                    }
+                    const double vkp = Q[k * m1 + p], vkq = Q[k * m1 + qq];
+                    Q[k * m1 + p] = cc * vkp - s * vkq;
+                    Q[k * m1 + qq] = s * vkp + cc * vkq;
+                }
+                __syncwarp();
+                if (lane == 0) {
+                    A[p * m1 + p] = app - t * apq;
+                    A[qq * m1 + qq] = aqq + t * apq;
+                    A[p * m1 + qq] = 0.0;
+                    A[qq * m1 + p] = 0.0;
+                }
+                __syncwarp();
+            }
+    }
+    __syncwarp();
+    double nc = 0.0, nd = 0.0;
+    for (int i = lane; i < m1; i += 32) {
+        double v = 0.0;
+        for (int k = 0; k < m1; ++k) {
+            const double lam = A[k * m1 + k];
+            v += Q[i * m1 + k] * sqrt(lam > 0.0 ? lam : 0.0) * Q[k];  // Q[0 * m1 + k]
+        }
+        const double prev = i < m1 - 1 ? c_prev[i] : 0.0;
+        nc += v * v;
+        nd += (v - prev) * (v - prev);
+        c[i] = v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nc += __shfl_xor_sync(0xffffffffu, nc, o);
+        nd += __shfl_xor_sync(0xffffffffu, nd, o);
+    }
+    __syncwarp();
+    for (int i = lane; i < m1; i += 32) c_prev[i] = c[i];
+    if (lane == 0) change[0] = nc > 0.0 ? sqrt(nd / nc) : 0.0;
+}
+
+// ---------------------------------------------------------------------------
+// host helpers
+
+static int read_scalar(rpbd_handle* h, const double* dev, double* out, cudaStream_t st)
+{
+    RPBD_CU(h, cudaMemcpyAsync(h->host_small, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
+    RPBD_CU(h, cudaStreamSynchronize(st));
+    *out = h->host_small[0];
+    return RPBD_OK;
+}
+
+static int check_flag(rpbd_handle* h, cudaStream_t st)
+{
+    int flag = 0;
+    RPBD_CU(h, cudaMemcpyAsync(&flag, h->dev_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RPBD_CU(h, cudaStreamSynchronize(st));
+    if (flag == 1) return set_error(h, RPBD_TIMEOUT, "a pair kernel's bounded wait expired");
+    return RPBD_OK;
+}
+
+// small device scratch layout (doubles)
+struct Small {
+    double* base;
+    int mdim;
+    double* H() { return base; }                                   // (mdim+1) * mdim
+    double* cs() { return H() + (int64_t)(mdim + 1) * mdim; }      // mdim
+    double* sn() { return cs() + mdim; }                           // mdim
+    double* g() { return sn() + mdim; }                            // mdim + 1
+    double* y() { return g() + mdim + 1; }                         // mdim + 1
+    double* hcol() { return y() + mdim + 1; }                      // mdim + 2
+    double* scal() { return hcol() + mdim + 2; }                   // 8 scalars
+    double* partial() { return scal() + 8; }                       // DOT_BLOCKS * (mdim + 2)
+    static size_t count(int mdim)
+    {
+        return (size_t)(mdim + 1) * mdim + 2 * mdim + 3 * (mdim + 1) + 1 + 8 + (size_t)DOT_BLOCKS * (mdim + 2);
+    }
+};
+
+// ---------------------------------------------------------------------------
+// Lanczos
+
+int lanczos_impl(rpbd_handle* h, int64_t n, const double* r, const double* W, double* out, double tol, int max_iter,
+                 int dtype, int use_precond, rpbd_stats* stats, cudaStream_t st)
+{
+    if (n <= 0) return set_error(h, RPBD_BAD_ARG, "lanczos: n <= 0");
+    if (max_iter < 1 || max_iter > LANCZOS_MAX) return set_error(h, RPBD_BAD_ARG, "lanczos: max_iter must be in 1..80");
+    if (use_precond && (!h->prec_valid || h->prec_nb * h->prec_nper != n))
+        return set_error(h, RPBD_BAD_ARG, "lanczos: preconditioner not built for these blobs");
+    const int64_t len = 3 * n;
+    double *V, *vec, *sm;
+    RPBD_TRY(ensure_t(h, BUF_KRYLOV, (size_t)(max_iter + 1) * len, &V));
+    RPBD_TRY(ensure_t(h, BUF_VEC, (size_t)3 * len, &vec));
+    const int mdim = LANCZOS_MAX + 1;
+    RPBD_TRY(ensure_t(h, BUF_SMALL, Small::count(mdim) + 4 * (size_t)mdim, &sm));
+    Small S{sm, mdim};
+    double* alpha = S.partial() + (size_t)DOT_BLOCKS * (mdim + 2);
+    double* beta = alpha + mdim;
+    double* cvec = beta + mdim;
+    double* cprev = cvec + mdim;
+    double* z = vec;
+    double* y = vec + len;
+    double* w = vec + 2 * len;
+    double* sc = S.scal();  // [0] |W|^2, [1] |w|^2, [2] change
+    static bool attr = false;
+    if (!attr) {
+        RPBD_CU(h, cudaFuncSetAttribute(lanczos_sqrt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                        2 * LANCZOS_MAX * LANCZOS_MAX * (int)sizeof(double)));
+        attr = true;
+    }
+    RPBD_CU(h, cudaMemsetAsync(h->dev_flag, 0, sizeof(int), st));
+    RPBD_CU(h, cudaMemsetAsync(cprev, 0, sizeof(double) * mdim, st));
+    const unsigned g = vgrid(len);
+    RPBD_TRY(multidot(h, len, W, 0, 1, W, &sc[0], 0, S.partial(), st));
+    normalize_kernel<<<g, 256, 0, st>>>(len, W, &sc[0], V); count_launch();
+    RPBD_LAUNCH_CHECK(h);
+    double W2;
+    RPBD_TRY(read_scalar(h, &sc[0], &W2, st));
+    if (!(W2 > 0.0)) {
+        RPBD_CU(h, cudaMemsetAsync(out, 0, sizeof(double) * len, st));
+        if (stats) *stats = rpbd_stats{0, 0, 0.0, RPBD_OK};
+        return RPBD_OK;
+    }
+    int m = 0, matvecs = 0, status = RPBD_NOT_CONVERGED;
+    double change = INFINITY;
+    for (;; ++m) {
+        const double* vm = V + (int64_t)m * len;
+        // w = G v_m
+        if (use_precond) {
+            RPBD_TRY(precond_apply_impl(h, 2, vm, z, st));
+            RPBD_TRY(mobility_apply_impl(h, n, r, z, y, 1, dtype, true, st));
+            RPBD_TRY(precond_apply_impl(h, 1, y, w, st));
+        } else {
+            RPBD_TRY(mobility_apply_impl(h, n, r, vm, w, 1, dtype, true, st));
+        }
+        ++matvecs;
+        // full reorthogonalisation, classical Gram-Schmidt twice
+        RPBD_TRY(multidot(h, len, V, len, m + 1, w, S.hcol(), 0, S.partial(), st));
+        multiaxpy_kernel<<<g, 256, 0, st>>>(len, V, len, m + 1, S.hcol(), w); count_launch();
+        RPBD_TRY(multidot(h, len, V, len, m + 1, w, S.y(), 0, S.partial(), st));
+        multiaxpy_kernel<<<g, 256, 0, st>>>(len, V, len, m + 1, S.y(), w); count_launch();
+        add_kernel<<<1, 128, 0, st>>>(m + 1, S.y(), S.hcol()); count_launch();
+        RPBD_TRY(multidot(h, len, w, 0, 1, w, &sc[1], 0, S.partial(), st));
+        lanczos_coef_kernel<<<1, 1, 0, st>>>(m, S.hcol(), &sc[1], alpha, beta); count_launch();
+        const int m1 = m + 1;
+        lanczos_sqrt_kernel<<<1, 32, 2 * m1 * m1 * sizeof(double), st>>>(m1, alpha, beta, cvec, cprev, &sc[2]); count_launch();
+        normalize_kernel<<<g, 256, 0, st>>>(len, w, &sc[1], V + (int64_t)(m + 1) * len); count_launch();
+        RPBD_LAUNCH_CHECK(h);
+        double cur[3];
+        RPBD_CU(h, cudaMemcpyAsync(h->host_small, sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RPBD_CU(h, cudaStreamSynchronize(st));
+        cur[1] = h->host_small[1];
+        cur[2] = h->host_small[2];
+        if (m >= 1) {
+            change = cur[2];
+            if (change < tol) { status = RPBD_OK; break; }
+        }
+        if (!(cur[1] > 1e-300 * W2) ) { status = RPBD_OK; break; }  // invariant subspace: exact
+        if (m + 1 >= max_iter) break;
+    }
+    RPBD_TRY(check_flag(h, st));
+    const int nv = m + 1;
+    // y = |W| V c
+    lincomb_kernel<<<g, 256, 0, st>>>(len, V, len, nv, cvec, std::sqrt(W2), nullptr, use_precond ? y : out); count_launch();
+    if (use_precond) RPBD_TRY(precond_apply_impl(h, 0, y, out, st));
+    RPBD_LAUNCH_CHECK(h);
+    if (stats) *stats = rpbd_stats{nv, matvecs, m >= 1 ? change : 0.0, status};
+    return status == RPBD_OK ? RPBD_OK : RPBD_NOT_CONVERGED;
+}
+
+// ---------------------------------------------------------------------------
+// GMRES on the saddle system
+
+struct SaddleOp {
+    rpbd_handle* h;
+    int64_t nb, n;
+    int nper;
+    const double* r;
+    const double* q;
+    int dtype;
+    cudaStream_t st;
+    // out = A x: [M lam - K U; -K^T lam]
+    int apply(const double* x, double* out)
+    {
+        const double* lam = x;
+        const double* U = x + 3 * n;
+        RPBD_TRY(mobility_apply_impl(h, n, r, lam, out, 1, dtype, true, st));
+        K_sub_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nb, nper, r, q, U, out); count_launch();
+        launch_KT(nb, nper, r, q, lam, out + 3 * n, st);
+        negate_kernel<<<vgrid(6 * nb), 256, 0, st>>>(6 * nb, out + 3 * n); count_launch();
+        RPBD_LAUNCH_CHECK(h);
+        return RPBD_OK;
+    }
+    int precond(const double* x, double* out)
+    {
+        return precond_saddle_impl(h, x, x + 3 * n, out, out + 3 * n, st);
+    }
+};
+
+int gmres_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* slip,
+               const double* FT, double* lambda, double* U, double tol, int max_iter, int restart, int dtype,
+               int build_precond, rpbd_stats* stats, cudaStream_t st)
+{
+    if (nb <= 0 || nper <= 0) return set_error(h, RPBD_BAD_ARG, "gmres: no bodies");
+    if (restart < 1 || restart > 200 || max_iter < 1) return set_error(h, RPBD_BAD_ARG, "gmres: bad restart/max_iter");
+    const int64_t n = nb * nper;
+    if (build_precond) RPBD_TRY(precond_build_impl(h, nb, nper, r, q, st));
+    if (!h->prec_valid || h->prec_nb != nb || h->prec_nper != nper)
+        return set_error(h, RPBD_BAD_ARG, "gmres: preconditioner not built for these bodies");
+    const int64_t len = 3 * n + 6 * nb;
+    const int mdim = restart;
+    double *V, *vec, *sm;
+    RPBD_TRY(ensure_t(h, BUF_KRYLOV, (size_t)(mdim + 1) * len, &V));
+    RPBD_TRY(ensure_t(h, BUF_VEC, (size_t)4 * len, &vec));
+    RPBD_TRY(ensure_t(h, BUF_SMALL, Small::count(mdim), &sm));
+    Small S{sm, mdim};
+    double* x = vec;
+    double* b = vec + len;
+    double* w = vec + 2 * len;
+    double* z = vec + 3 * len;
+    double* sc = S.scal();  // [0] |.|^2, [1] bnorm, [2] residual estimate
+    RPBD_CU(h, cudaMemsetAsync(h->dev_flag, 0, sizeof(int), st));
+    // b = [-slip; -FT]
+    if (slip) launch_scale_copy(3 * n, -1.0, slip, b, st);
+    else RPBD_CU(h, cudaMemsetAsync(b, 0, sizeof(double) * 3 * n, st));
+    if (FT) launch_scale_copy(6 * nb, -1.0, FT, b + 3 * n, st);
+    else RPBD_CU(h, cudaMemsetAsync(b + 3 * n, 0, sizeof(double) * 6 * nb, st));
+    RPBD_CU(h, cudaMemsetAsync(x, 0, sizeof(double) * len, st));
+    SaddleOp A{h, nb, n, nper, r, q, dtype, st};
+    const unsigned g = vgrid(len);
+    int total = 0, matvecs = 0, status = RPBD_NOT_CONVERGED;
+    double res = 1.0;
+    bool first = true;
+    for (;;) {
+        // r0 = b - A x  (x = 0 on the first cycle)
+        if (first) {
+            launch_scale_copy(len, 1.0, b, w, st);
+        } else {
+            RPBD_TRY(A.apply(x, w));
+            ++matvecs;
+            launch_axpby(len, 1.0, b, -1.0, w, w, st);
+        }
+        RPBD_TRY(multidot(h, len, w, 0, 1, w, &sc[0], 0, S.partial(), st));
+        gmres_start_kernel<<<1, 1, 0, st>>>(mdim, &sc[0], S.g(), &sc[1], first ? 1 : 0, &sc[2]); count_launch();
+        normalize_kernel<<<g, 256, 0, st>>>(len, w, &sc[0], V); count_launch();
+        RPBD_LAUNCH_CHECK(h);
+        RPBD_TRY(read_scalar(h, &sc[2], &res, st));
+        {
+            double bn;
+            RPBD_TRY(read_scalar(h, &sc[1], &bn, st));
+            if (!(bn > 0.0)) {  // zero right-hand side: zero solution
+                status = RPBD_OK;
+                res = 0.0;
+                break;
+            }
+        }
+        first = false;
+        if (res <= tol) { status = RPBD_OK; break; }
+        if (total >= max_iter) break;
+        int j = 0;
+        for (; j < mdim && total < max_iter; ++j) {
+            const double* vj = V + (int64_t)j * len;
+            RPBD_TRY(A.precond(vj, z));
+            RPBD_TRY(A.apply(z, w));
+            ++matvecs;
+            RPBD_TRY(multidot(h, len, V, len, j + 1, w, S.hcol(), 0, S.partial(), st));
+            multiaxpy_kernel<<<g, 256, 0, st>>>(len, V, len, j + 1, S.hcol(), w); count_launch();
+            RPBD_TRY(multidot(h, len, V, len, j + 1, w, S.y(), 0, S.partial(), st));
+            multiaxpy_kernel<<<g, 256, 0, st>>>(len, V, len, j + 1, S.y(), w); count_launch();
+            add_kernel<<<1, 256, 0, st>>>(j + 1, S.y(), S.hcol()); count_launch();
+            RPBD_TRY(multidot(h, len, w, 0, 1, w, S.hcol() + j + 1, 0, S.partial(), st));
+            normalize_kernel<<<g, 256, 0, st>>>(len, w, S.hcol() + j + 1, V + (int64_t)(j + 1) * len); count_launch();
+            gmres_column_kernel<<<1, 1, 0, st>>>(j, mdim, S.hcol(), S.H(), S.cs(), S.sn(), S.g(), &sc[1], &sc[2]); count_launch();
+            RPBD_LAUNCH_CHECK(h);
+            ++total;
+            RPBD_TRY(read_scalar(h, &sc[2], &res, st));
+            if (res <= tol) { ++j; break; }
+        }
+        // x += P^-1 (V y)
+        gmres_backsolve_kernel<<<1, 1, 0, st>>>(j, mdim, S.H(), S.g(), S.y()); count_launch();
+        lincomb_kernel<<<g, 256, 0, st>>>(len, V, len, j, S.y(), 1.0, nullptr, w); count_launch();
+        RPBD_TRY(A.precond(w, z));
+        add_kernel<<<g, 256, 0, st>>>(len, z, x); count_launch();
+        RPBD_LAUNCH_CHECK(h);
+        if (res <= tol) { status = RPBD_OK; break; }
+        if (total >= max_iter) break;
+    }
+    RPBD_TRY(check_flag(h, st));
+    RPBD_CU(h, cudaMemcpyAsync(lambda, x, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
+    RPBD_CU(h, cudaMemcpyAsync(U, x + 3 * n, sizeof(double) * 6 * nb, cudaMemcpyDeviceToDevice, st));
+    if (stats) *stats = rpbd_stats{total, matvecs + total, res, status};
+    return status == RPBD_OK ? RPBD_OK : RPBD_NOT_CONVERGED;
+}
+
+}  // namespace rpbd
+
+using namespace rpbd;
+
+extern "C" {
+
+int rpbd_lanczos_sqrt_apply(rpbd_handle* h, int64_t n, const double* r, const double* W, double* out, double tol,
+                            int max_iter, int dtype, int use_precond, rpbd_stats* stats, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (!r || !W || !out) return set_error(h, RPBD_BAD_ARG, "lanczos: null pointer");
+    if (!(tol > 0)) return set_error(h, RPBD_BAD_ARG, "lanczos: tol must be > 0");
+    if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "lanczos: bad dtype");
+    return lanczos_impl(h, n, r, W, out, tol, max_iter, dtype, use_precond, stats,
+                        reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rpbd_gmres_rigid_solve(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* slip,
+                           const double* FT, double* lambda, double* U, double tol, int max_iter, int restart,
+                           int dtype, int build_precond, rpbd_stats* stats, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (!r || !q || !lambda || !U) return set_error(h, RPBD_BAD_ARG, "gmres: null pointer");
+    if (!(tol > 0)) return set_error(h, RPBD_BAD_ARG, "gmres: tol must be > 0");
+    if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "gmres: bad dtype");
+    return gmres_impl(h, nb, nper, r, q, slip, FT, lambda, U, tol, max_iter, restart, dtype, build_precond, stats,
+                      reinterpret_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

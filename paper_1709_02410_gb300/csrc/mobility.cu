@@ -1,0 +1,400 @@
+// Wall-RPY blob-mobility matvec U = M(r) F (Sec. 2.1; the dense GPU sum
+// the paper uses for every application of M, Sec. 2.1 and Sec. 4.2).
+//
+// Pipeline of one apply:
+//   1. pack:   per blob, one 16-byte aligned record holding its position
+//              (FP32: hi/lo split of x, y; FP64: plain) and its k force
+//              vectors pre-scaled by the wall-overlap scale s_j.
+//   2. pairs:  grid (target tiles) x (source chunks).  Each CTA streams its
+//              chunk of source records through shared memory with 1-D TMA
+//              bulk copies (cp.async.bulk + mbarrier, NST-deep ring); each
+//              thread owns one target blob, forms the 3x3 block of every
+//              pair once and applies it to all k right-hand sides from
+//              registers.  FP32 kernels keep FP32 sums over one chunk.
+//   3. reduce: sums the chunk partials in FP64 in a fixed order (the
+//              result is deterministic), multiplies by s_i / (8 pi eta) and
+//              writes U in the caller's type.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+
+#include "rpbd_internal.cuh"
+#include "wall_rpy.cuh"
+
+namespace rpbd {
+
+// ---------------------------------------------------------------------------
+// record layouts
+
+template <class R, int K>
+struct Rec;
+// FP32: [x_hi, y_hi, x_lo, y_lo][z~, F(0,x), F(0,y), F(0,z), F(1,x) ...] padded to 4 floats
+template <int K>
+struct Rec<float, K> {
+    static constexpr int TAIL = ((1 + 3 * K) + 3) / 4 * 4;
+    static constexpr int LEN = 4 + TAIL;  // floats
+};
+// FP64: [x, y, z~, F(0,x), F(0,y), F(0,z), ...] padded to 2 doubles
+template <int K>
+struct Rec<double, K> {
+    static constexpr int LEN = ((3 + 3 * K) + 1) / 2 * 2;  // doubles
+};
+
+// partial sums: FP32 kernels store float chunk sums, FP64 kernels double
+template <class R>
+struct PartialT { using type = R; };
+
+// ---------------------------------------------------------------------------
+// PTX helpers: mbarrier + 1-D TMA bulk copy
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init()
+{
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async()
+{
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void tma_load_1d(void* dst, const void* src, uint32_t bytes, uint64_t* bar)
+{
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_u32(dst)),
+        "l"(src), "r"(bytes), "r"(smem_u32(bar))
+        : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
+{
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+// bounded wait: ~2 s of SM clock at most; false on timeout
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+{
+    if (mbar_try_wait(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (!mbar_try_wait(bar, parity)) {
+        if (clock64() - t0 > 4000000000LL) return false;
+    }
+    return true;
+}
+
+// ---------------------------------------------------------------------------
+// 1. pack
+
+template <class R, int K, class In>
+__global__ void pack_kernel(int64_t n, int64_t n_pad, int k, const double* __restrict__ r,
+                            const In* __restrict__ F, double a, int wall, double s_min,
+                            R* __restrict__ rec, double* __restrict__ scale)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    constexpr int LEN = Rec<R, K>::LEN;
+    R* o = rec + i * LEN;
+    double x, y, zt, s;
+    if (i < n) {
+        x = r[i];
+        y = r[n + i];
+        const double z = r[2 * n + i];
+        if (wall) {
+            zt = z > a ? z : a;
+            const double t = z / a;
+            s = t >= 1.0 ? 1.0 : (t <= s_min ? s_min : t);
+        } else {
+            zt = z;
+            s = 1.0;
+        }
+        scale[i] = s;
+    } else {  // padding source: far away, zero force
+        x = 1.0e7;
+        y = 1.0e7;
+        zt = a;
+        s = 0.0;
+    }
+    if constexpr (sizeof(R) == 4) {
+        const float xh = (float)x, yh = (float)y;
+        o[0] = xh;
+        o[1] = yh;
+        o[2] = (float)(x - (double)xh);
+        o[3] = (float)(y - (double)yh);
+        o[4] = (float)zt;
+        constexpr int TAIL = Rec<R, K>::TAIL;
+#pragma unroll
+        for (int q = 1; q < TAIL; ++q) o[4 + q] = 0.0f;
+        if (i < n)
+            for (int m = 0; m < k; ++m)
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    o[5 + 3 * m + c] = (float)(s * (double)F[((int64_t)m * 3 + c) * n + i]);
+    } else {
+        o[0] = x;
+        o[1] = y;
+        o[2] = zt;
+#pragma unroll
+        for (int q = 3; q < LEN; ++q) o[q] = 0.0;
+        if (i < n)
+            for (int m = 0; m < k; ++m)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o[3 + 3 * m + c] = s * (double)F[((int64_t)m * 3 + c) * n + i];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2. pair kernel
+
+template <class R, int K, int BT, int TS, int NST, bool WALL>
+__global__ void __launch_bounds__(BT) pair_kernel(const R* __restrict__ rec, int64_t n, int64_t n_pad,
+                                                  int tiles_per_chunk, int n_tiles, PairConst<R> pc,
+                                                  typename PartialT<R>::type* __restrict__ partial,
+                                                  int* __restrict__ err_flag)
+{
+    constexpr int LEN = Rec<R, K>::LEN;
+    constexpr uint32_t TILE_BYTES = TS * LEN * sizeof(R);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    R* stage = reinterpret_cast<R*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + NST * TILE_BYTES);
+
+    const int tid = threadIdx.x;
+    const int chunk = blockIdx.y;
+    const int tile0 = chunk * tiles_per_chunk;
+    const int ntile = min(tiles_per_chunk, n_tiles - tile0);
+    const int64_t i = blockIdx.x * (int64_t)BT + tid;
+    const int64_t ii = i < n ? i : n - 1;
+
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int s = 0; s < NST && s < ntile; ++s) {
+            mbar_expect_tx(&bar[s], TILE_BYTES);
+            tma_load_1d(stage + (size_t)s * TS * LEN, rec + (size_t)(tile0 + s) * TS * LEN, TILE_BYTES, &bar[s]);
+        }
+    }
+
+    // target position
+    const R* me = rec + ii * LEN;
+    R xh, yh, xl = R(0), yl = R(0), zi;
+    if constexpr (sizeof(R) == 4) {
+        const float4 p = *reinterpret_cast<const float4*>(me);
+        xh = p.x; yh = p.y; xl = p.z; yl = p.w;
+        zi = me[4];
+    } else {
+        xh = me[0]; yh = me[1]; zi = me[2];
+    }
+
+    R acc[3 * K];
+#pragma unroll
+    for (int q = 0; q < 3 * K; ++q) acc[q] = R(0);
+
+    int t = 0;
+    bool bad = false;
+    for (; t < ntile; ++t) {
+        const int s = t % NST;
+        const uint32_t par = (t / NST) & 1;
+        const bool ok = mbar_wait_bounded(&bar[s], par);
+        if (ok) {
+            const R* st = stage + (size_t)s * TS * LEN;
+#pragma unroll 1
+            for (int jj = 0; jj < TS; ++jj) {
+                const R* rj = st + jj * LEN;
+                R dx, dy, zj;
+                R f[3 * K];
+                if constexpr (sizeof(R) == 4) {
+                    const float4 p = *reinterpret_cast<const float4*>(rj);
+                    dx = (xh - p.x) + (xl - p.z);
+                    dy = (yh - p.y) + (yl - p.w);
+                    constexpr int TAIL = Rec<R, K>::TAIL;
+                    float tail[TAIL];
+#pragma unroll
+                    for (int q = 0; q < TAIL / 4; ++q) {
+                        const float4 v = reinterpret_cast<const float4*>(rj + 4)[q];
+                        tail[4 * q + 0] = v.x; tail[4 * q + 1] = v.y;
+                        tail[4 * q + 2] = v.z; tail[4 * q + 3] = v.w;
+                    }
+                    zj = tail[0];
+#pragma unroll
+                    for (int q = 0; q < 3 * K; ++q) f[q] = tail[1 + q];
+                } else {
+                    dx = xh - rj[0];
+                    dy = yh - rj[1];
+                    zj = rj[2];
+#pragma unroll
+                    for (int q = 0; q < 3 * K; ++q) f[q] = rj[3 + q];
+                }
+                const R dz = zi - zj;
+                R Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz;
+                pair_block<R, R, WALL>(dx, dy, dz, zi, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
+#pragma unroll
+                for (int m = 0; m < K; ++m) {
+                    const R fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
+                    acc[3 * m + 0] += Mxx * fx + Mxy * fy + Mxz * fz;
+                    acc[3 * m + 1] += Mxy * fx + Myy * fy + Myz * fz;
+                    acc[3 * m + 2] += Mzx * fx + Mzy * fy + Mzz * fz;
+                }
+            }
+        }
+        if (__syncthreads_or(!ok)) {
+            bad = true;
+            break;
+        }
+        if (tid == 0 && t + NST < ntile) {
+            fence_proxy_async();
+            mbar_expect_tx(&bar[s], TILE_BYTES);
+            tma_load_1d(stage + (size_t)s * TS * LEN, rec + (size_t)(tile0 + t + NST) * TS * LEN, TILE_BYTES,
+                        &bar[s]);
+        }
+    }
+    if (bad) {
+        // record the timeout, then let copies still in flight land (bounded)
+        if (tid == 0) {
+            atomicExch(err_flag, 1);
+            for (int u = t + 1; u < ntile && u < t + NST; ++u)
+                mbar_wait_bounded(&bar[u % NST], (u / NST) & 1);
+        }
+        return;
+    }
+    if (i < n) {
+#pragma unroll
+        for (int q = 0; q < 3 * K; ++q) partial[((int64_t)chunk * 3 * K + q) * n_pad + i] = acc[q];
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. reduce
+
+template <class P, class Out>
+__global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_chunks,
+                              const P* __restrict__ partial, const double* __restrict__ scale,
+                              double inv8pieta, Out* __restrict__ U)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double s = scale[i] * inv8pieta;
+    for (int q = 0; q < 3 * k; ++q) {
+        double sum = 0.0;
+        for (int c = 0; c < n_chunks; ++c) sum += (double)partial[((int64_t)c * 3 * kt + q) * n_pad + i];
+        U[(int64_t)q * n + i] = (Out)(s * sum);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// launch
+
+struct Tile {
+    int BT, TS, NST;
+};
+
+template <class R, int K>
+constexpr Tile default_tile()
+{
+    if constexpr (sizeof(R) == 4) return Tile{128, 64, 3};
+    else return Tile{128, 32, 3};
+}
+
+template <class R, int K, bool WALL, class In, class Out>
+static int apply_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
+{
+    constexpr Tile T = default_tile<R, K>();
+    constexpr int BT = T.BT, TS = T.TS, NST = T.NST;
+    constexpr int LEN = Rec<R, K>::LEN;
+    const int64_t n_pad = (n + TS - 1) / TS * TS;
+    const int n_tiles = (int)(n_pad / TS);
+    const int64_t tgt_tiles = (n + BT - 1) / BT;
+    // chunk: enough CTAs to fill the GPU several times over, at most
+    // MAX_CHUNK sources summed in the kernel's own precision
+    const int max_chunk_tiles = (sizeof(R) == 4 ? 2048 : 4096) / TS;
+    const int64_t want_ctas = (int64_t)h->sm_count * 8;
+    int64_t S = (want_ctas + tgt_tiles - 1) / tgt_tiles;
+    if (S < 1) S = 1;
+    int tiles_per_chunk = (int)((n_tiles + S - 1) / S);
+    if (tiles_per_chunk > max_chunk_tiles) tiles_per_chunk = max_chunk_tiles;
+    if (tiles_per_chunk < 1) tiles_per_chunk = 1;
+    const int n_chunks = (n_tiles + tiles_per_chunk - 1) / tiles_per_chunk;
+
+    R* rec;
+    double* scale;
+    typename PartialT<R>::type* partial;
+    RPBD_TRY(ensure_t(h, BUF_PACK, (size_t)n_pad * LEN, &rec));
+    RPBD_TRY(ensure_t(h, BUF_SCALE, (size_t)n_pad, &scale));
+    RPBD_TRY(ensure_t(h, BUF_PARTIAL, (size_t)n_chunks * 3 * K * n_pad, &partial));
+
+    const PairConst<R> pc = PairConst<R>::make(h->p.a);
+    pack_kernel<R, K, In><<<(unsigned)((n_pad + 255) / 256), 256, 0, st>>>(n, n_pad, k, r, F, h->p.a, h->p.wall,
+                                                                           h->p.s_min, rec, scale); count_launch();
+    RPBD_LAUNCH_CHECK(h);
+    const size_t smem = (size_t)NST * TS * LEN * sizeof(R) + NST * sizeof(uint64_t);
+    auto kern = pair_kernel<R, K, BT, TS, NST, WALL>;
+    static bool attr_set = false;
+    if (!attr_set) {
+        RPBD_CU(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        attr_set = true;
+    }
+    dim3 grid((unsigned)tgt_tiles, (unsigned)n_chunks);
+    if (h->profile) prof_begin(h, st);
+    kern<<<grid, BT, smem, st>>>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, h->dev_flag); count_launch();
+    if (h->profile) prof_end(h, st, sizeof(R) == 4 ? RPBD_F32 : RPBD_F64, K, (double)n * (double)n);
+    RPBD_LAUNCH_CHECK(h);
+    const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
+    reduce_kernel<typename PartialT<R>::type, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+        n, n_pad, k, K, n_chunks, partial, scale, inv8pieta, U); count_launch();
+    RPBD_LAUNCH_CHECK(h);
+    return RPBD_OK;
+}
+
+template <class R, bool WALL, class In, class Out>
+static int apply_dispatch(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
+{
+    if (k <= 1) return apply_k<R, 1, WALL>(h, n, r, F, U, k, st);
+    if (k <= 2) return apply_k<R, 2, WALL>(h, n, r, F, U, k, st);
+    if (k <= 4) return apply_k<R, 4, WALL>(h, n, r, F, U, k, st);
+    if (k <= 8) return apply_k<R, 8, WALL>(h, n, r, F, U, k, st);
+    return apply_k<R, 16, WALL>(h, n, r, F, U, k, st);
+}
+
+template <class In, class Out>
+static int apply_typed(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, int dtype,
+                       cudaStream_t st)
+{
+    const bool wall = h->p.wall != 0;
+    if (dtype == RPBD_F32)
+        return wall ? apply_dispatch<float, true>(h, n, r, F, U, k, st)
+                    : apply_dispatch<float, false>(h, n, r, F, U, k, st);
+    return wall ? apply_dispatch<double, true>(h, n, r, F, U, k, st)
+                : apply_dispatch<double, false>(h, n, r, F, U, k, st);
+}
+
+int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* F, void* U, int k, int dtype,
+                        bool io_double, cudaStream_t st)
+{
+    if (n <= 0) return RPBD_OK;
+    if (k < 1 || k > 16) return set_error(h, RPBD_BAD_ARG, "k must be in 1..16");
+    if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "bad dtype");
+    if (!r || !F || !U) return set_error(h, RPBD_BAD_ARG, "null pointer");
+    if (io_double || dtype == RPBD_F64)
+        return apply_typed<double, double>(h, n, r, (const double*)F, (double*)U, k, dtype, st);
+    return apply_typed<float, float>(h, n, r, (const float*)F, (float*)U, k, dtype, st);
+}
+
+}  // namespace rpbd

@@ -1,0 +1,154 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "../../include/rpbd.h"
+
+namespace rpbd {
+
+// ---------------------------------------------------------------------------
+// Error handling
+
+struct Status {
+    int code = RPBD_OK;
+};
+
+#define RPBD_CU(h, call)                                                          \
+    do {                                                                          \
+        cudaError_t e_ = (call);                                                  \
+        if (e_ != cudaSuccess) return rpbd::set_error((h), RPBD_CUDA,             \
+                                                      std::string(#call) + ": " + \
+                                                          cudaGetErrorString(e_)); \
+    } while (0)
+
+#define RPBD_LAUNCH_CHECK(h)                                                  \
+    do {                                                                      \
+        cudaError_t e_ = cudaGetLastError();                                  \
+        if (e_ != cudaSuccess)                                                \
+            return rpbd::set_error((h), RPBD_CUDA,                            \
+                                   std::string("launch: ") + cudaGetErrorString(e_)); \
+    } while (0)
+
+#define RPBD_TRY(expr)          \
+    do {                        \
+        int s_ = (expr);        \
+        if (s_ != RPBD_OK) return s_; \
+    } while (0)
+
+// ---------------------------------------------------------------------------
+// Device workspace: named growable buffers owned by the handle.
+
+enum Buf {
+    BUF_PACK = 0,    // packed source records of the pair kernels
+    BUF_SCALE,       // per-blob overlap scale s_i
+    BUF_PARTIAL,     // per-chunk partial sums of the pair kernels
+    BUF_PREC_L,      // block Cholesky factors
+    BUF_PREC_LINV,   // their inverses
+    BUF_PREC_MINV,   // M(pp)^-1
+    BUF_PREC_MINVK,  // M(pp)^-1 K_p
+    BUF_PREC_N,      // N_p
+    BUF_PREC_Q,      // tracking points of the preconditioner's bodies
+    BUF_KRYLOV,      // Krylov basis
+    BUF_VEC,         // solver vectors
+    BUF_SMALL,       // small device scalars (Hessenberg, tridiagonal, flags)
+    BUF_STEP,        // time-step vectors
+    BUF_R2,          // displaced positions (RFD, predictor)
+    BUF_AUX,         // misc
+    BUF_COUNT
+};
+
+struct ProfRec {
+    cudaEvent_t a, b;
+    int dtype, k;
+    double pairs;
+};
+
+}  // namespace rpbd
+
+#include <vector>
+
+struct rpbd_handle {
+    rpbd_params p;
+    int device = 0;
+    int sm_count = 0;
+    std::string err;
+    void* buf[rpbd::BUF_COUNT] = {};
+    size_t cap[rpbd::BUF_COUNT] = {};
+    // preconditioner state
+    int64_t prec_nb = 0;
+    int prec_nper = 0;
+    bool prec_valid = false;
+    // pinned host mirror for small read-backs
+    double* host_small = nullptr;
+    // device error flag (bounded waits in kernels)
+    int* dev_flag = nullptr;
+    // pair-kernel timing
+    bool profile = false;
+    std::vector<rpbd::ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace rpbd {
+
+int set_error(rpbd_handle* h, int code, const std::string& msg);
+// library-wide count of kernel launches (read by rpbd_launch_count)
+void count_launch();
+// pair-kernel timing records (rpbd_profile_*)
+void prof_begin(rpbd_handle* h, cudaStream_t st);
+void prof_end(rpbd_handle* h, cudaStream_t st, int dtype, int k, double pairs);
+// Ensure buffer b holds at least `bytes`; contents are not preserved.
+int ensure(rpbd_handle* h, Buf b, size_t bytes, void** out);
+template <class T>
+inline int ensure_t(rpbd_handle* h, Buf b, size_t count, T** out)
+{
+    void* p = nullptr;
+    int s = ensure(h, b, count * sizeof(T), &p);
+    *out = static_cast<T*>(p);
+    return s;
+}
+
+// mobility apply on FP64 blob vectors; dtype chooses the pair arithmetic
+int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* F, void* U,
+                        int k, int dtype, bool io_double, cudaStream_t st);
+
+// rigid kernels (FP64)
+void launch_K(int64_t nb, int nper, const double* r, const double* q, const double* U,
+              double* out, cudaStream_t st);
+void launch_KT(int64_t nb, int nper, const double* r, const double* q, const double* lam,
+               double* out, cudaStream_t st);
+void launch_blobs(int64_t nb, int nper, const double* shape, const double* q,
+                  const double* theta, double* r, cudaStream_t st);
+void launch_normals(uint64_t seed, uint32_t step, uint32_t sid, int64_t n, double* out,
+                    cudaStream_t st);
+void launch_blob_forces(int64_t n, const double* r, const rpbd_forces& f, double* out,
+                        cudaStream_t st);
+// q += s * U[:, :3]; theta = Rotate(theta, s * U[:, 3:])
+void launch_advance(int64_t nb, const double* q0, const double* th0, const double* U, double s,
+                    double* q1, double* th1, cudaStream_t st);
+
+// FP64 vector helpers
+void launch_axpby(int64_t n, double a, const double* x, double b, const double* y, double* out,
+                  cudaStream_t st);
+void launch_scale_copy(int64_t n, double a, const double* x, double* out, cudaStream_t st);
+int check_finite(rpbd_handle* h, int64_t n, const double* x, cudaStream_t st);
+
+int precond_apply_impl(rpbd_handle* h, int mode, const double* x, double* out, cudaStream_t st);
+// saddle block solve: (lam, U) = P^-1 (a, b)
+int precond_saddle_impl(rpbd_handle* h, const double* a, const double* b, double* lam,
+                        double* U, cudaStream_t st);
+
+int lanczos_impl(rpbd_handle* h, int64_t n, const double* r, const double* W, double* out,
+                 double tol, int max_iter, int dtype, int use_precond, rpbd_stats* stats,
+                 cudaStream_t st);
+int gmres_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q,
+               const double* slip, const double* FT, double* lambda, double* U, double tol,
+               int max_iter, int restart, int dtype, int build_precond, rpbd_stats* stats,
+               cudaStream_t st);
+int precond_build_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q,
+                       cudaStream_t st);
+
+}  // namespace rpbd

@@ -1,0 +1,208 @@
+// Device pair block of the wall-corrected RPY blob mobility.
+//
+// For a target blob at (xi, yi, zi) and a source blob at (xj, yj, zj), with
+// heights already clamped to z >= a (the wall-overlap reading), returns
+// 8 pi eta times the 3x3 block M_ij = M_RPY(d) + M_wall:
+//
+//   free-space RPY (Sec. 2.1):  d = r_i - r_j, r = |d|
+//     r >= 2a:  (1/r) [(1 + 2a^2/(3r^2)) I + (1 - 2a^2/r^2) d d^T / r^2]
+//     0<r<2a:   (4/(3a)) [(1 - 9r/(32a)) I + 3 d d^T / (32 a r)]
+//     r = 0:    (4/(3a)) I                      (self block, Stokes drag)
+//
+//   wall (Rotne-Prager-Blake, used in Sec. 4): image vector
+//   R = (dx, dy, zi + zj), e = R/|R|, t = zj/|R|, s = a/|R|:
+//     M_wall = (1/|R|) [A I + B e e^T + C e z^T + D z e^T + E z z^T]
+//     A = -1 - 2 e_z t + 2 t^2 + s^2 (2 e_z^2 - 2/3) + s^4 (2/3 - 10/3 e_z^2)
+//     B = -1 + 6 e_z t - 6 t^2 + s^2 (2 - 10 e_z^2) + s^4 (70/3 e_z^2 - 10/3)
+//     C = t (2 - 12 e_z^2) + 12 e_z t^2 + e_z s^2 (20 e_z^2 - 4)
+//         + e_z s^4 (40/3 - 140/3 e_z^2)
+//     D = 2 t - 20/3 e_z s^4
+//     E = -4 t^2 - 4 e_z^2 s^2 + s^4 (20 e_z^2 - 8/3)
+//   This is Blake's image system for a point force with the RPY (Faxen)
+//   regularisation (1 + a^2/6 Lap) applied at both blobs, reduced by hand to
+//   the five scalar coefficients above.
+//
+// Because R and d share their x, y components, the block assembles as
+//   Mxx = alpha + beta dx^2, Mxy = Myx = beta dx dy, Myy = alpha + beta dy^2,
+//   Mxz = dx gx, Myz = dy gx, Mzx = dx gz, Mzy = dy gz,
+//   Mzz = alpha + c2 dz^2 + b3 Rz^2 + (C + D) Rz/|R|^2 + E/|R|,
+// with alpha = c1 + A/|R|, b3 = B/|R|^3, beta = c2 + b3,
+//   gx = c2 dz + b3 Rz + C/|R|^2, gz = c2 dz + b3 Rz + D/|R|^2.
+#pragma once
+
+#include <cuda_runtime.h>
+
+namespace rpbd {
+
+// Geometry constants of one launch (blob radius a).
+template <class R>
+struct PairConst {
+    R a2;        // a^2
+    R a23;       // 2 a^2 / 3
+    R two_a2;    // 2 a^2
+    R four_a2;   // 4 a^2
+    R k_self;    // 4 / (3 a)
+    R k_ovl;     // 3 / (8 a^2)
+    R inv8a2;    // 1 / (8 a^2)
+    __host__ __device__ static PairConst make(double a)
+    {
+        PairConst c;
+        c.a2 = R(a * a);
+        c.a23 = R(2.0 * a * a / 3.0);
+        c.two_a2 = R(2.0 * a * a);
+        c.four_a2 = R(4.0 * a * a);
+        c.k_self = R(4.0 / (3.0 * a));
+        c.k_ovl = R(3.0 / (8.0 * a * a));
+        c.inv8a2 = R(1.0 / (8.0 * a * a));
+        return c;
+    }
+};
+
+__device__ __forceinline__ float rsqrt_(float x) { return rsqrtf(x); }
+__device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
+__device__ __forceinline__ float val_(float x) { return x; }
+__device__ __forceinline__ double val_(double x) { return x; }
+
+// Block entries, 8 pi eta times M_ij.  T is float, double or a dual number;
+// K is the plain scalar type of the constants.
+template <class T, class K, bool WALL>
+__device__ __forceinline__ void pair_block(T dx, T dy, T dz, T zi, T zj, const PairConst<K>& c,
+                                           T& Mxx, T& Mxy, T& Mxz, T& Myy, T& Myz, T& Mzx,
+                                           T& Mzy, T& Mzz)
+{
+    T rho2 = dx * dx + dy * dy;
+    T r2 = rho2 + dz * dz;
+    T rinv = rsqrt_(r2);
+    T rinv2 = rinv * rinv;
+    // far branch
+    T c1f = rinv * (K(1) + c.a23 * rinv2);
+    T c2f = rinv * rinv2 * (K(1) - c.two_a2 * rinv2);
+    // overlap branch
+    T rr = r2 * rinv;
+    T c1o = c.k_self - c.k_ovl * rr;
+    T c2o = rinv * c.inv8a2;
+    const bool far = val_(r2) >= val_(c.four_a2);
+    const bool self = !(val_(r2) > K(0));
+    T c1 = far ? c1f : (self ? T(c.k_self) : c1o);
+    T c2 = far ? c2f : (self ? T(K(0)) : c2o);
+    if (!WALL) {
+        T g = c2 * dz;
+        Mxx = c1 + c2 * dx * dx;
+        Mxy = c2 * dx * dy;
+        Myy = c1 + c2 * dy * dy;
+        Mxz = dx * g;
+        Myz = dy * g;
+        Mzx = Mxz;
+        Mzy = Myz;
+        Mzz = c1 + c2 * dz * dz;
+        return;
+    }
+    T Rz = zi + zj;
+    T R2 = rho2 + Rz * Rz;
+    T Rinv = rsqrt_(R2);
+    T Rinv2 = Rinv * Rinv;
+    T ez = Rz * Rinv;
+    T t = zj * Rinv;
+    T s2 = c.a2 * Rinv2;
+    T s4 = s2 * s2;
+    T ez2 = ez * ez;
+    T t2 = t * t;
+    T u = ez * t;
+    T p = K(2) * (t2 - u);  // -2 e_z t + 2 t^2
+    T A = (p - K(1)) + s2 * (K(2) * ez2 - K(2.0 / 3.0)) + s4 * (K(2.0 / 3.0) - K(10.0 / 3.0) * ez2);
+    T B = (K(-1) - K(3) * p) + s2 * (K(2) - K(10) * ez2) + s4 * (K(70.0 / 3.0) * ez2 - K(10.0 / 3.0));
+    T C = t * (K(2) - K(12) * ez2) + K(12) * ez * t2 +
+          ez * (s2 * (K(20) * ez2 - K(4)) + s4 * (K(40.0 / 3.0) - K(140.0 / 3.0) * ez2));
+    T D = K(2) * t - K(20.0 / 3.0) * ez * s4;
+    T E = K(-4) * t2 - K(4) * ez2 * s2 + s4 * (K(20) * ez2 - K(8.0 / 3.0));
+    T b3 = B * Rinv * Rinv2;
+    T alpha = c1 + A * Rinv;
+    T beta = c2 + b3;
+    T cR = C * Rinv2;
+    T dR = D * Rinv2;
+    T g0 = c2 * dz + b3 * Rz;
+    T gx = g0 + cR;
+    T gz = g0 + dR;
+    Mxx = alpha + beta * dx * dx;
+    Mxy = beta * dx * dy;
+    Myy = alpha + beta * dy * dy;
+    Mxz = dx * gx;
+    Myz = dy * gx;
+    Mzx = dx * gz;
+    Mzy = dy * gz;
+    Mzz = alpha + c2 * dz * dz + b3 * Rz * Rz + (cR + dR) * Rz + E * Rinv;
+}
+
+// Forward-mode dual number with NP partials (device, FP64).
+template <int NP>
+struct Dual {
+    double v;
+    double g[NP];
+    __device__ Dual() {}
+    __device__ Dual(double x) : v(x)
+    {
+#pragma unroll
+        for (int q = 0; q < NP; ++q) g[q] = 0.0;
+    }
+};
+template <int NP>
+__device__ __forceinline__ double val_(const Dual<NP>& x) { return x.v; }
+template <int NP>
+__device__ __forceinline__ Dual<NP> operator+(const Dual<NP>& a, const Dual<NP>& b)
+{
+    Dual<NP> r; r.v = a.v + b.v;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r.g[q] = a.g[q] + b.g[q];
+    return r;
+}
+template <int NP>
+__device__ __forceinline__ Dual<NP> operator-(const Dual<NP>& a, const Dual<NP>& b)
+{
+    Dual<NP> r; r.v = a.v - b.v;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r.g[q] = a.g[q] - b.g[q];
+    return r;
+}
+template <int NP>
+__device__ __forceinline__ Dual<NP> operator*(const Dual<NP>& a, const Dual<NP>& b)
+{
+    Dual<NP> r; r.v = a.v * b.v;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r.g[q] = fma(a.g[q], b.v, a.v * b.g[q]);
+    return r;
+}
+template <int NP>
+__device__ __forceinline__ Dual<NP> operator+(const Dual<NP>& a, double b) { Dual<NP> r = a; r.v += b; return r; }
+template <int NP>
+__device__ __forceinline__ Dual<NP> operator+(double b, const Dual<NP>& a) { Dual<NP> r = a; r.v += b; return r; }
+template <int NP>
+__device__ __forceinline__ Dual<NP> operator-(const Dual<NP>& a, double b) { Dual<NP> r = a; r.v -= b; return r; }
+template <int NP>
+__device__ __forceinline__ Dual<NP> operator-(double b, const Dual<NP>& a)
+{
+    Dual<NP> r; r.v = b - a.v;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r.g[q] = -a.g[q];
+    return r;
+}
+template <int NP>
+__device__ __forceinline__ Dual<NP> operator*(const Dual<NP>& a, double b)
+{
+    Dual<NP> r; r.v = a.v * b;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r.g[q] = a.g[q] * b;
+    return r;
+}
+template <int NP>
+__device__ __forceinline__ Dual<NP> operator*(double b, const Dual<NP>& a) { return a * b; }
+template <int NP>
+__device__ __forceinline__ Dual<NP> rsqrt_(const Dual<NP>& a)
+{
+    Dual<NP> r; r.v = rsqrt(a.v);
+    double d = -0.5 * r.v * r.v * r.v;
+#pragma unroll
+    for (int q = 0; q < NP; ++q) r.g[q] = d * a.g[q];
+    return r;
+}
+
+}  // namespace rpbd

@@ -1,0 +1,114 @@
+"""GPU parity of the wall-RPY matvec (FP64 and FP32 multi-RHS kernels) and of
+the blob geometry against the CPU oracle, through the C ABI."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import mobility as om, rigid
+from paper_1709_02410_gb300 import F32, F64, synth
+
+from gpu_util import DEV, handle_for, oracle_params, positions, rel2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def test_blob_geometry_matches_oracle():
+    s = synth.c0_boomerangs_1920()
+    h = handle_for(s)
+    r = h.blobs_from_bodies(to_dev(s.shape), to_dev(s.q), to_dev(s.theta)).cpu().numpy()
+    np.testing.assert_allclose(r, positions(s), rtol=0, atol=1e-13)
+
+
+@pytest.mark.parametrize("wall", [True, False])
+def test_f64_matvec_c0(wall):
+    s = synth.c0_boomerangs_1920()
+    r = positions(s)
+    F = synth.gaussian(10, (3, s.n))
+    h = handle_for(s, wall=wall)
+    U = h.mobility_apply(to_dev(r), to_dev(F)).cpu().numpy()
+    Uo = om.apply(r, F, oracle_params(s, wall))
+    assert rel2(U, Uo) <= 1e-12
+
+
+@pytest.mark.parametrize("n", [1, 2, 15, 17, 33, 129, 1000])
+@pytest.mark.parametrize("k", [1, 3, 16])
+def test_f64_matvec_ragged(n, k):
+    """sizes below, at and across tile boundaries, penetrating blobs included"""
+    rng = np.random.default_rng(n * 31 + k)
+    box = max(2.0, np.sqrt(n) * 0.8)
+    r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
+    F = rng.standard_normal((k, 3, n))
+    s = synth.c0_boomerangs_1920()
+    h = handle_for(s)
+    U = h.mobility_apply(to_dev(r), to_dev(F)).cpu().numpy()
+    Uo = om.apply(r, F, oracle_params(s))
+    assert rel2(U, Uo) <= 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 4, 8, 16])
+def test_f32_matvec_c0(k):
+    s = synth.c0_boomerangs_1920()
+    r = positions(s)
+    F32in = synth.gaussian(20 + k, (k, 3, s.n), np.float32)
+    h = handle_for(s)
+    U = h.mobility_apply(to_dev(r), to_dev(F32in, torch.float32)).cpu().numpy()
+    Uo = om.apply(r, F32in.astype(np.float64), oracle_params(s))
+    for m in range(k):
+        assert rel2(U[m], Uo[m]) <= 1e-5
+
+
+@pytest.mark.parametrize("n", [1, 17, 65, 1000])
+def test_f32_matvec_ragged(n):
+    rng = np.random.default_rng(n)
+    box = max(2.0, np.sqrt(n))
+    r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
+    F = rng.standard_normal((5, 3, n)).astype(np.float32)
+    s = synth.c0_boomerangs_1920()
+    h = handle_for(s)
+    U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
+    assert rel2(U, Uo) <= 1e-5
+
+
+def test_mixed_mode_f32_pairs_f64_vectors():
+    s = synth.c0_boomerangs_1920()
+    r = positions(s)
+    F = synth.gaussian(30, (3, s.n))
+    h = handle_for(s)
+    U = h.mobility_apply(to_dev(r), to_dev(F), dtype=F32).cpu().numpy()
+    assert rel2(U, om.apply(r, F, oracle_params(s))) <= 1e-5
+
+
+def test_empty_is_noop():
+    s = synth.c0_boomerangs_1920()
+    h = handle_for(s)
+    r = torch.zeros((3, 0), dtype=torch.float64, device=DEV)
+    F = torch.zeros((3, 0), dtype=torch.float64, device=DEV)
+    U = h.mobility_apply(r, F)
+    assert U.numel() == 0
+
+
+def test_f32_k16_full_size_row_sampled():
+    """65,535 blobs, 16 right-hand sides, in the bench's launch configuration;
+    128 sampled target rows against the oracle."""
+    s = synth.c1_boomerangs_65535()
+    r = positions(s)
+    k = 16
+    F = synth.gaussian(40, (k, 3, s.n), np.float32)
+    h = handle_for(s)
+    U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    rows = np.random.default_rng(41).choice(s.n, 128, replace=False)
+    rows[0], rows[1] = 0, s.n - 1
+    Uo = om.apply(r, F.astype(np.float64), oracle_params(s), rows=rows)
+    assert rel2(U[:, :, rows], Uo) <= 1e-5
+
+
+def test_f64_full_size_row_sampled():
+    s = synth.c1_boomerangs_65535()
+    r = positions(s)
+    F = synth.gaussian(42, (3, s.n))
+    h = handle_for(s)
+    U = h.mobility_apply(to_dev(r), to_dev(F)).cpu().numpy()
+    rows = np.random.default_rng(43).choice(s.n, 64, replace=False)
+    Uo = om.apply(r, F, oracle_params(s), rows=rows)
+    assert rel2(U[:, rows], Uo) <= 1e-12

@@ -1,0 +1,173 @@
+"""GPU parity of the block preconditioner, Lanczos M^{1/2} W, GMRES saddle
+solve, RFD drift, adjoint and divergence against the oracle."""
+import numpy as np
+import pytest
+import scipy.linalg
+
+from oracle import krylov, mobility as om, precond, rfd, saddle
+from paper_1709_02410_gb300 import F32, F64, synth
+
+from gpu_util import handle_for, oracle_params, positions, rel2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def small(nb=8, seed=3, box=8.0, lift=True):
+    return synth.boomerang_suspension(nb, box, seed, lift=lift)
+
+
+@pytest.mark.parametrize("mode", [0, 1, 2, 3])
+def test_precond_apply_modes(mode):
+    s = small(12, 4)
+    r = positions(s)
+    pc = precond.BlockPrecond(r, s.q, s.nper, oracle_params(s))
+    x = np.random.default_rng(mode).standard_normal((3, s.n))
+    ref = [pc.L_apply, pc.Linv_apply, pc.LinvT_apply,
+           lambda v: om.blob_to_soa(np.concatenate([pc.Minv[p] @ om.soa_to_blob(v).reshape(s.nb, -1)[p]
+                                                    for p in range(s.nb)]))][mode](x)
+    h = handle_for(s)
+    h.precond_build(s.nper, to_dev(r), to_dev(s.q))
+    out = h.precond_apply(mode, to_dev(x)).cpu().numpy()
+    assert rel2(out, ref) <= 1e-11
+
+
+def test_lanczos_preconditioned_matches_dense():
+    s = small(8, 5)
+    r = positions(s)
+    prm = oracle_params(s)
+    pc = precond.BlockPrecond(r, s.q, s.nper, prm)
+    M = om.dense(r, prm)
+    Lb = scipy.linalg.block_diag(*pc.L)
+    G = np.linalg.solve(Lb, np.linalg.solve(Lb, M).T).T
+    W = synth.gaussian(6, (3, s.n))
+    ref = Lb @ (scipy.linalg.sqrtm(0.5 * (G + G.T)).real @ om.soa_to_blob(W))
+    h = handle_for(s)
+    h.precond_build(s.nper, to_dev(r), to_dev(s.q))
+    out, st = h.lanczos_sqrt_apply(to_dev(r), to_dev(W), tol=1e-12, max_iter=80)
+    assert st["status"] == 0
+    assert rel2(om.soa_to_blob(out.cpu().numpy()), ref) <= 1e-9
+
+
+def test_lanczos_matches_oracle_iterates():
+    """same tolerance, same stop rule: same iteration count and answer"""
+    s = small(10, 7)
+    r = positions(s)
+    prm = oracle_params(s)
+    pc = precond.BlockPrecond(r, s.q, s.nper, prm)
+    W = synth.gaussian(8, (3, s.n))
+    G = lambda v: pc.Linv_apply(om.apply(r, pc.LinvT_apply(v), prm))
+    y, it, ch = krylov.lanczos_sqrt(G, W, 1e-4, 80)
+    ref = pc.L_apply(y)
+    h = handle_for(s)
+    h.precond_build(s.nper, to_dev(r), to_dev(s.q))
+    out, st = h.lanczos_sqrt_apply(to_dev(r), to_dev(W), tol=1e-4, max_iter=80)
+    assert abs(st["iterations"] - it) <= 1
+    assert rel2(out.cpu().numpy(), ref) <= 1e-4
+
+
+def test_lanczos_unpreconditioned():
+    s = small(4, 9)
+    r = positions(s)
+    M = om.dense(r, oracle_params(s))
+    W = synth.gaussian(10, (3, s.n))
+    ref = scipy.linalg.sqrtm(M).real @ om.soa_to_blob(W)
+    h = handle_for(s)
+    out, st = h.lanczos_sqrt_apply(to_dev(r), to_dev(W), tol=1e-11, max_iter=80, use_precond=False)
+    assert rel2(om.soa_to_blob(out.cpu().numpy()), ref) <= 1e-8
+
+
+@pytest.mark.parametrize("dtype,tol,bound", [(F64, 1e-12, 1e-9), (F32, 1e-6, 1e-4)])
+def test_gmres_matches_dense_schur(dtype, tol, bound):
+    s = small(8, 11)
+    r = positions(s)
+    rng = np.random.default_rng(12)
+    slip = rng.standard_normal((3, s.n))
+    FT = rng.standard_normal((s.nb, 6)) * 1e-2
+    lam_d, U_d, _ = saddle.dense_solution(r, s.q, s.nper, oracle_params(s), slip, FT)
+    h = handle_for(s)
+    lam, U, st = h.gmres_rigid_solve(s.nper, to_dev(r), to_dev(s.q), to_dev(slip), to_dev(FT), tol=tol,
+                                     max_iter=200, restart=30, dtype=dtype)
+    assert st["status"] == 0
+    assert rel2(U.cpu().numpy(), U_d) <= bound
+    assert rel2(lam.cpu().numpy(), lam_d) <= 10 * bound
+
+
+def test_gmres_restarts_and_null_inputs():
+    s = small(6, 13)
+    r = positions(s)
+    FT = np.random.default_rng(14).standard_normal((s.nb, 6)) * 1e-2
+    lam_d, U_d, _ = saddle.dense_solution(r, s.q, s.nper, oracle_params(s), None, FT)
+    h = handle_for(s)
+    lam, U, st = h.gmres_rigid_solve(s.nper, to_dev(r), to_dev(s.q), None, to_dev(FT), tol=1e-12, restart=4,
+                                     max_iter=400)
+    assert st["status"] == 0
+    assert rel2(U.cpu().numpy(), U_d) <= 1e-9
+    # zero right-hand side gives zero
+    lam0, U0, st0 = h.gmres_rigid_solve(s.nper, to_dev(r), to_dev(s.q), None, None, tol=1e-8)
+    assert float(U0.abs().max()) == 0.0 and st0["iterations"] == 0
+
+
+def test_gmres_not_converged_reports_status():
+    s = small(8, 15)
+    r = positions(s)
+    slip = np.random.default_rng(16).standard_normal((3, s.n))
+    h = handle_for(s)
+    lam, U, st = h.gmres_rigid_solve(s.nper, to_dev(r), to_dev(s.q), to_dev(slip), None, tol=1e-14, max_iter=2)
+    assert st["status"] == -4 and st["iterations"] == 2
+
+
+@pytest.mark.parametrize("dtype,delta,bound", [(F64, 1e-6, 1e-7), (F32, 1e-3, 2e-3)])
+def test_rfd_drift_matches_oracle(dtype, delta, bound):
+    s = synth.c0_boomerangs_1920()
+    r = positions(s)
+    W = synth.gaussian(17, (3, s.n))
+    ref = rfd.rfd_drift(r, W, delta, oracle_params(s))
+    h = handle_for(s)
+    out = h.rfd_drift(to_dev(r), to_dev(W), delta, dtype=dtype).cpu().numpy()
+    assert rel2(out, ref) <= bound
+
+
+@pytest.mark.parametrize("lift", [True, False])
+def test_adjoint_matches_oracle_gradient(lift):
+    s = synth.boomerang_suspension(40, 10.0, 18, lift=lift)
+    r = positions(s)
+    rng = np.random.default_rng(19)
+    u, F = rng.standard_normal((2, 3, s.n))
+    h = handle_for(s)
+    g = h.mobility_adjoint(to_dev(r), to_dev(u), to_dev(F)).cpu().numpy()
+    go = om.grad(r, u, F, oracle_params(s))
+    assert rel2(g, go) <= 1e-11
+
+
+def test_divergence_matches_oracle():
+    s = synth.boomerang_suspension(30, 8.0, 20, lift=False)
+    r = positions(s)
+    h = handle_for(s)
+    d = h.mobility_divergence(to_dev(r)).cpu().numpy()
+    assert rel2(d, om.divergence(r, oracle_params(s))) <= 1e-11
+
+
+def test_adjoint_c2_sampled_and_fd():
+    """16,380 blobs: oracle gradient on sampled blobs, plus central
+    differences of the GPU matvec itself (h = 1e-6 a) on 64 coordinates."""
+    s = synth.c2_blobs_16384()
+    r = positions(s)
+    rng = np.random.default_rng(21)
+    u, F = rng.standard_normal((2, 3, s.n))
+    h = handle_for(s)
+    rd, ud, Fd = to_dev(r), to_dev(u), to_dev(F)
+    g = h.mobility_adjoint(rd, ud, Fd).cpu().numpy()
+    rows = rng.choice(s.n, 24, replace=False)
+    go = om.grad(r, u, F, oracle_params(s), rows=rows)
+    assert rel2(g[:, rows], go) <= 1e-11
+    hstep = 1e-6 * s.a
+    coords = rng.choice(3 * s.n, 64, replace=False)
+    for cidx in coords:
+        c, k = divmod(int(cidx), s.n)
+        rp, rm = r.copy(), r.copy()
+        rp[c, k] += hstep
+        rm[c, k] -= hstep
+        fp = float((ud * h.mobility_apply(to_dev(rp), Fd)).sum())
+        fm = float((ud * h.mobility_apply(to_dev(rm), Fd)).sum())
+        fd = (fp - fm) / (2 * hstep)
+        assert abs(fd - g[c, k]) <= 1e-5 * np.abs(g).max() + 1e-6 * abs(g[c, k])
