@@ -1,0 +1,47 @@
+"""Time one wall-RPY matvec variant on synthetic boomerangs (CUDA events).
+
+    python -m paper_1709_02410_gb300.profile_case --n 65535 --k 16 --dtype f32 --reps 5
+
+Prints one JSON line: seconds per launch (pack + pair kernel + reduce),
+pairs/s and matvecs/s.  Useful on its own and as the target of profilers.
+"""
+import argparse
+import json
+
+import numpy as np
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=65535, help="blobs (rounded down to whole 15-blob bodies)")
+    ap.add_argument("--k", type=int, default=1)
+    ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
+    ap.add_argument("--reps", type=int, default=3)
+    ap.add_argument("--wall", type=int, default=1)
+    a = ap.parse_args()
+    import torch
+    from . import F32, F64, Handle, synth
+    nb = max(1, a.n // 15)
+    s = synth.boomerang_suspension(nb, 40.0 * np.sqrt(nb / 128), 1)
+    dev = "cuda:0"
+    h = Handle(synth.ETA, s.a, synth.KT, wall=bool(a.wall))
+    T = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
+    r = h.blobs_from_bodies(T(s.shape), T(s.q), T(s.theta))
+    dt = torch.float32 if a.dtype == "f32" else torch.float64
+    F = T(synth.gaussian(7, (a.k, 3, s.n)), dt)
+    U = torch.empty_like(F)
+    h.mobility_apply(r, F, out=U)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        h.mobility_apply(r, F, out=U)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / a.reps
+    print(json.dumps({"n": s.n, "k": a.k, "dtype": a.dtype, "s_per_launch": t, "pairs_per_s": s.n * s.n / t,
+                      "matvecs_per_s": a.k / t}))
+
+
+if __name__ == "__main__":
+    main()
