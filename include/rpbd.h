@@ -40,6 +40,7 @@ extern "C" {
 #define RPBD_NOT_CONVERGED (-4)
 #define RPBD_TIMEOUT (-5)
 #define RPBD_NO_MEM (-6)
+#define RPBD_TOO_LARGE (-7) /* beyond the fixed scratch of rpbd_mobility_apply_f32_noalloc */
 
 /* arithmetic of the pair kernels */
 #define RPBD_F64 0 /* FP64 pair math, FP64 accumulation */
@@ -120,6 +121,29 @@ int rpbd_mobility_apply(rpbd_handle* h, int64_t n, const double* r, const void* 
  * dtype (the mixed mode the Krylov solvers use). */
 int rpbd_mobility_apply_mixed(rpbd_handle* h, int64_t n, const double* r, const double* F,
                               double* U, int k, int dtype, void* stream);
+
+/* Allocation-free FP32 matvec, for callers that must not call the CUDA
+ * allocator at all: for example a plug-in running inside a host framework
+ * whose caching allocator owns the device memory, or a real-time loop where
+ * an allocation's latency or failure is not acceptable.  The paper has no
+ * counterpart; it computes exactly what rpbd_mobility_apply computes with
+ * dtype RPBD_F32 (F and U float [k][3][n], r double SoA).
+ *  - No handle: the physical parameters come in *p.  Allocates nothing and
+ *    calls no allocating routine; its scratch is one 27.6 MiB array in device
+ *    memory that the library declares statically, which every GPU that loads
+ *    the library holds until the process exits.
+ *  - Limits set by that array: n <= 16384 blobs and k <= 16; larger sizes
+ *    return RPBD_TOO_LARGE and do nothing.
+ *  - The first call on a device looks up the array's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call uses the same array, whatever the stream: calls that can
+ *    overlap on the GPU (different streams, or different host threads) race
+ *    on it and corrupt each other's results; order them.
+ *  - Asynchronous on `stream`; returns RPBD_OK, RPBD_TOO_LARGE, RPBD_BAD_ARG
+ *    or RPBD_CUDA (no handle, so no message beyond rpbd_status_string). */
+int rpbd_mobility_apply_f32_noalloc(const rpbd_params* p, int64_t n, const double* r, const float* F,
+                                    float* U, int k, void* stream);
 
 /* ---- a7: adjoint and divergence ---------------------------------------- */
 

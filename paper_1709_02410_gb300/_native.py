@@ -8,7 +8,7 @@ LIB_PATH = os.path.join(HERE, "librpbd.so")
 
 F64, F32 = 0, 1
 STATUS = {0: "ok", -1: "bad argument", -2: "bad input", -3: "CUDA error", -4: "not converged",
-          -5: "device wait timed out", -6: "out of device memory"}
+          -5: "device wait timed out", -6: "out of device memory", -7: "too large for the fixed scratch"}
 
 
 class Params(C.Structure):
@@ -61,6 +61,7 @@ SIGNATURES = [
     ("rpbd_step_emt", _I, [_P, _I64, _I, _P, _P, _P, C.POINTER(Forces), C.POINTER(StepParams),
                            C.POINTER(Stats), _P]),
     ("rpbd_blob_forces", _I, [_P, _I64, _P, C.POINTER(Forces), _P, _P]),
+    ("rpbd_mobility_apply_f32_noalloc", _I, [C.POINTER(Params), _I64, _P, _P, _P, _I, _P]),
     ("rpbd_launch_count", C.c_longlong, []),
     ("rpbd_profile_enable", _I, [_P, _I]),
     ("rpbd_profile_read", _I, [_P, _I, _I, C.POINTER(C.c_double), C.POINTER(C.c_longlong),

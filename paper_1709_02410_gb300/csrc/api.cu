@@ -88,6 +88,7 @@ const char* rpbd_status_string(int status)
     case RPBD_NOT_CONVERGED: return "iteration did not converge";
     case RPBD_TIMEOUT: return "device wait timed out";
     case RPBD_NO_MEM: return "out of device memory";
+    case RPBD_TOO_LARGE: return "size beyond the allocation-free matvec's fixed scratch (n <= 16384, k <= 16)";
     default: return "unknown status";
     }
 }

@@ -398,3 +398,134 @@ int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* 
 }
 
 }  // namespace rpbd
+
+// ---------------------------------------------------------------------------
+// Allocation-free variant of the FP32 multi-RHS matvec.
+//
+// Its scratch (packed source records, overlap scales, chunk partials and the
+// wait-timeout flag) lives in one file-scope device array instead of the
+// handle's workspace, so the call needs neither a handle nor cudaMalloc.
+// Sizes are fixed by that array: n <= NOALLOC_MAX_N blobs, 1 <= k <= 16.
+
+namespace rpbd {
+namespace noalloc {
+
+constexpr int64_t NOALLOC_MAX_N = 16384;
+constexpr int MAX_CHUNK_SOURCES = 2048;  // FP32 chunk length, as in the workspace path
+constexpr int64_t MAX_CHUNKS = NOALLOC_MAX_N / MAX_CHUNK_SOURCES;
+constexpr size_t REC_BYTES = (size_t)NOALLOC_MAX_N * Rec<float, 16>::LEN * sizeof(float);
+constexpr size_t SCALE_BYTES = (size_t)NOALLOC_MAX_N * sizeof(double);
+constexpr size_t PARTIAL_BYTES = (size_t)MAX_CHUNKS * 3 * 16 * NOALLOC_MAX_N * sizeof(float);
+constexpr size_t FLAG_BYTES = 256;
+constexpr size_t SCRATCH_BYTES = REC_BYTES + SCALE_BYTES + PARTIAL_BYTES + FLAG_BYTES;  // 27.6 MiB
+
+}  // namespace noalloc
+}  // namespace rpbd
+
+// Every device that loads the library holds this array until the process exits.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[rpbd::noalloc::SCRATCH_BYTES];
+
+namespace rpbd {
+namespace noalloc {
+
+constexpr int MAX_DEVICES = 64;
+static void* g_scratch_addr[MAX_DEVICES] = {};
+
+// Device address of the scratch array on the current device; looked up once
+// per device (host code may not use the symbol itself as a pointer).
+static int scratch_address(unsigned char** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) return RPBD_CUDA;
+    if (!g_scratch_addr[dev]) {
+        void* p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return RPBD_CUDA;
+        g_scratch_addr[dev] = p;
+    }
+    *out = static_cast<unsigned char*>(g_scratch_addr[dev]);
+    return RPBD_OK;
+}
+
+template <int K, bool WALL>
+static int apply(int sm_count, const rpbd_params& p, int64_t n, const double* r, const float* F, float* U, int k,
+                 cudaStream_t st)
+{
+    constexpr Tile T = default_tile<float, K>();
+    constexpr int BT = T.BT, TS = T.TS, NST = T.NST;
+    constexpr int LEN = Rec<float, K>::LEN;
+    unsigned char* base = nullptr;
+    if (scratch_address(&base) != RPBD_OK) return RPBD_CUDA;
+    float* rec = reinterpret_cast<float*>(base);
+    double* scale = reinterpret_cast<double*>(base + REC_BYTES);
+    float* partial = reinterpret_cast<float*>(base + REC_BYTES + SCALE_BYTES);
+    int* flag = reinterpret_cast<int*>(base + REC_BYTES + SCALE_BYTES + PARTIAL_BYTES);
+
+    const int64_t n_pad = (n + TS - 1) / TS * TS;
+    const int n_tiles = (int)(n_pad / TS);
+    const int64_t tgt_tiles = (n + BT - 1) / BT;
+    const int max_chunk_tiles = MAX_CHUNK_SOURCES / TS;
+    const int64_t want_ctas = (int64_t)sm_count * 8;
+    int64_t S = (want_ctas + tgt_tiles - 1) / tgt_tiles;
+    if (S < 1) S = 1;
+    int tiles_per_chunk = (int)((n_tiles + S - 1) / S);
+    if (tiles_per_chunk > max_chunk_tiles) tiles_per_chunk = max_chunk_tiles;
+    if (tiles_per_chunk < 1) tiles_per_chunk = 1;
+    // no more chunks than the partial region holds (at n = NOALLOC_MAX_N and
+    // K = 16 this is exactly the 2048-source chunk)
+    const int64_t fit = (int64_t)(PARTIAL_BYTES / ((size_t)3 * K * n_pad * sizeof(float)));
+    const int min_tiles = (int)((n_tiles + fit - 1) / fit);
+    if (tiles_per_chunk < min_tiles) tiles_per_chunk = min_tiles;
+    const int n_chunks = (n_tiles + tiles_per_chunk - 1) / tiles_per_chunk;
+    // the layout below must fit the array (guaranteed by n <= NOALLOC_MAX_N)
+    if ((size_t)n_pad * LEN * sizeof(float) > REC_BYTES || (size_t)n_pad * sizeof(double) > SCALE_BYTES ||
+        (size_t)n_chunks * 3 * K * n_pad * sizeof(float) > PARTIAL_BYTES)
+        return RPBD_BAD_ARG;
+
+    if (cudaMemsetAsync(flag, 0, sizeof(int), st) != cudaSuccess) return RPBD_CUDA;
+    const PairConst<float> pc = PairConst<float>::make(p.a);
+    pack_kernel<float, K, float><<<(unsigned)((n_pad + 255) / 256), 256, 0, st>>>(n, n_pad, k, r, F, p.a, p.wall,
+                                                                               p.s_min, rec, scale);
+    count_launch();
+    const size_t smem = (size_t)NST * TS * LEN * sizeof(float) + NST * sizeof(uint64_t);
+    static_assert((size_t)NST * TS * Rec<float, 16>::LEN * sizeof(float) + NST * sizeof(uint64_t) <= 48 * 1024,
+                  "the no-alloc kernels must fit the default dynamic shared memory limit");
+    pair_kernel<float, K, BT, TS, NST, WALL><<<dim3((unsigned)tgt_tiles, (unsigned)n_chunks), BT, smem, st>>>(
+        rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, flag);
+    count_launch();
+    const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * p.eta);
+    reduce_kernel<float, float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_chunks, partial, scale,
+                                                                          inv8pieta, U);
+    count_launch();
+    return cudaGetLastError() == cudaSuccess ? RPBD_OK : RPBD_CUDA;
+}
+
+template <bool WALL>
+static int dispatch(int sm, const rpbd_params& p, int64_t n, const double* r, const float* F, float* U, int k,
+                    cudaStream_t st)
+{
+    if (k <= 1) return apply<1, WALL>(sm, p, n, r, F, U, k, st);
+    if (k <= 2) return apply<2, WALL>(sm, p, n, r, F, U, k, st);
+    if (k <= 4) return apply<4, WALL>(sm, p, n, r, F, U, k, st);
+    if (k <= 8) return apply<8, WALL>(sm, p, n, r, F, U, k, st);
+    return apply<16, WALL>(sm, p, n, r, F, U, k, st);
+}
+
+}  // namespace noalloc
+}  // namespace rpbd
+
+extern "C" int rpbd_mobility_apply_f32_noalloc(const rpbd_params* p, int64_t n, const double* r, const float* F,
+                                               float* U, int k, void* stream)
+{
+    using namespace rpbd::noalloc;
+    if (!p || !(p->eta > 0) || !(p->a > 0) || !(p->s_min > 0) || p->s_min > 1) return RPBD_BAD_ARG;
+    if (n < 0 || k < 1) return RPBD_BAD_ARG;
+    if (n > NOALLOC_MAX_N || k > 16) return RPBD_TOO_LARGE;  // beyond the fixed scratch array
+    if (n == 0) return RPBD_OK;
+    if (!r || !F || !U) return RPBD_BAD_ARG;
+    int dev = 0, sm = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return RPBD_CUDA;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return p->wall ? dispatch<true>(sm, *p, n, r, F, U, k, st) : dispatch<false>(sm, *p, n, r, F, U, k, st);
+}
