@@ -35,6 +35,9 @@ N = NB * NPER
 K_RHS = 16
 F_GEOM = 116                 # algorithmic flops of one pair block (FMA = 2), see the design doc
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
+# DRAM bytes (read + write) per launch from one ncu capture of the current
+# kernels (profiles/pair_kernel_f32_k*_boomerangs_65535.md); None when not captured
+NCU_TRAFFIC = {"f32_k1": 2106368, "f32_k16": 20269312 + 342761728}
 
 
 def f_pair(k):
@@ -276,7 +279,7 @@ def run_ours(args, rank, world, local):
             flops = d["pairs"] / d["launches"] * f_pair(k)
             ach = flops / avg / 1e12
             roof = {"bound": "alu", "kernel": f"pair_kernel<{name}>", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": None,
+                    "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(name),
                     "flops_per_pair": f_pair(k), "avg_launch_ms": avg * 1e3,
                     "share_of_step": d["ms"] / (t_local * 1e3)}
         # accuracy vs the FP64 oracle on sampled rows (outside the timed region)

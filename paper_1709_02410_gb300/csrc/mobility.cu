@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(BT) pair_kernel(const R* __restrict__ rec, int
         const bool ok = mbar_wait_bounded(&bar[s], par);
         if (ok) {
             const R* st = stage + (size_t)s * TS * LEN;
-#pragma unroll 1
+#pragma unroll(K <= 4 ? 2 : 1)
             for (int jj = 0; jj < TS; ++jj) {
                 const R* rj = st + jj * LEN;
                 R dx, dy, zj;
@@ -248,10 +248,11 @@ __global__ void __launch_bounds__(BT) pair_kernel(const R* __restrict__ rec, int
                 pair_block<R, R, WALL>(dx, dy, dz, zi, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
 #pragma unroll
                 for (int m = 0; m < K; ++m) {
+                    // three FMA chains: 9 FMA per right-hand side
                     const R fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
-                    acc[3 * m + 0] += Mxx * fx + Mxy * fy + Mxz * fz;
-                    acc[3 * m + 1] += Mxy * fx + Myy * fy + Myz * fz;
-                    acc[3 * m + 2] += Mzx * fx + Mzy * fy + Mzz * fz;
+                    acc[3 * m + 0] = fma(Mxz, fz, fma(Mxy, fy, fma(Mxx, fx, acc[3 * m + 0])));
+                    acc[3 * m + 1] = fma(Myz, fz, fma(Myy, fy, fma(Mxy, fx, acc[3 * m + 1])));
+                    acc[3 * m + 2] = fma(Mzz, fz, fma(Mzy, fy, fma(Mzx, fx, acc[3 * m + 2])));
                 }
             }
         }

@@ -75,16 +75,20 @@ __device__ __forceinline__ void pair_block(T dx, T dy, T dz, T zi, T zj, const P
     T rinv = rsqrt_(r2);
     T rinv2 = rinv * rinv;
     // far branch
-    T c1f = rinv * (K(1) + c.a23 * rinv2);
-    T c2f = rinv * rinv2 * (K(1) - c.two_a2 * rinv2);
-    // overlap branch
-    T rr = r2 * rinv;
-    T c1o = c.k_self - c.k_ovl * rr;
-    T c2o = rinv * c.inv8a2;
-    const bool far = val_(r2) >= val_(c.four_a2);
-    const bool self = !(val_(r2) > K(0));
-    T c1 = far ? c1f : (self ? T(c.k_self) : c1o);
-    T c2 = far ? c2f : (self ? T(K(0)) : c2o);
+    T c1 = rinv * (K(1) + c.a23 * rinv2);
+    T c2 = rinv * rinv2 * (K(1) - c.two_a2 * rinv2);
+    // overlapping pair (r < 2a) or self block (r = 0): rare, so a branch
+    // rather than selects on every pair
+    if (val_(r2) < val_(c.four_a2)) {
+        if (val_(r2) > K(0)) {
+            T rr = r2 * rinv;
+            c1 = c.k_self - c.k_ovl * rr;
+            c2 = rinv * c.inv8a2;
+        } else {
+            c1 = T(c.k_self);
+            c2 = T(K(0));
+        }
+    }
     if (!WALL) {
         T g = c2 * dz;
         Mxx = c1 + c2 * dx * dx;
