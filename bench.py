@@ -267,6 +267,8 @@ def run_ours(args, rank, world, local):
     extra["speedup_f32_k16_vs_f64_k1_per_rhs"] = (t64 * K_RHS) / t16
     extra["speedup_f32_k1_vs_f64_k1"] = t64 / t32k1
 
+    batched = measure_batched(h.lib, dev, T) if rank == 0 else None
+
     out = None
     if rank == 0:
         # dominant pair-kernel variant of the step -> roofline
@@ -327,10 +329,76 @@ def run_ours(args, rank, world, local):
             "pair_kernels_in_step": prof,
             "solver_iterations_per_step": iters,
             "matvec": extra,
+            "batched_c4": batched,
             "accuracy": acc,
             "wall_s_timed": wall,
         }
     return out
+
+
+# ---------------------------------------------------------------------------
+# uneven batch: 64 boomerang suspensions, body counts log-uniform in [32, 1500]
+
+def measure_batched(lib, dev, T, tol=1e-4, max_iter=60):
+    import torch
+    import paper_1709_02410_gb300 as P
+    from paper_1709_02410_gb300 import synth
+    systems = synth.c4_uneven_batch()
+    a = systems[0].a
+    hb = P.Handle(synth.ETA, a, synth.KT)
+    shape = T(systems[0].shape)
+    q = T(np.concatenate([s.q for s in systems]))
+    th = T(np.concatenate([s.theta for s in systems]))
+    r = hb.blobs_from_bodies(shape, q, th)
+    counts = [s.n for s in systems]
+    off = np.concatenate([[0], np.cumsum(counts)]).astype(np.int64)
+    n = int(off[-1])
+    W = T(synth.gaussian(300, (3, n)))
+    F = T(synth.gaussian(301, (3, n)))
+    hb.precond_build(15, r, q)
+    variant, tune_ms = hb.autotune_batched(off, r, 1)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    out, U, iters = hb.lanczos_sqrt_apply_batched(off, r, W, tol, max_iter, use_graph=True, F=F)  # capture
+    reps = 3
+    torch.cuda.synchronize()
+    ev0.record()
+    for _ in range(reps):
+        out, U, iters = hb.lanczos_sqrt_apply_batched(off, r, W, tol, max_iter, use_graph=True, F=F, out=out, U=U)
+    ev1.record()
+    torch.cuda.synchronize()
+    t_graph = ev0.elapsed_time(ev1) / 1e3 / reps
+    # per-system loop of plain launches: one handle per system, its own
+    # preconditioner built beforehand, host-driven Lanczos + one matvec
+    hs, rs, Ws, Fs = [], [], [], []
+    for si, s in enumerate(systems):
+        hi = P.Handle(synth.ETA, a, synth.KT)
+        ri = r[:, off[si]:off[si + 1]].contiguous()
+        hi.precond_build(15, ri, q[sum(c // 15 for c in counts[:si]):sum(c // 15 for c in counts[:si + 1])].contiguous())
+        hs.append(hi)
+        rs.append(ri)
+        Ws.append(W[:, off[si]:off[si + 1]].contiguous())
+        Fs.append(F[:, off[si]:off[si + 1]].contiguous())
+    def loop():
+        it = []
+        for hi, ri, wi, fi in zip(hs, rs, Ws, Fs):
+            _, st = hi.lanczos_sqrt_apply(ri, wi, tol, max_iter, dtype=P.F32)
+            hi.mobility_apply(ri, fi, dtype=P.F32)
+            it.append(st["iterations"])
+        return it
+    loop()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    it_loop = loop()
+    torch.cuda.synchronize()
+    t_loop = time.perf_counter() - t0
+    pairs = float(sum(c * c for c in counts))
+    mv = sum(iters) and (max(iters) + 1)
+    return {"n_sys": len(systems), "blobs": n, "pairs_per_matvec": pairs, "autotuned_variant": variant,
+            "autotune_ms_per_launch": tune_ms, "graph_s": t_graph, "loop_s": t_loop,
+            "speedup_graph_vs_loop": t_loop / t_graph, "lanczos_iters_min_max": [min(iters), max(iters)],
+            "loop_iters_min_max": [min(it_loop), max(it_loop)],
+            "pairs_per_s_graph": pairs * (sum(iters) / len(iters) + 1) / t_graph,
+            "tol": tol, "dtype": "f32 pairs, f64 vectors"}
 
 
 # ---------------------------------------------------------------------------

@@ -206,6 +206,41 @@ int rpbd_gmres_rigid_solve(rpbd_handle* h, int64_t nb, int nper, const double* r
 int rpbd_rfd_drift(rpbd_handle* h, int64_t n, const double* r, const double* W, double delta,
                    double* drift, int dtype, void* stream);
 
+/* ---- many independent suspensions (batched; the paper's per-suspension
+ *      matvec and Lanczos of Sec. 2.1-2.2 applied to a batch) --------------- */
+
+/* System s owns blobs [offsets[s], offsets[s+1]) of the concatenated SoA
+ * arrays r [3][N], F, U [k][3][N] (N = offsets[n_sys]); blobs interact only
+ * inside their system.  offsets is a HOST array of n_sys + 1 int64 starting
+ * at 0.  FP32 pair arithmetic, FP32 F and U, 1 <= k <= 16 (k in {1, 4, 16}
+ * hit specialised kernels, other k run as the next larger one).  One
+ * persistent launch over a work list of (system, target tile, source chunk)
+ * items with the tile shape chosen by rpbd_autotune_batched (default:
+ * 128 targets x 64 sources).  The work list is cached per offsets. */
+int rpbd_mobility_apply_batched(rpbd_handle* h, int n_sys, const int64_t* offsets, const double* r,
+                                const float* F, float* U, int k, void* stream);
+
+/* Times every compiled tile variant of the batched kernel on this batch (k
+ * right-hand sides, zero forces), keeps the fastest in the handle and
+ * returns its index (>= 0) or a negative status.  *best_ms (host, may be
+ * NULL) receives its time per launch.  Synchronises the stream. */
+int rpbd_autotune_batched(rpbd_handle* h, int n_sys, const int64_t* offsets, const double* r, int k,
+                          double* best_ms, void* stream);
+
+/* Preconditioned (use_precond != 0: the block preconditioner built on all N
+ * blobs) Lanczos M^{1/2} W of every system at once, FP32 pairs, FP64 vectors
+ * and tridiagonal square root, per-system stop test as in
+ * rpbd_lanczos_sqrt_apply; optionally also U = M F per system (F, U FP64
+ * [3][N], both NULL to skip).  use_graph != 0 captures the whole sequence
+ * (max_iter iterations, converged systems masked off on the device) into a
+ * CUDA graph on first use and replays it: one launch per call.  iters (host,
+ * n_sys ints, may be NULL) receives each system's Lanczos iterations; then
+ * the call synchronises the stream.  1 <= max_iter <= 64. */
+int rpbd_lanczos_sqrt_apply_batched(rpbd_handle* h, int n_sys, const int64_t* offsets,
+                                    const double* r, const double* W, double* out, const double* F,
+                                    double* U, double tol, int max_iter, int use_precond,
+                                    int use_graph, int* iters, void* stream);
+
 /* ---- random numbers ---------------------------------------------------- */
 
 /* out[e] for e < n: standard normals from Philox4x32-10 (Salmon et al.,

@@ -61,6 +61,9 @@ SIGNATURES = [
     ("rpbd_step_emt", _I, [_P, _I64, _I, _P, _P, _P, C.POINTER(Forces), C.POINTER(StepParams),
                            C.POINTER(Stats), _P]),
     ("rpbd_blob_forces", _I, [_P, _I64, _P, C.POINTER(Forces), _P, _P]),
+    ("rpbd_mobility_apply_batched", _I, [_P, _I, _P, _P, _P, _P, _I, _P]),
+    ("rpbd_autotune_batched", _I, [_P, _I, _P, _P, _I, C.POINTER(C.c_double), _P]),
+    ("rpbd_lanczos_sqrt_apply_batched", _I, [_P, _I, _P, _P, _P, _P, _P, _P, _D, _I, _I, _I, _P, _P]),
     ("rpbd_mobility_apply_f32_noalloc", _I, [C.POINTER(Params), _I64, _P, _P, _P, _I, _P]),
     ("rpbd_launch_count", C.c_longlong, []),
     ("rpbd_profile_enable", _I, [_P, _I]),

@@ -170,6 +170,45 @@ class Handle:
                     "rfd_drift")
         return out
 
+    # ---- batched suspensions
+    @staticmethod
+    def _offsets(offsets):
+        import numpy as np
+        off = np.ascontiguousarray(offsets, dtype=np.int64)
+        return off, off.ctypes.data_as(C.c_void_p)
+
+    def mobility_apply_batched(self, offsets, r, F, out=None):
+        off, op = self._offsets(offsets)
+        n_sys = off.size - 1
+        k = 1 if F.dim() == 2 else F.shape[0]
+        _need(F, torch.float32, name="F")
+        out = torch.empty_like(F) if out is None else out
+        self._check(self.lib.rpbd_mobility_apply_batched(self.h, n_sys, op, _ptr(r), _ptr(F), _ptr(out), k,
+                                                         _stream()), "mobility_apply_batched")
+        return out
+
+    def autotune_batched(self, offsets, r, k=1):
+        off, op = self._offsets(offsets)
+        ms = C.c_double()
+        v = self.lib.rpbd_autotune_batched(self.h, off.size - 1, op, _ptr(r), k, C.byref(ms), _stream())
+        if v < 0:
+            self._check(v, "autotune_batched")
+        return v, ms.value
+
+    def lanczos_sqrt_apply_batched(self, offsets, r, W, tol, max_iter=40, use_precond=True, use_graph=True,
+                                   F=None, out=None, U=None):
+        off, op = self._offsets(offsets)
+        n_sys = off.size - 1
+        out = torch.empty_like(W) if out is None else out
+        if F is not None and U is None:
+            U = torch.empty_like(F)
+        iters = (C.c_int * n_sys)()
+        self._check(self.lib.rpbd_lanczos_sqrt_apply_batched(self.h, n_sys, op, _ptr(r), _ptr(W), _ptr(out), _ptr(F),
+                                                             _ptr(U), tol, max_iter, int(bool(use_precond)),
+                                                             int(bool(use_graph)), iters, _stream()),
+                    "lanczos_sqrt_apply_batched")
+        return out, U, list(iters)
+
     # ---- random numbers
     def philox_normals(self, n, seed, step, sid, device="cuda"):
         out = torch.empty(n, dtype=torch.float64, device=device)

@@ -126,6 +126,8 @@ int rpbd_destroy(rpbd_handle* h)
         cudaEventDestroy(r.b);
     }
     for (auto e : h->ev_pool) cudaEventDestroy(e);
+    batched_free_graphs(h);
+    batched_free_plans(h);
     for (int b = 0; b < BUF_COUNT; ++b)
         if (h->buf[b]) cudaFree(h->buf[b]);
     if (h->dev_flag) cudaFree(h->dev_flag);

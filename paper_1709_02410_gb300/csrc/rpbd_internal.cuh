@@ -58,8 +58,17 @@ enum Buf {
     BUF_STEP,        // time-step vectors
     BUF_R2,          // displaced positions (RFD, predictor)
     BUF_AUX,         // misc
+    BUF_BPACK,       // batched: packed records of all systems
+    BUF_BSCALE,      // batched: overlap scales
+    BUF_BPARTIAL,    // batched: chunk partials
+    BUF_BAUX,        // batched: autotune vectors
+    BUF_BLZ,         // batched Lanczos: basis and vectors
+    BUF_BLZ_SMALL,   // batched Lanczos: per-system scalars
     BUF_COUNT
 };
+
+struct BatchPlan;
+struct BatchGraph;
 
 struct ProfRec {
     cudaEvent_t a, b;
@@ -90,6 +99,10 @@ struct rpbd_handle {
     bool profile = false;
     std::vector<rpbd::ProfRec> prof;
     std::vector<cudaEvent_t> ev_pool;
+    // batched launches: cached work lists, chosen tile variant, captured graphs
+    std::vector<rpbd::BatchPlan*> bplans;
+    int batch_variant = -1;
+    std::vector<rpbd::BatchGraph*> bgraphs;
 };
 
 namespace rpbd {
@@ -150,5 +163,11 @@ int gmres_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const doub
                cudaStream_t st);
 int precond_build_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q,
                        cudaStream_t st);
+
+// batched systems (concatenated SoA; host offsets)
+int batched_apply_impl(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, const void* F, void* U,
+                       int k, bool io_double, const int* active, cudaStream_t st);
+void batched_free_plans(rpbd_handle* h);
+void batched_free_graphs(rpbd_handle* h);
 
 }  // namespace rpbd

@@ -1,0 +1,76 @@
+"""GPU parity of the batched path (many uneven suspensions in one launch)
+against the oracle per system, the autotuner, and the graph-captured batched
+Lanczos against the oracle's Lanczos per system."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import krylov, mobility as om, precond, rigid
+from paper_1709_02410_gb300 import synth
+
+from gpu_util import DEV, handle_for, oracle_params, rel2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+def batch(counts, seed=0, box_per_body=2.5):
+    systems = [synth.boomerang_suspension(c, max(4.0, np.sqrt(c) * box_per_body), seed * 100 + i)
+               for i, c in enumerate(counts)]
+    rs = [rigid.blob_positions(s.q, s.theta, s.shape) for s in systems]
+    off = np.concatenate([[0], np.cumsum([r.shape[1] for r in rs])]).astype(np.int64)
+    r = np.concatenate(rs, axis=1)
+    return systems, rs, off, r
+
+
+@pytest.mark.parametrize("k", [1, 3, 16])
+def test_batched_matvec_matches_oracle_per_system(k):
+    systems, rs, off, r = batch([1, 2, 9, 40, 3])
+    h = handle_for(systems[0])
+    F = synth.gaussian(5 + k, (k, 3, r.shape[1]), np.float32)
+    U = h.mobility_apply_batched(off, to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    for s, (sy, rr) in enumerate(zip(systems, rs)):
+        sl = slice(off[s], off[s + 1])
+        ref = om.apply(rr, F[:, :, sl].astype(np.float64), oracle_params(sy))
+        assert rel2(U[:, :, sl], ref) <= 1e-5
+
+
+def test_autotune_and_variants_agree():
+    systems, rs, off, r = batch([30, 7, 64, 100, 12], seed=1)
+    h = handle_for(systems[0])
+    rd = to_dev(r)
+    F = to_dev(synth.gaussian(9, (1, 3, r.shape[1]), np.float32), torch.float32)
+    U0 = h.mobility_apply_batched(off, rd, F).cpu().numpy()
+    v, ms = h.autotune_batched(off, rd, 1)
+    assert 0 <= v < 3 and ms > 0
+    U1 = h.mobility_apply_batched(off, rd, F).cpu().numpy()
+    assert rel2(U1, U0) <= 1e-6
+
+
+@pytest.mark.parametrize("use_graph", [False, True])
+def test_batched_lanczos_matches_oracle(use_graph):
+    counts = [3, 11, 25, 6]
+    systems, rs, off, r = batch(counts, seed=2)
+    h = handle_for(systems[0])
+    rd = to_dev(r)
+    # block preconditioner over all bodies of the batch (bodies never couple systems)
+    q = np.concatenate([s.q for s in systems])
+    h.precond_build(15, rd, to_dev(q))
+    W = synth.gaussian(11, (3, r.shape[1]))
+    F = synth.gaussian(12, (3, r.shape[1]))
+    out, U, iters = h.lanczos_sqrt_apply_batched(off, rd, to_dev(W), tol=1e-5, max_iter=60, use_graph=use_graph,
+                                                 F=to_dev(F))
+    if use_graph:      # replay the captured graph on new inputs
+        W = synth.gaussian(13, (3, r.shape[1]))
+        out, U, iters = h.lanczos_sqrt_apply_batched(off, rd, to_dev(W), tol=1e-5, max_iter=60, use_graph=True,
+                                                     F=to_dev(F))
+    out, U = out.cpu().numpy(), U.cpu().numpy()
+    for s, (sy, rr) in enumerate(zip(systems, rs)):
+        sl = slice(off[s], off[s + 1])
+        prm = oracle_params(sy)
+        pc = precond.BlockPrecond(rr, sy.q, sy.nper, prm)
+        G = lambda v: pc.Linv_apply(om.apply(rr, pc.LinvT_apply(v), prm))
+        y, it, ch = krylov.lanczos_sqrt(G, W[:, sl], 1e-5, 60)
+        ref = pc.L_apply(y)
+        assert abs(iters[s] - it) <= 1
+        assert rel2(out[:, sl], ref) <= 1e-4
+        assert rel2(U[:, sl], om.apply(rr, F[:, sl], prm)) <= 1e-5
