@@ -37,11 +37,13 @@ F_GEOM = 116                 # algorithmic flops of one pair block (FMA = 2), se
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/pair_kernel_f32_k*_boomerangs_65535.md); None when not captured
-NCU_TRAFFIC = {"f32_k1": 2106368, "f32_k16": 20269312 + 342761728}
+NCU_TRAFFIC = {"f32_k16": 20269312 + 342761728, "f32sym_k1": 2672640 + 154834944}
 
 
-def f_pair(k):
-    return F_GEOM + 18 * k
+def f_pair(k, symmetric=False):
+    """Algorithmic flops per ordered pair: one block (F_GEOM) and 9 FMA per
+    right-hand side; the symmetric kernel forms one block per unordered pair."""
+    return (F_GEOM / 2 if symmetric else F_GEOM) + 18 * k
 
 
 def parse():
@@ -173,7 +175,7 @@ def run_ours(args, rank, world, local):
     t_local = sum(ms_steps) / 1e3
     # per-variant pair-kernel time from the library's own events
     prof = {}
-    for dt, name in ((1, "f32"), (0, "f64")):
+    for dt, name in ((1, "f32"), (0, "f64"), (3, "f32sym")):
         for k in (1, 2, 4, 8, 16):
             ms, nl, pr = C.c_double(), C.c_longlong(), C.c_double()
             lib.rpbd_profile_read(h.h, dt, k, C.byref(ms), C.byref(nl), C.byref(pr), 0)
@@ -218,7 +220,7 @@ def run_ours(args, rank, world, local):
     e2e_t = time.perf_counter() - e0
     lib.rpbd_profile_enable(h.h, 0)
     e2e_pairs = 0.0
-    for dt in (1, 0):
+    for dt in (1, 0, 3):
         for k in (1, 2, 4, 8, 16):
             ms, nl, pr = C.c_double(), C.c_longlong(), C.c_double()
             lib.rpbd_profile_read(h.h, dt, k, C.byref(ms), C.byref(nl), C.byref(pr), 0)
@@ -262,7 +264,13 @@ def run_ours(args, rank, world, local):
     t32k1 = time_launch(lambda: h.mobility_apply(r, F1f, out=U1f), 3)
     extra["f32_k16"] = dict(s_per_launch=t16, pairs_per_s=N * N / t16, matvecs_per_s=K_RHS / t16,
                             tflops=N * N * f_pair(16) / t16 / 1e12)
-    extra["f32_k1"] = dict(s_per_launch=t32k1, pairs_per_s=N * N / t32k1, tflops=N * N * f_pair(1) / t32k1 / 1e12)
+    extra["f32_k1_symmetric"] = dict(s_per_launch=t32k1, pairs_per_s=N * N / t32k1,
+                                     tflops=N * N * f_pair(1, True) / t32k1 / 1e12)
+    h.set_symmetric(False)
+    t32k1d = time_launch(lambda: h.mobility_apply(r, F1f, out=U1f), 3)
+    h.set_symmetric(True)
+    extra["f32_k1_one_direction"] = dict(s_per_launch=t32k1d, pairs_per_s=N * N / t32k1d,
+                                         tflops=N * N * f_pair(1) / t32k1d / 1e12)
     extra["f64_k1"] = dict(s_per_launch=t64, pairs_per_s=N * N / t64)
     extra["speedup_f32_k16_vs_f64_k1_per_rhs"] = (t64 * K_RHS) / t16
     extra["speedup_f32_k1_vs_f64_k1"] = t64 / t32k1
@@ -277,12 +285,13 @@ def run_ours(args, rank, world, local):
         if dom:
             name, d = dom
             k = int(name.split("_k")[1])
+            sym = name.startswith("f32sym")
             avg = d["ms"] / d["launches"] / 1e3
-            flops = d["pairs"] / d["launches"] * f_pair(k)
+            flops = d["pairs"] / d["launches"] * f_pair(k, sym)
             ach = flops / avg / 1e12
             roof = {"bound": "alu", "kernel": f"pair_kernel<{name}>", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(name),
-                    "flops_per_pair": f_pair(k), "avg_launch_ms": avg * 1e3,
+                    "flops_per_pair": f_pair(k, sym), "avg_launch_ms": avg * 1e3,
                     "share_of_step": d["ms"] / (t_local * 1e3)}
         # accuracy vs the FP64 oracle on sampled rows (outside the timed region)
         acc = {}

@@ -268,6 +268,14 @@ int rpbd_step_emt(rpbd_handle* h, int64_t nb, int nper, const double* shape, dou
 int rpbd_blob_forces(rpbd_handle* h, int64_t n, const double* r, const rpbd_forces* forces,
                      double* f, void* stream);
 
+/* ---- options -------------------------------------------------------------- */
+
+/* value != 0 (default): FP32 matvecs with k <= 4 use the symmetric kernel,
+ * which forms each unordered pair's block once and applies it both ways
+ * (M_ji = M_ij^T, Sec. 2.1); 0: the one-direction kernel for every k. */
+#define RPBD_OPT_SYMMETRIC 1
+int rpbd_set_option(rpbd_handle* h, int option, int value);
+
 /* ---- instrumentation ----------------------------------------------------- */
 
 /* Number of kernels this library has launched since it was loaded. */
@@ -275,8 +283,9 @@ long long rpbd_launch_count(void);
 /* on != 0: bracket every pair-kernel launch of h with CUDA events on its
  * stream (used to time the kernel inside a larger step). */
 int rpbd_profile_enable(rpbd_handle* h, int on);
-/* Sum of the recorded pair-kernel durations for (dtype, k-variant), their
- * launch count and pairs (n^2 per launch); synchronises the device.  reset
+/* Sum of the recorded pair-kernel durations for (kind, k-variant), their
+ * launch count and pairs (n^2 per launch); kind: RPBD_F64, RPBD_F32 (one-direction
+ * kernel), 2 (batched FP32), 3 (symmetric FP32).  Synchronises the device.  reset
  * != 0 drops every record afterwards. */
 int rpbd_profile_read(rpbd_handle* h, int dtype, int k, double* ms, long long* launches, double* pairs,
                       int reset);

@@ -66,6 +66,10 @@ class Handle:
             raise RpbdError(f"{what}: {_native.STATUS.get(st, st)}: {msg}")
         return st
 
+    def set_symmetric(self, on: bool):
+        """FP32 matvecs with k <= 4: symmetric kernel (default) or one-direction."""
+        self._check(self.lib.rpbd_set_option(self.h, 1, int(bool(on))), "set_option")
+
     # ---- a1
     def blobs_from_bodies(self, shape, q, theta, out=None):
         nb, nper = q.shape[0], shape.shape[0]

@@ -154,6 +154,15 @@ int rpbd_reserve(rpbd_handle* h, int64_t n, int64_t nb, int nper, int k, int bas
 
 long long rpbd_launch_count(void) { return g_launches.load(); }
 
+int rpbd_set_option(rpbd_handle* h, int option, int value)
+{
+    if (!h) return RPBD_BAD_ARG;
+    switch (option) {
+    case RPBD_OPT_SYMMETRIC: h->use_sym = value != 0; return RPBD_OK;
+    default: return set_error(h, RPBD_BAD_ARG, "unknown option");
+    }
+}
+
 int rpbd_profile_enable(rpbd_handle* h, int on)
 {
     if (!h) return RPBD_BAD_ARG;

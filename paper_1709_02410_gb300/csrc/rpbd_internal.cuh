@@ -64,6 +64,7 @@ enum Buf {
     BUF_BAUX,        // batched: autotune vectors
     BUF_BLZ,         // batched Lanczos: basis and vectors
     BUF_BLZ_SMALL,   // batched Lanczos: per-system scalars
+    BUF_SYM_ITEMS,   // symmetric kernel: work items
     BUF_COUNT
 };
 
@@ -103,6 +104,10 @@ struct rpbd_handle {
     std::vector<rpbd::BatchPlan*> bplans;
     int batch_variant = -1;
     std::vector<rpbd::BatchGraph*> bgraphs;
+    // symmetric FP32 kernel (k <= 4): on by default, work list cached per n
+    int use_sym = 1;
+    int64_t sym_plan_n = -1;
+    int sym_n_items = 0, sym_n_home = 0, sym_max_slots = 0;
 };
 
 namespace rpbd {
@@ -163,6 +168,10 @@ int gmres_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const doub
                cudaStream_t st);
 int precond_build_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q,
                        cudaStream_t st);
+
+// symmetric FP32 matvec, k <= 4
+int sym_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* F, void* U, int k, bool io_double,
+                   cudaStream_t st);
 
 // batched systems (concatenated SoA; host offsets)
 int batched_apply_impl(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, const void* F, void* U,

@@ -112,3 +112,20 @@ def test_f64_full_size_row_sampled():
     rows = np.random.default_rng(43).choice(s.n, 64, replace=False)
     Uo = om.apply(r, F, oracle_params(s), rows=rows)
     assert rel2(U[:, rows], Uo) <= 1e-12
+
+
+@pytest.mark.parametrize("k", [1, 2, 4])
+@pytest.mark.parametrize("n", [5, 129, 1000])
+def test_f32_symmetric_and_one_direction_agree(k, n):
+    """the symmetric kernel (default for k <= 4) and the one-direction kernel"""
+    rng = np.random.default_rng(7 * n + k)
+    box = max(2.0, np.sqrt(n))
+    r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
+    F = rng.standard_normal((k, 3, n)).astype(np.float32)
+    s = synth.c0_boomerangs_1920()
+    h = handle_for(s)
+    U1 = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    h.set_symmetric(False)
+    U2 = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
+    assert rel2(U1, Uo) <= 1e-5 and rel2(U2, Uo) <= 1e-5
