@@ -53,6 +53,7 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle accuracy / CPU legs")
+    ap.add_argument("--no-rollers", action="store_true", help="skip the 196,608-blob roller T-S step")
     return ap.parse_args()
 
 
@@ -108,6 +109,21 @@ class Clocks:
 
 
 # ---------------------------------------------------------------------------
+# replicas: whole-job throughput = pairs summed over ranks / slowest rank's time
+
+def aggregate(t_local, work_local, world, dev):
+    if world <= 1:
+        return t_local, work_local
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    ww = torch.tensor([work_local], device=dev, dtype=torch.float64)
+    dist.all_reduce(ww, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(ww.item())
+
+
+# ---------------------------------------------------------------------------
 # our arm
 
 def run_ours(args, rank, world, local):
@@ -131,7 +147,7 @@ def run_ours(args, rank, world, local):
     Lp = 14 * 1.05 * s.a          # arm length: 7 spacings of 2.1 a
 
     def sp(i):
-        return StepParams(0.01, 1e-3, Lp, 1e-6, 1e-4, 200, 50, 80, P.F32, 2024 + rank, i)
+        return StepParams(0.01, 1e-3, Lp, 1e-6, 1e-4, 300, 100, 80, P.F32, 2024 + rank, i)
 
     stats_log = []
 
@@ -184,14 +200,7 @@ def run_ours(args, rank, world, local):
     pairs_local = sum(v["pairs"] for v in prof.values())
 
     # whole job: max time over ranks, pairs summed over ranks
-    t_max, pairs_total = t_local, pairs_local
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([t_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        pp = torch.tensor([pairs_local], device=dev, dtype=torch.float64)
-        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
-        t_max, pairs_total = float(tt.item()), float(pp.item())
+    t_max, pairs_total = aggregate(t_local, pairs_local, world, dev)
     value = pairs_total / t_max
 
     timed_stats = list(stats_log)
@@ -228,13 +237,7 @@ def run_ours(args, rank, world, local):
     lib.rpbd_profile_read(h.h, 1, 1, C.byref(C.c_double()), C.byref(C.c_longlong()), C.byref(C.c_double()), 1)
     h2d = q0.numel() * 8 + th0.numel() * 8 + F16.numel() * 4
     d2h = h2d
-    if world > 1:
-        import torch.distributed as dist
-        tt = torch.tensor([e2e_t], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        pp = torch.tensor([e2e_pairs], device=dev, dtype=torch.float64)
-        dist.all_reduce(pp, op=dist.ReduceOp.SUM)
-        e2e_t, e2e_pairs = float(tt.item()), float(pp.item())
+    e2e_t, e2e_pairs = aggregate(e2e_t, e2e_pairs, world, dev)
 
     # ---- separate measurements (outside the timed steps): k = 16 FP32 batch and
     # the plain FP64 single-RHS kernel, each alone, and their accuracy
@@ -276,6 +279,7 @@ def run_ours(args, rank, world, local):
     extra["speedup_f32_k1_vs_f64_k1"] = t64 / t32k1
 
     batched = measure_batched(h.lib, dev, T) if rank == 0 else None
+    rollers = measure_rollers(dev, T) if (rank == 0 and not args.no_rollers) else None
 
     out = None
     if rank == 0:
@@ -326,7 +330,8 @@ def run_ours(args, rank, world, local):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded boomerang suspension, forces N(0,1))",
             "config": {"workload": "boomerangs_65535: 4369 L-bodies x 15 blobs, T-S step + k=16 FP32 batch",
-                       "n_blobs": N, "n_bodies": NB, "k_rhs": K_RHS, "gmres_tol": 1e-6, "lanczos_tol": 1e-4,
+                       "n_blobs": N, "n_bodies": NB, "k_rhs": K_RHS, "gmres_tol": 1e-6, "gmres_restart": 100,
+                       "lanczos_tol": 1e-4,
                        "rfd_delta": 1e-3, "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "steps_per_s": args.steps / t_max * world,
@@ -339,10 +344,43 @@ def run_ours(args, rank, world, local):
             "solver_iterations_per_step": iters,
             "matvec": extra,
             "batched_c4": batched,
+            "ts_step_rollers_c3": rollers,
             "accuracy": acc,
             "wall_s_timed": wall,
         }
     return out
+
+
+# ---------------------------------------------------------------------------
+# full T-S step on the dense microroller suspension: 16,384 rollers x 12 blobs
+
+def measure_rollers(dev, T, steps=1):
+    import torch
+    import paper_1709_02410_gb300 as P
+    from paper_1709_02410_gb300 import synth
+    from paper_1709_02410_gb300._native import Forces, StepParams
+    s = synth.c3_rollers_196608()
+    h = P.Handle(synth.ETA, s.a, synth.KT)
+    shape, q, th = T(s.shape), T(s.q), T(s.theta)
+    # buoyant weight m_e g = 1.24e-14 N = 1.24e-2 mg um/s^2 per roller, shared by its 12 blobs;
+    # constant torque 1.0 about +y on every roller; blob-wall Yukawa as for the boomerangs
+    forces = Forces(1.24e-2 / 12, 0.096, 0.162, 0.1, (0.0, 1.0, 0.0))
+    sp = lambda i: StepParams(0.008, 1e-3, synth.RH_ROLLER, 1e-6, 1e-4, 300, 100, 80, P.F32, 77, i)
+    h.step_ts(shape, q, th, forces, sp(0))          # warm-up: workspace, plans
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    its = []
+    ev0.record()
+    for i in range(steps):
+        st, status = h.step_ts(shape, q, th, forces, sp(1 + i))
+        its.append([x["iterations"] for x in st])
+    ev1.record()
+    torch.cuda.synchronize()
+    t = ev0.elapsed_time(ev1) / 1e3 / steps
+    mv = [it[0] + it[1] + it[2] + it[3] + 2 for it in its]
+    return {"workload": "rollers_196608: 16384 x 12-blob rollers, phi = 0.4", "n_blobs": s.n, "s_per_step": t,
+            "steps_per_s": 1.0 / t, "iterations_rfd_lanczos_pred_corr": its, "matvecs_per_step": mv,
+            "gmres_tol": 1e-6, "lanczos_tol": 1e-4, "dt": 0.008, "dtype": "f32 pairs, f64 Krylov"}
 
 
 # ---------------------------------------------------------------------------

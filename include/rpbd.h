@@ -152,6 +152,11 @@ int rpbd_mobility_apply_f32_noalloc(const rpbd_params* p, int64_t n, const doubl
 int rpbd_mobility_adjoint(rpbd_handle* h, int64_t n, const double* r, const double* u,
                           const double* F, double* grad, void* stream);
 
+/* Same gradient with the pair block and its derivative evaluated in FP32
+ * (position differences formed in FP64 first; sums in FP64). */
+int rpbd_mobility_adjoint_f32(rpbd_handle* h, int64_t n, const double* r, const double* u,
+                              const double* F, double* grad, void* stream);
+
 /* div[3][n] = sum_j d_{r_j} . M_ij (the quantity the RFD of Sec. 3 estimates
  * with B = M), FP64. */
 int rpbd_mobility_divergence(rpbd_handle* h, int64_t n, const double* r, double* div,

@@ -101,11 +101,12 @@ class Handle:
         return out
 
     # ---- a7
-    def mobility_adjoint(self, r, u, F, out=None):
+    def mobility_adjoint(self, r, u, F, out=None, dtype=F64):
+        """d(u^T M(r) F)/dr, FP64 vectors; dtype F32 evaluates the pair derivative in FP32."""
         n = r.shape[1]
         out = torch.empty((3, n), dtype=torch.float64, device=r.device) if out is None else out
-        self._check(self.lib.rpbd_mobility_adjoint(self.h, n, _ptr(r), _ptr(u), _ptr(F), _ptr(out), _stream()),
-                    "mobility_adjoint")
+        fn = self.lib.rpbd_mobility_adjoint_f32 if dtype == F32 else self.lib.rpbd_mobility_adjoint
+        self._check(fn(self.h, n, _ptr(r), _ptr(u), _ptr(F), _ptr(out), _stream()), "mobility_adjoint")
         return out
 
     def mobility_divergence(self, r, out=None):

@@ -1,4 +1,4 @@
-// Derivatives of the wall-RPY mobility (FP64):
+// Derivatives of the wall-RPY mobility (FP64; the adjoint also in FP32):
 //
 //  adjoint:    g_k = d(u^T M(r) F)/d r_k  (derivative of the matvec of
 //              Sec. 2.1 with respect to blob positions)
@@ -22,7 +22,6 @@
 
 namespace rpbd {
 
-using D3 = Dual<3>;
 
 struct RegBlob {
     double x, y, zt, s, dzt, ds;
@@ -47,30 +46,33 @@ __device__ __forceinline__ RegBlob reg_blob(const double* r, int64_t n, int64_t 
 }
 
 // block of target t (dual: partials w.r.t. t's regularised coordinates) and
-// source s; out[9] row-major
-template <bool WALL>
-__device__ __forceinline__ void dual_block(const RegBlob& t, const RegBlob& s, const PairConst<double>& pc, D3 M[9])
+// source s; out[9] row-major.  Differences are taken in FP64, then the block
+// is evaluated in S (double, or float for the FP32 variant).
+template <bool WALL, class S>
+__device__ __forceinline__ void dual_block(const RegBlob& t, const RegBlob& s, const PairConst<S>& pc,
+                                           Dual<3, S> M[9])
 {
-    D3 dx(t.x - s.x), dy(t.y - s.y), dz(t.zt - s.zt), zi(t.zt), zj(s.zt);
-    dx.g[0] = 1.0;
-    dy.g[1] = 1.0;
-    dz.g[2] = 1.0;
-    zi.g[2] = 1.0;
+    using D3 = Dual<3, S>;
+    D3 dx(S(t.x - s.x)), dy(S(t.y - s.y)), dz(S(t.zt - s.zt)), zi(S(t.zt)), zj(S(s.zt));
+    dx.g[0] = S(1);
+    dy.g[1] = S(1);
+    dz.g[2] = S(1);
+    zi.g[2] = S(1);
     D3 Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz;
-    pair_block<D3, double, WALL>(dx, dy, dz, zi, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
+    pair_block<D3, S, WALL>(dx, dy, dz, zi, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
     M[0] = Mxx; M[1] = Mxy; M[2] = Mxz;
     M[3] = Mxy; M[4] = Myy; M[5] = Myz;
     M[6] = Mzx; M[7] = Mzy; M[8] = Mzz;
 }
 
-template <bool WALL>
+template <bool WALL, class S>
 __global__ void adjoint_kernel(int64_t n, const double* __restrict__ r, const double* __restrict__ u,
                                const double* __restrict__ F, double a, double s_min, double inv8pieta,
                                double* __restrict__ g)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const PairConst<double> pc = PairConst<double>::make(a);
+    const PairConst<S> pc = PairConst<S>::make(a);
     const RegBlob bk = reg_blob(r, n, k, a, WALL, s_min);
     const double uk[3] = {u[k], u[n + k], u[2 * n + k]};
     const double Fk[3] = {F[k], F[n + k], F[2 * n + k]};
@@ -79,16 +81,16 @@ __global__ void adjoint_kernel(int64_t n, const double* __restrict__ r, const do
         const RegBlob bj = reg_blob(r, n, j, a, WALL, s_min);
         const double Fj[3] = {bj.s * F[j], bj.s * F[n + j], bj.s * F[2 * n + j]};
         const double uj[3] = {bj.s * u[j], bj.s * u[n + j], bj.s * u[2 * n + j]};
-        D3 M[9];
-        dual_block<WALL>(bk, bj, pc, M);
+        Dual<3, S> M[9];
+        dual_block<WALL, S>(bk, bj, pc, M);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
             for (int d = 0; d < 3; ++d) {
                 const double w = uk[c] * Fj[d] + Fk[c] * uj[d];
-                psi += w * M[c * 3 + d].v;
+                psi += w * (double)M[c * 3 + d].v;
 #pragma unroll
-                for (int e = 0; e < 3; ++e) gr[e] += w * M[c * 3 + d].g[e];
+                for (int e = 0; e < 3; ++e) gr[e] += w * (double)M[c * 3 + d].g[e];
             }
     }
     g[k] = inv8pieta * bk.s * gr[0];
@@ -103,12 +105,12 @@ __global__ void divergence_kernel(int64_t n, const double* __restrict__ r, doubl
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const PairConst<double> pc = PairConst<double>::make(a);
-    const RegBlob bi = reg_blob(r, n, i, a, WALL, s_min);
+    const RegBlob bi = reg_blob(r, n, i, a, WALL, s_min);  // divergence: FP64 only
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t j = 0; j < n; ++j) {
-        D3 T[9];
+        Dual<3, double> T[9];
         if (j == i) {
-            dual_block<WALL>(bi, bi, pc, T);
+            dual_block<WALL, double>(bi, bi, pc, T);
 #pragma unroll
             for (int aa = 0; aa < 3; ++aa) {
                 double v = 2.0 * bi.s * bi.ds * T[aa * 3 + 2].v;
@@ -121,7 +123,7 @@ __global__ void divergence_kernel(int64_t n, const double* __restrict__ r, doubl
             }
         } else {
             const RegBlob bj = reg_blob(r, n, j, a, WALL, s_min);
-            dual_block<WALL>(bj, bi, pc, T);  // target j, source i
+            dual_block<WALL, double>(bj, bi, pc, T);  // target j, source i
 #pragma unroll
             for (int aa = 0; aa < 3; ++aa) {
                 double v = bi.s * bj.ds * T[2 * 3 + aa].v;
@@ -144,8 +146,8 @@ using namespace rpbd;
 
 extern "C" {
 
-int rpbd_mobility_adjoint(rpbd_handle* h, int64_t n, const double* r, const double* u, const double* F, double* grad,
-                          void* stream)
+static int adjoint_entry(rpbd_handle* h, int64_t n, const double* r, const double* u, const double* F, double* grad,
+                         void* stream, bool f32)
 {
     if (!h) return RPBD_BAD_ARG;
     if (n < 0 || (n > 0 && (!r || !u || !F || !grad))) return set_error(h, RPBD_BAD_ARG, "adjoint: bad arguments");
@@ -153,11 +155,29 @@ int rpbd_mobility_adjoint(rpbd_handle* h, int64_t n, const double* r, const doub
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
     const unsigned grid = (unsigned)((n + 127) / 128);
-    if (h->p.wall) adjoint_kernel<true><<<grid, 128, 0, st>>>(n, r, u, F, h->p.a, h->p.s_min, inv8pieta, grad);
-    else adjoint_kernel<false><<<grid, 128, 0, st>>>(n, r, u, F, h->p.a, h->p.s_min, inv8pieta, grad);
+    const double a = h->p.a, sm = h->p.s_min;
+    if (f32) {
+        if (h->p.wall) adjoint_kernel<true, float><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, inv8pieta, grad);
+        else adjoint_kernel<false, float><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, inv8pieta, grad);
+    } else {
+        if (h->p.wall) adjoint_kernel<true, double><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, inv8pieta, grad);
+        else adjoint_kernel<false, double><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, inv8pieta, grad);
+    }
     count_launch();
     RPBD_LAUNCH_CHECK(h);
     return RPBD_OK;
+}
+
+int rpbd_mobility_adjoint(rpbd_handle* h, int64_t n, const double* r, const double* u, const double* F, double* grad,
+                          void* stream)
+{
+    return adjoint_entry(h, n, r, u, F, grad, stream, false);
+}
+
+int rpbd_mobility_adjoint_f32(rpbd_handle* h, int64_t n, const double* r, const double* u, const double* F,
+                              double* grad, void* stream)
+{
+    return adjoint_entry(h, n, r, u, F, grad, stream, true);
 }
 
 int rpbd_mobility_divergence(rpbd_handle* h, int64_t n, const double* r, double* div, void* stream)

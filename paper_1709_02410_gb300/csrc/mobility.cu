@@ -162,7 +162,7 @@ __global__ void pack_kernel(int64_t n, int64_t n_pad, int k, const double* __res
 // 2. pair kernel
 
 template <class R, int K, int BT, int TS, int NST, bool WALL>
-__global__ void __launch_bounds__(BT) pair_kernel(const R* __restrict__ rec, int64_t n, int64_t n_pad,
+__global__ void __launch_bounds__(BT, (sizeof(R) == 4 && K == 16) ? 5 : 1) pair_kernel(const R* __restrict__ rec, int64_t n, int64_t n_pad,
                                                   int tiles_per_chunk, int n_tiles, PairConst<R> pc,
                                                   typename PartialT<R>::type* __restrict__ partial,
                                                   int* __restrict__ err_flag)

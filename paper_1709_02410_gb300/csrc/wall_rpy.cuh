@@ -137,73 +137,73 @@ __device__ __forceinline__ void pair_block(T dx, T dy, T dz, T zi, T zj, const P
     Mzz = alpha + c2 * dz * dz + b3 * Rz * Rz + (cR + dR) * Rz + E * Rinv;
 }
 
-// Forward-mode dual number with NP partials (device, FP64).
-template <int NP>
+// Forward-mode dual number with NP partials (device), scalar S (float or double).
+template <int NP, class S = double>
 struct Dual {
-    double v;
-    double g[NP];
+    S v;
+    S g[NP];
     __device__ Dual() {}
-    __device__ Dual(double x) : v(x)
+    __device__ Dual(S x) : v(x)
     {
 #pragma unroll
-        for (int q = 0; q < NP; ++q) g[q] = 0.0;
+        for (int q = 0; q < NP; ++q) g[q] = S(0);
     }
 };
-template <int NP>
-__device__ __forceinline__ double val_(const Dual<NP>& x) { return x.v; }
-template <int NP>
-__device__ __forceinline__ Dual<NP> operator+(const Dual<NP>& a, const Dual<NP>& b)
+template <int NP, class S>
+__device__ __forceinline__ S val_(const Dual<NP, S>& x) { return x.v; }
+template <int NP, class S>
+__device__ __forceinline__ Dual<NP, S> operator+(const Dual<NP, S>& a, const Dual<NP, S>& b)
 {
-    Dual<NP> r; r.v = a.v + b.v;
+    Dual<NP, S> r; r.v = a.v + b.v;
 #pragma unroll
     for (int q = 0; q < NP; ++q) r.g[q] = a.g[q] + b.g[q];
     return r;
 }
-template <int NP>
-__device__ __forceinline__ Dual<NP> operator-(const Dual<NP>& a, const Dual<NP>& b)
+template <int NP, class S>
+__device__ __forceinline__ Dual<NP, S> operator-(const Dual<NP, S>& a, const Dual<NP, S>& b)
 {
-    Dual<NP> r; r.v = a.v - b.v;
+    Dual<NP, S> r; r.v = a.v - b.v;
 #pragma unroll
     for (int q = 0; q < NP; ++q) r.g[q] = a.g[q] - b.g[q];
     return r;
 }
-template <int NP>
-__device__ __forceinline__ Dual<NP> operator*(const Dual<NP>& a, const Dual<NP>& b)
+template <int NP, class S>
+__device__ __forceinline__ Dual<NP, S> operator*(const Dual<NP, S>& a, const Dual<NP, S>& b)
 {
-    Dual<NP> r; r.v = a.v * b.v;
+    Dual<NP, S> r; r.v = a.v * b.v;
 #pragma unroll
     for (int q = 0; q < NP; ++q) r.g[q] = fma(a.g[q], b.v, a.v * b.g[q]);
     return r;
 }
-template <int NP>
-__device__ __forceinline__ Dual<NP> operator+(const Dual<NP>& a, double b) { Dual<NP> r = a; r.v += b; return r; }
-template <int NP>
-__device__ __forceinline__ Dual<NP> operator+(double b, const Dual<NP>& a) { Dual<NP> r = a; r.v += b; return r; }
-template <int NP>
-__device__ __forceinline__ Dual<NP> operator-(const Dual<NP>& a, double b) { Dual<NP> r = a; r.v -= b; return r; }
-template <int NP>
-__device__ __forceinline__ Dual<NP> operator-(double b, const Dual<NP>& a)
+template <int NP, class S>
+__device__ __forceinline__ Dual<NP, S> operator+(const Dual<NP, S>& a, S b) { Dual<NP, S> r = a; r.v += b; return r; }
+template <int NP, class S>
+__device__ __forceinline__ Dual<NP, S> operator+(S b, const Dual<NP, S>& a) { Dual<NP, S> r = a; r.v += b; return r; }
+template <int NP, class S>
+__device__ __forceinline__ Dual<NP, S> operator-(const Dual<NP, S>& a, S b) { Dual<NP, S> r = a; r.v -= b; return r; }
+template <int NP, class S>
+__device__ __forceinline__ Dual<NP, S> operator-(S b, const Dual<NP, S>& a)
 {
-    Dual<NP> r; r.v = b - a.v;
+    Dual<NP, S> r; r.v = b - a.v;
 #pragma unroll
     for (int q = 0; q < NP; ++q) r.g[q] = -a.g[q];
     return r;
 }
-template <int NP>
-__device__ __forceinline__ Dual<NP> operator*(const Dual<NP>& a, double b)
+template <int NP, class S>
+__device__ __forceinline__ Dual<NP, S> operator*(const Dual<NP, S>& a, S b)
 {
-    Dual<NP> r; r.v = a.v * b;
+    Dual<NP, S> r; r.v = a.v * b;
 #pragma unroll
     for (int q = 0; q < NP; ++q) r.g[q] = a.g[q] * b;
     return r;
 }
-template <int NP>
-__device__ __forceinline__ Dual<NP> operator*(double b, const Dual<NP>& a) { return a * b; }
-template <int NP>
-__device__ __forceinline__ Dual<NP> rsqrt_(const Dual<NP>& a)
+template <int NP, class S>
+__device__ __forceinline__ Dual<NP, S> operator*(S b, const Dual<NP, S>& a) { return a * b; }
+template <int NP, class S>
+__device__ __forceinline__ Dual<NP, S> rsqrt_(const Dual<NP, S>& a)
 {
-    Dual<NP> r; r.v = rsqrt(a.v);
-    double d = -0.5 * r.v * r.v * r.v;
+    Dual<NP, S> r; r.v = rsqrt_(a.v);
+    const S d = S(-0.5) * r.v * r.v * r.v;
 #pragma unroll
     for (int q = 0; q < NP; ++q) r.g[q] = d * a.g[q];
     return r;

@@ -3,6 +3,7 @@ solve, RFD drift, adjoint and divergence against the oracle."""
 import numpy as np
 import pytest
 import scipy.linalg
+import torch
 
 from oracle import krylov, mobility as om, precond, rfd, saddle
 from paper_1709_02410_gb300 import F32, F64, synth
@@ -171,3 +172,37 @@ def test_adjoint_c2_sampled_and_fd():
         fm = float((ud * h.mobility_apply(to_dev(rm), Fd)).sum())
         fd = (fp - fm) / (2 * hstep)
         assert abs(fd - g[c, k]) <= 1e-5 * np.abs(g).max() + 1e-6 * abs(g[c, k])
+
+
+def test_rfd_mean_matches_exact_divergence():
+    """Sec. 3 (eq. RFDB): the mean of the blob RFD over random W is div M.
+    GPU RFD samples (FP64, delta = 1e-5) against the GPU divergence kernel,
+    which is itself checked against the oracle; 4,000 seeds on 60 blobs."""
+    s = synth.boomerang_suspension(4, 4.0, 22, lift=False)
+    r = positions(s)
+    h = handle_for(s)
+    rd = to_dev(r)
+    div = h.mobility_divergence(rd).cpu().numpy()
+    np.testing.assert_allclose(div, om.divergence(r, oracle_params(s)), rtol=1e-10, atol=1e-10 * np.abs(div).max())
+    ns = 4000
+    Ws = torch.randn((ns, 3, s.n), dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(5))
+    acc = torch.zeros((3, s.n), dtype=torch.float64, device="cuda")
+    acc2 = torch.zeros_like(acc)
+    for i in range(ns):
+        d = h.rfd_drift(rd, Ws[i].contiguous(), 1e-5, dtype=F64)
+        acc += d
+        acc2 += d * d
+    mean = (acc / ns).cpu().numpy()
+    se = np.sqrt(np.maximum((acc2 / ns).cpu().numpy() - mean**2, 0) / ns)
+    z = np.abs(mean - div) / (se + 1e-30)
+    assert np.mean(z < 3) > 0.97 and z.max() < 6
+
+
+def test_adjoint_f32_variant():
+    s = synth.boomerang_suspension(60, 12.0, 23, lift=False)
+    r = positions(s)
+    rng = np.random.default_rng(24)
+    u, F = rng.standard_normal((2, 3, s.n))
+    h = handle_for(s)
+    g = h.mobility_adjoint(to_dev(r), to_dev(u), to_dev(F), dtype=F32).cpu().numpy()
+    assert rel2(g, om.grad(r, u, F, oracle_params(s))) <= 1e-5
