@@ -146,6 +146,10 @@ def run_ours(args, rank, world, local):
     forces = Forces(1.57e-11 * 9.81e6, 0.096, 0.162, 0.1, (0.0, 0.0, 0.0))
     Lp = 14 * 1.05 * s.a          # arm length: 7 spacings of 2.1 a
 
+    # pick the fastest FP32 kernel variant for this suspension (k = 1: the Krylov matvecs)
+    r0 = h.blobs_from_bodies(shape, q0, th0)
+    tuned = h.autotune(r0, 1)
+
     def sp(i):
         return StepParams(0.01, 1e-3, Lp, 1e-6, 1e-4, 300, 100, 80, P.F32, 2024 + rank, i)
 
@@ -342,6 +346,8 @@ def run_ours(args, rank, world, local):
             "clocks": clk,
             "pair_kernels_in_step": prof,
             "solver_iterations_per_step": iters,
+            "autotune_k1": {"choice": tuned[0], "ms_per_launch": tuned[1],
+                            "legend": "0: one-direction kernel; 1 + v: symmetric kernel variant v"},
             "matvec": extra,
             "batched_c4": batched,
             "ts_step_rollers_c3": rollers,

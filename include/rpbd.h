@@ -279,7 +279,17 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, const double* r, const rpbd_forc
  * which forms each unordered pair's block once and applies it both ways
  * (M_ji = M_ij^T, Sec. 2.1); 0: the one-direction kernel for every k. */
 #define RPBD_OPT_SYMMETRIC 1
+/* -1 (default): per-k default; 0..3: loop-unroll / occupancy variant of the
+ * symmetric kernel. */
+#define RPBD_OPT_SYM_VARIANT 2
 int rpbd_set_option(rpbd_handle* h, int option, int value);
+
+/* Times the FP32 matvec kernels on n blobs at r (k right-hand sides, zero
+ * forces): the one-direction kernel and, for k <= 4, every symmetric variant;
+ * keeps the fastest in the handle and returns its index (0: one-direction,
+ * 1 + v: symmetric variant v) or a negative status.  *best_ms (host, may be
+ * NULL) receives its time per launch.  Synchronises the stream. */
+int rpbd_autotune(rpbd_handle* h, int64_t n, const double* r, int k, double* best_ms, void* stream);
 
 /* ---- instrumentation ----------------------------------------------------- */
 

@@ -70,6 +70,17 @@ class Handle:
         """FP32 matvecs with k <= 4: symmetric kernel (default) or one-direction."""
         self._check(self.lib.rpbd_set_option(self.h, 1, int(bool(on))), "set_option")
 
+    def set_sym_variant(self, v: int):
+        self._check(self.lib.rpbd_set_option(self.h, 2, int(v)), "set_option")
+
+    def autotune(self, r, k=1):
+        """Pick the fastest FP32 kernel for this n and k; returns (choice, ms per launch)."""
+        ms = C.c_double()
+        c = self.lib.rpbd_autotune(self.h, r.shape[1], _ptr(r), k, C.byref(ms), _stream())
+        if c < 0:
+            self._check(c, "autotune")
+        return c, ms.value
+
     # ---- a1
     def blobs_from_bodies(self, shape, q, theta, out=None):
         nb, nper = q.shape[0], shape.shape[0]

@@ -159,6 +159,10 @@ int rpbd_set_option(rpbd_handle* h, int option, int value)
     if (!h) return RPBD_BAD_ARG;
     switch (option) {
     case RPBD_OPT_SYMMETRIC: h->use_sym = value != 0; return RPBD_OK;
+    case RPBD_OPT_SYM_VARIANT:
+        if (value < -1 || value > 3) return set_error(h, RPBD_BAD_ARG, "symmetric variant must be -1..3");
+        h->sym_variant = value;
+        return RPBD_OK;
     default: return set_error(h, RPBD_BAD_ARG, "unknown option");
     }
 }
@@ -195,6 +199,49 @@ int rpbd_profile_read(rpbd_handle* h, int dtype, int k, double* ms, long long* l
     }
     h->prof.swap(keep);
     return RPBD_OK;
+}
+
+int rpbd_autotune(rpbd_handle* h, int64_t n, const double* r, int k, double* best_ms, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (n <= 0 || !r || k < 1 || k > 16) return set_error(h, RPBD_BAD_ARG, "autotune: bad arguments");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    float* F;
+    RPBD_TRY(ensure_t(h, BUF_AUX, (size_t)2 * k * 3 * n, &F));
+    float* U = F + (size_t)k * 3 * n;
+    RPBD_CU(h, cudaMemsetAsync(F, 0, sizeof(float) * k * 3 * n, st));
+    cudaEvent_t e0, e1;
+    RPBD_CU(h, cudaEventCreate(&e0));
+    RPBD_CU(h, cudaEventCreate(&e1));
+    // candidates: one-direction kernel (-1) and, for k <= 4, the symmetric variants 0..3
+    const int ncand = k <= 4 ? 5 : 1;
+    double best = 1e300;
+    int best_c = -1;
+    const bool prof = h->profile;
+    h->profile = false;
+    for (int c = -1; c < ncand - 1; ++c) {
+        h->use_sym = c >= 0;
+        if (c >= 0) h->sym_variant = c;
+        int s = mobility_apply_impl(h, n, r, F, U, k, RPBD_F32, false, st);
+        if (s != RPBD_OK) { h->profile = prof; return s; }
+        RPBD_CU(h, cudaEventRecord(e0, st));
+        for (int rep = 0; rep < 2; ++rep) RPBD_TRY(mobility_apply_impl(h, n, r, F, U, k, RPBD_F32, false, st));
+        RPBD_CU(h, cudaEventRecord(e1, st));
+        RPBD_CU(h, cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        RPBD_CU(h, cudaEventElapsedTime(&ms, e0, e1));
+        if (ms / 2.0 < best) {
+            best = ms / 2.0;
+            best_c = c;
+        }
+    }
+    h->profile = prof;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    h->use_sym = best_c >= 0;
+    h->sym_variant = best_c >= 0 ? best_c : 0;
+    if (best_ms) *best_ms = best;
+    return best_c + 1;
 }
 
 int rpbd_blobs_from_bodies(rpbd_handle* h, int64_t nb, int nper, const double* shape, const double* q,

@@ -162,10 +162,9 @@ __global__ void pack_kernel(int64_t n, int64_t n_pad, int k, const double* __res
 // 2. pair kernel
 
 template <class R, int K, int BT, int TS, int NST, bool WALL>
-__global__ void __launch_bounds__(BT, (sizeof(R) == 4 && K == 16) ? 5 : 1) pair_kernel(const R* __restrict__ rec, int64_t n, int64_t n_pad,
-                                                  int tiles_per_chunk, int n_tiles, PairConst<R> pc,
-                                                  typename PartialT<R>::type* __restrict__ partial,
-                                                  int* __restrict__ err_flag)
+__device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, int64_t n_pad, int tiles_per_chunk,
+                                          int n_tiles, PairConst<R> pc, typename PartialT<R>::type* __restrict__ partial,
+                                          int* __restrict__ err_flag)
 {
     constexpr int LEN = Rec<R, K>::LEN;
     constexpr uint32_t TILE_BYTES = TS * LEN * sizeof(R);
@@ -282,6 +281,32 @@ __global__ void __launch_bounds__(BT, (sizeof(R) == 4 && K == 16) ? 5 : 1) pair_
     }
 }
 
+template <class R, int K, int BT, int TS, int NST, bool WALL>
+__global__ void __launch_bounds__(BT) pair_kernel(const R* __restrict__ rec, int64_t n, int64_t n_pad,
+                                                  int tiles_per_chunk, int n_tiles, PairConst<R> pc,
+                                                  typename PartialT<R>::type* __restrict__ partial,
+                                                  int* __restrict__ err_flag)
+{
+    pair_body<R, K, BT, TS, NST, WALL>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag);
+}
+
+// FP32, 16 right-hand sides: registers capped so five CTAs share an SM
+template <class R, int K, int BT, int TS, int NST, bool WALL>
+__global__ void __launch_bounds__(BT, 5) pair_kernel_k16(const R* __restrict__ rec, int64_t n, int64_t n_pad,
+                                                         int tiles_per_chunk, int n_tiles, PairConst<R> pc,
+                                                         typename PartialT<R>::type* __restrict__ partial,
+                                                         int* __restrict__ err_flag)
+{
+    pair_body<R, K, BT, TS, NST, WALL>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag);
+}
+
+template <class R, int K, int BT, int TS, int NST, bool WALL>
+static auto pick_pair_kernel()
+{
+    if constexpr (sizeof(R) == 4 && K == 16) return pair_kernel_k16<R, K, BT, TS, NST, WALL>;
+    else return pair_kernel<R, K, BT, TS, NST, WALL>;
+}
+
 // ---------------------------------------------------------------------------
 // 3. reduce
 
@@ -346,7 +371,7 @@ static int apply_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out*
                                                                            h->p.s_min, rec, scale); count_launch();
     RPBD_LAUNCH_CHECK(h);
     const size_t smem = (size_t)NST * TS * LEN * sizeof(R) + NST * sizeof(uint64_t);
-    auto kern = pair_kernel<R, K, BT, TS, NST, WALL>;
+    auto kern = pick_pair_kernel<R, K, BT, TS, NST, WALL>();
     static bool attr_set = false;
     if (!attr_set) {
         RPBD_CU(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));

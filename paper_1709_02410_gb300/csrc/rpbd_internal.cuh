@@ -106,6 +106,7 @@ struct rpbd_handle {
     std::vector<rpbd::BatchGraph*> bgraphs;
     // symmetric FP32 kernel (k <= 4): on by default, work list cached per n
     int use_sym = 1;
+    int sym_variant = -1;  // -1: default per k; 0..3: loop unroll / occupancy variants of the symmetric kernel
     int64_t sym_plan_n = -1;
     int sym_n_items = 0, sym_n_home = 0, sym_max_slots = 0;
 };

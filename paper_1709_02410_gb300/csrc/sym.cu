@@ -43,6 +43,14 @@ struct Rec {
     static constexpr int LEN = 4 + TAIL;
 };
 
+// tuning variants per K: visitor-loop unroll and minimum resident CTAs per SM
+// (the latter caps registers: 65536 / (MINB * 128)); chosen so no variant spills
+template <int K, int V>
+struct SymVar {
+    static constexpr int UNR = V == 1 ? 1 : (V == 3 ? 4 : 2);
+    static constexpr int MINB = K == 1 ? (V == 2 ? 10 : 8) : (K == 2 ? (V == 2 ? 8 : 7) : (V == 2 ? 5 : 4));
+};
+
 struct SymItem {
     int home;   // home tile index
     int v0;     // first visitor blob (multiple of VT)
@@ -140,8 +148,8 @@ __device__ __forceinline__ void load_rec(const float* rj, float& xh, float& yh, 
     for (int q = 0; q < 3 * K; ++q) f[q] = tail[1 + q];
 }
 
-template <int K, bool WALL>
-__global__ void __launch_bounds__(HT) sym_kernel(const float* __restrict__ rec, int64_t n, int64_t n_pad,
+template <int K, bool WALL, int UNR, int MINB>
+__global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__ rec, int64_t n, int64_t n_pad,
                                                  const SymItem* __restrict__ items, int n_home_tiles, PairConst<float> pc,
                                                  float* __restrict__ partial, int* __restrict__ err_flag)
 {
@@ -201,7 +209,7 @@ __global__ void __launch_bounds__(HT) sym_kernel(const float* __restrict__ rec, 
             float vacc[3 * K];
 #pragma unroll
             for (int q = 0; q < 3 * K; ++q) vacc[q] = 0.0f;
-#pragma unroll 2
+#pragma unroll UNR
             for (int step = 0; step < VT; ++step) {
                 const int v = (step + lane) & (VT - 1);
                 float xh, yh, xl, yl, zj, f[3 * K];
@@ -343,7 +351,14 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
     const PairConst<float> pc = PairConst<float>::make(h->p.a);
     if (h->profile) prof_begin(h, st);
-    sym_kernel<K, WALL><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag);
+    // variant -1: the measured default per K (k = 1: unroll 4; otherwise unroll 2)
+    const int var = h->sym_variant >= 0 ? h->sym_variant : (K == 1 ? 3 : 0);
+    switch (var) {  // tuning variants: (visitor-loop unroll, min CTAs per SM), see SymVar
+    case 1: sym_kernel<K, WALL, SymVar<K, 1>::UNR, SymVar<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    case 2: sym_kernel<K, WALL, SymVar<K, 2>::UNR, SymVar<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    case 3: sym_kernel<K, WALL, SymVar<K, 3>::UNR, SymVar<K, 3>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    default: sym_kernel<K, WALL, SymVar<K, 0>::UNR, SymVar<K, 0>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    }
     count_launch();
     if (h->profile) prof_end(h, st, 3 /* symmetric FP32 */, K, (double)n * (double)n);
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);

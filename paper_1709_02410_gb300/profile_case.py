@@ -18,6 +18,8 @@ def main():
     ap.add_argument("--dtype", choices=["f32", "f64"], default="f32")
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--wall", type=int, default=1)
+    ap.add_argument("--sym", type=int, default=1, help="FP32 k <= 4: symmetric kernel (1) or one-direction (0)")
+    ap.add_argument("--variant", type=int, default=-1, help="symmetric kernel variant 0..3 (-1: default)")
     a = ap.parse_args()
     import torch
     from . import F32, F64, Handle, synth
@@ -25,6 +27,8 @@ def main():
     s = synth.boomerang_suspension(nb, 40.0 * np.sqrt(nb / 128), 1)
     dev = "cuda:0"
     h = Handle(synth.ETA, s.a, synth.KT, wall=bool(a.wall))
+    h.set_symmetric(bool(a.sym))
+    h.set_sym_variant(a.variant)
     T = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
     r = h.blobs_from_bodies(T(s.shape), T(s.q), T(s.theta))
     dt = torch.float32 if a.dtype == "f32" else torch.float64
@@ -39,7 +43,8 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / a.reps
-    print(json.dumps({"n": s.n, "k": a.k, "dtype": a.dtype, "s_per_launch": t, "pairs_per_s": s.n * s.n / t,
+    print(json.dumps({"n": s.n, "k": a.k, "dtype": a.dtype, "sym": a.sym, "variant": a.variant,
+                      "s_per_launch": t, "pairs_per_s": s.n * s.n / t,
                       "matvecs_per_s": a.k / t}))
 
 

@@ -129,3 +129,19 @@ def test_f32_symmetric_and_one_direction_agree(k, n):
     U2 = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
     Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
     assert rel2(U1, Uo) <= 1e-5 and rel2(U2, Uo) <= 1e-5
+
+
+def test_autotune_picks_a_correct_kernel():
+    s = synth.c0_boomerangs_1920()
+    r = positions(s)
+    F = synth.gaussian(60, (1, 3, s.n), np.float32)
+    h = handle_for(s)
+    choice, ms = h.autotune(to_dev(r), 1)
+    assert 0 <= choice <= 4 and ms > 0
+    U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    assert rel2(U, om.apply(r, F.astype(np.float64), oracle_params(s))) <= 1e-5
+    for v in range(4):
+        h.set_symmetric(True)
+        h.set_sym_variant(v)
+        U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+        assert rel2(U, om.apply(r, F.astype(np.float64), oracle_params(s))) <= 1e-5
