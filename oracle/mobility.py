@@ -24,12 +24,12 @@ def lib():
         d, i64, i = C.c_double, C.c_int64, C.c_int
         P = C.POINTER(C.c_double)
         PI = C.POINTER(C.c_int64)
-        _lib.orc_mobility_apply_rows.argtypes = [i64, P, P, P, i, d, d, i, d, PI, i64]
-        _lib.orc_mobility_dense.argtypes = [i64, P, P, d, d, i, d]
-        _lib.orc_mobility_grad_rows.argtypes = [i64, P, P, P, P, d, d, i, d, PI, i64]
-        _lib.orc_mobility_div_rows.argtypes = [i64, P, P, d, d, i, d, PI, i64]
-        _lib.orc_pair_block.argtypes = [P, P, i, d, d, i, d, P]
-        _lib.orc_pair_dblock.argtypes = [P, P, i, d, d, i, d, P, P]
+        _lib.orc_mobility_apply_rows.argtypes = [i64, P, P, P, i, d, d, i, d, d, d, PI, i64]
+        _lib.orc_mobility_dense.argtypes = [i64, P, P, d, d, i, d, d, d]
+        _lib.orc_mobility_grad_rows.argtypes = [i64, P, P, P, P, d, d, i, d, d, d, PI, i64]
+        _lib.orc_mobility_div_rows.argtypes = [i64, P, P, d, d, i, d, d, d, PI, i64]
+        _lib.orc_pair_block.argtypes = [P, P, i, d, d, i, d, d, d, P]
+        _lib.orc_pair_dblock.argtypes = [P, P, i, d, d, i, d, d, d, P, P]
         _lib.orc_blake_point.argtypes = [P, P, P]
         _lib.orc_num_threads.restype = i
     return _lib
@@ -44,11 +44,15 @@ def _c(a):
 
 
 class Params:
-    def __init__(self, eta, a, wall=True, s_min=1e-3):
+    """eta, a, wall on/off, overlap floor s_min; Lx, Ly > 0 switch on the
+    pseudo-periodic sum of Sec. 4.2 (minimum image + 8 nearest images)."""
+
+    def __init__(self, eta, a, wall=True, s_min=1e-3, Lx=0.0, Ly=0.0):
         self.eta, self.a, self.wall, self.s_min = float(eta), float(a), int(bool(wall)), float(s_min)
+        self.Lx, self.Ly = float(Lx), float(Ly)
 
     def args(self):
-        return (self.eta, self.a, self.wall, self.s_min)
+        return (self.eta, self.a, self.wall, self.s_min, self.Lx, self.Ly)
 
 
 def num_threads() -> int:

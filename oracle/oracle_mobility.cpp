@@ -21,6 +21,8 @@
  *     so M = S M(r~) S is SPD whenever M(r~) is.
  *   - wall = 0 switches the image part and the regularisation off
  *     (unbounded RPY); used by the free-space pins.
+ *   - Lx, Ly > 0: pseudo-periodic suspension (Sec. 4.2): every pair sums the
+ *     source's minimum image in x, y and its 8 nearest periodic images.
  *
  * Derivatives (adjoint, divergence) are exact: the same block code is
  * instantiated on a forward-mode dual number carrying d/d(x_i, x_j).
@@ -94,6 +96,7 @@ struct Params {
     double eta, a;
     int wall;
     double s_min;
+    double Lx, Ly;  // pseudo-periodic cell in x, y (0: open)
 };
 
 /* regularised height and scale of one blob, with their z-derivatives */
@@ -147,8 +150,8 @@ void block_t(const Params& p, const T* xi, const T* xj, bool same, T* B)
     }
 }
 
-/* M_ij in physical units */
-void block(const Params& p, const double* ri, const double* rj, bool same, double* M)
+/* M_ij in physical units, one image */
+void block_one(const Params& p, const double* ri, const double* rj, bool same, double* M)
 {
     double zti, si, dzi, dsi, ztj, sj, dzj, dsj;
     reg(p, ri[2], &zti, &si, &dzi, &dsi);
@@ -164,7 +167,7 @@ void block(const Params& p, const double* ri, const double* rj, bool same, doubl
  * Dy likewise for r_j, with the overlap regularisation chained in.  For
  * i == j the caller adds Dx + Dy (both arguments are the same blob).  The
  * free-space part of a coincident pair is constant and contributes nothing. */
-void dblock(const Params& p, const double* ri, const double* rj, bool same, double* Dx, double* Dy)
+void dblock_one(const Params& p, const double* ri, const double* rj, bool same, double* Dx, double* Dy)
 {
     double zti, si, dzi, dsi, ztj, sj, dzj, dsj;
     reg(p, ri[2], &zti, &si, &dzi, &dsi);
@@ -185,6 +188,47 @@ void dblock(const Params& p, const double* ri, const double* rj, bool same, doub
             Dy[q * 3 + e] = c0 * vy;
         }
     }
+}
+
+/* Pseudo-periodic sum (Sec. 4.2): the source is moved to its minimum image
+ * in x and y, then that image and its 8 nearest periodic images all act on
+ * the target.  For i == j the unshifted term is the self block. */
+template <class F>
+void for_images(const Params& p, const double* ri, const double* rj, bool same, F f)
+{
+    if (!(p.Lx > 0.0 && p.Ly > 0.0)) {
+        f(rj, same);
+        return;
+    }
+    const double mx = std::nearbyint((ri[0] - rj[0]) / p.Lx), my = std::nearbyint((ri[1] - rj[1]) / p.Ly);
+    for (int a = -1; a <= 1; ++a)
+        for (int b = -1; b <= 1; ++b) {
+            const double img[3] = {rj[0] + (mx + a) * p.Lx, rj[1] + (my + b) * p.Ly, rj[2]};
+            f(img, same && a == 0 && b == 0);
+        }
+}
+
+void block(const Params& p, const double* ri, const double* rj, bool same, double* M)
+{
+    for (int q = 0; q < 9; ++q) M[q] = 0.0;
+    for_images(p, ri, rj, same, [&](const double* y, bool sm) {
+        double B[9];
+        block_one(p, ri, y, sm, B);
+        for (int q = 0; q < 9; ++q) M[q] += B[q];
+    });
+}
+
+void dblock(const Params& p, const double* ri, const double* rj, bool same, double* Dx, double* Dy)
+{
+    for (int q = 0; q < 27; ++q) Dx[q] = Dy[q] = 0.0;
+    for_images(p, ri, rj, same, [&](const double* y, bool sm) {
+        double X[27], Y[27];
+        dblock_one(p, ri, y, sm, X, Y);
+        for (int q = 0; q < 27; ++q) {
+            Dx[q] += X[q];
+            Dy[q] += Y[q];
+        }
+    });
 }
 
 /* Neumaier compensated accumulator */
@@ -211,10 +255,10 @@ extern "C" {
 /* U = M F for k right-hand sides on the rows listed in `rows` (all rows when
  * rows == NULL, nrows == n).  Output layout [k][3][nrows]. */
 void orc_mobility_apply_rows(int64_t n, const double* r, const double* F, double* U, int k,
-                             double eta, double a, int wall, double s_min,
+                             double eta, double a, int wall, double s_min, double Lx, double Ly,
                              const int64_t* rows, int64_t nrows)
 {
-    Params p{eta, a, wall, s_min};
+    Params p{eta, a, wall, s_min, Lx, Ly};
 #pragma omp parallel for schedule(dynamic, 8)
     for (int64_t q = 0; q < nrows; ++q) {
         int64_t i = rows ? rows[q] : q;
@@ -238,15 +282,16 @@ void orc_mobility_apply_rows(int64_t n, const double* r, const double* F, double
 }
 
 void orc_mobility_apply(int64_t n, const double* r, const double* F, double* U, int k,
-                        double eta, double a, int wall, double s_min)
+                        double eta, double a, int wall, double s_min, double Lx, double Ly)
 {
-    orc_mobility_apply_rows(n, r, F, U, k, eta, a, wall, s_min, nullptr, n);
+    orc_mobility_apply_rows(n, r, F, U, k, eta, a, wall, s_min, Lx, Ly, nullptr, n);
 }
 
 /* dense 3n x 3n matrix, row-major: entry (3i+c, 3j+d) = (M_ij)_cd */
-void orc_mobility_dense(int64_t n, const double* r, double* Md, double eta, double a, int wall, double s_min)
+void orc_mobility_dense(int64_t n, const double* r, double* Md, double eta, double a, int wall, double s_min,
+                        double Lx, double Ly)
 {
-    Params p{eta, a, wall, s_min};
+    Params p{eta, a, wall, s_min, Lx, Ly};
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t i = 0; i < n; ++i) {
         double ri[3], rj[3], M[9];
@@ -265,10 +310,10 @@ void orc_mobility_dense(int64_t n, const double* r, double* Md, double eta, doub
  * output [3][nrows].  Straight from the definition: every ordered pair (i, j)
  * depends on r_i as target and on r_j as source. */
 void orc_mobility_grad_rows(int64_t n, const double* r, const double* u, const double* F, double* g,
-                            double eta, double a, int wall, double s_min,
+                            double eta, double a, int wall, double s_min, double Lx, double Ly,
                             const int64_t* rows, int64_t nrows)
 {
-    Params p{eta, a, wall, s_min};
+    Params p{eta, a, wall, s_min, Lx, Ly};
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t q = 0; q < nrows; ++q) {
         int64_t k = rows ? rows[q] : q;
@@ -306,9 +351,9 @@ void orc_mobility_grad_rows(int64_t n, const double* r, const double* u, const d
  * (the divergence the RFD identity of Sec. 3 estimates, with B = M).
  * For j = i both arguments move together. Output [3][nrows]. */
 void orc_mobility_div_rows(int64_t n, const double* r, double* div, double eta, double a, int wall,
-                           double s_min, const int64_t* rows, int64_t nrows)
+                           double s_min, double Lx, double Ly, const int64_t* rows, int64_t nrows)
 {
-    Params p{eta, a, wall, s_min};
+    Params p{eta, a, wall, s_min, Lx, Ly};
 #pragma omp parallel for schedule(dynamic, 4)
     for (int64_t q = 0; q < nrows; ++q) {
         int64_t i = rows ? rows[q] : q;
@@ -333,17 +378,17 @@ void orc_mobility_div_rows(int64_t n, const double* r, double* div, double eta, 
 
 /* one block M_ij (physical units), for pins */
 void orc_pair_block(const double* ri, const double* rj, int same, double eta, double a, int wall,
-                    double s_min, double* M)
+                    double s_min, double Lx, double Ly, double* M)
 {
-    Params p{eta, a, wall, s_min};
+    Params p{eta, a, wall, s_min, Lx, Ly};
     block(p, ri, rj, same != 0, M);
 }
 
 /* one block's derivatives, for pins */
 void orc_pair_dblock(const double* ri, const double* rj, int same, double eta, double a, int wall,
-                     double s_min, double* Dx, double* Dy)
+                     double s_min, double Lx, double Ly, double* Dx, double* Dy)
 {
-    Params p{eta, a, wall, s_min};
+    Params p{eta, a, wall, s_min, Lx, Ly};
     dblock(p, ri, rj, same != 0, Dx, Dy);
 }
 
