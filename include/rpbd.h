@@ -55,6 +55,10 @@ typedef struct rpbd_params {
     double kT;    /* thermal energy k_B T */
     int wall;     /* 1: no-slip wall at z = 0 (Rotne-Prager-Blake); 0: unbounded RPY */
     double s_min; /* floor of the wall-overlap scale s_i = clamp(z_i/a, s_min, 1) */
+    double Lx, Ly; /* > 0 (both): pseudo-periodic cell of Sec. 4.2 -- every pair sums the
+                      source's minimum image in x, y and its 8 nearest periodic images;
+                      needs wall = 1.  0, 0: open in x, y.  The batched and
+                      allocation-free calls take open systems only. */
 } rpbd_params;
 
 /* Per-call solver statistics (host struct, filled before return). */

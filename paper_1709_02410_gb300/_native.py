@@ -13,7 +13,7 @@ STATUS = {0: "ok", -1: "bad argument", -2: "bad input", -3: "CUDA error", -4: "n
 
 class Params(C.Structure):
     _fields_ = [("eta", C.c_double), ("a", C.c_double), ("kT", C.c_double), ("wall", C.c_int),
-                ("s_min", C.c_double)]
+                ("s_min", C.c_double), ("Lx", C.c_double), ("Ly", C.c_double)]
 
 
 class Stats(C.Structure):

@@ -40,9 +40,9 @@ def _need(t, dtype, shape=None, name="tensor"):
 class Handle:
     """Owns an rpbd_handle (device workspace + physical parameters)."""
 
-    def __init__(self, eta, a, kT=0.0, wall=True, s_min=1e-3):
+    def __init__(self, eta, a, kT=0.0, wall=True, s_min=1e-3, Lx=0.0, Ly=0.0):
         self.lib = _native.load()
-        self.params = Params(eta, a, kT, int(bool(wall)), s_min)
+        self.params = Params(eta, a, kT, int(bool(wall)), s_min, Lx, Ly)
         h = C.c_void_p()
         st = self.lib.rpbd_create(C.byref(h), C.byref(self.params))
         if st != 0:

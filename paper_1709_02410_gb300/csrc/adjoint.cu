@@ -48,7 +48,7 @@ __device__ __forceinline__ RegBlob reg_blob(const double* r, int64_t n, int64_t 
 // block of target t (dual: partials w.r.t. t's regularised coordinates) and
 // source s; out[9] row-major.  Differences are taken in FP64, then the block
 // is evaluated in S (double, or float for the FP32 variant).
-template <bool WALL, class S>
+template <bool WALL, bool PER, class S>
 __device__ __forceinline__ void dual_block(const RegBlob& t, const RegBlob& s, const PairConst<S>& pc,
                                            Dual<3, S> M[9])
 {
@@ -59,20 +59,20 @@ __device__ __forceinline__ void dual_block(const RegBlob& t, const RegBlob& s, c
     dz.g[2] = S(1);
     zi.g[2] = S(1);
     D3 Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz;
-    pair_block<D3, S, WALL>(dx, dy, dz, zi, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
+    pair_block_images<D3, S, WALL, PER>(dx, dy, dz, zi, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
     M[0] = Mxx; M[1] = Mxy; M[2] = Mxz;
     M[3] = Mxy; M[4] = Myy; M[5] = Myz;
     M[6] = Mzx; M[7] = Mzy; M[8] = Mzz;
 }
 
-template <bool WALL, class S>
+template <bool WALL, bool PER, class S>
 __global__ void adjoint_kernel(int64_t n, const double* __restrict__ r, const double* __restrict__ u,
-                               const double* __restrict__ F, double a, double s_min, double inv8pieta,
-                               double* __restrict__ g)
+                               const double* __restrict__ F, double a, double s_min, double Lx, double Ly,
+                               double inv8pieta, double* __restrict__ g)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n) return;
-    const PairConst<S> pc = PairConst<S>::make(a);
+    const PairConst<S> pc = PairConst<S>::make(a, Lx, Ly);
     const RegBlob bk = reg_blob(r, n, k, a, WALL, s_min);
     const double uk[3] = {u[k], u[n + k], u[2 * n + k]};
     const double Fk[3] = {F[k], F[n + k], F[2 * n + k]};
@@ -82,7 +82,7 @@ __global__ void adjoint_kernel(int64_t n, const double* __restrict__ r, const do
         const double Fj[3] = {bj.s * F[j], bj.s * F[n + j], bj.s * F[2 * n + j]};
         const double uj[3] = {bj.s * u[j], bj.s * u[n + j], bj.s * u[2 * n + j]};
         Dual<3, S> M[9];
-        dual_block<WALL, S>(bk, bj, pc, M);
+        dual_block<WALL, PER, S>(bk, bj, pc, M);
 #pragma unroll
         for (int c = 0; c < 3; ++c)
 #pragma unroll
@@ -98,19 +98,19 @@ __global__ void adjoint_kernel(int64_t n, const double* __restrict__ r, const do
     g[2 * n + k] = inv8pieta * (bk.s * gr[2] * bk.dzt + bk.ds * psi);
 }
 
-template <bool WALL>
-__global__ void divergence_kernel(int64_t n, const double* __restrict__ r, double a, double s_min, double inv8pieta,
-                                  double* __restrict__ div)
+template <bool WALL, bool PER>
+__global__ void divergence_kernel(int64_t n, const double* __restrict__ r, double a, double s_min, double Lx,
+                                  double Ly, double inv8pieta, double* __restrict__ div)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const PairConst<double> pc = PairConst<double>::make(a);
+    const PairConst<double> pc = PairConst<double>::make(a, Lx, Ly);
     const RegBlob bi = reg_blob(r, n, i, a, WALL, s_min);  // divergence: FP64 only
     double acc[3] = {0.0, 0.0, 0.0};
     for (int64_t j = 0; j < n; ++j) {
         Dual<3, double> T[9];
         if (j == i) {
-            dual_block<WALL, double>(bi, bi, pc, T);
+            dual_block<WALL, PER, double>(bi, bi, pc, T);
 #pragma unroll
             for (int aa = 0; aa < 3; ++aa) {
                 double v = 2.0 * bi.s * bi.ds * T[aa * 3 + 2].v;
@@ -123,7 +123,7 @@ __global__ void divergence_kernel(int64_t n, const double* __restrict__ r, doubl
             }
         } else {
             const RegBlob bj = reg_blob(r, n, j, a, WALL, s_min);
-            dual_block<WALL, double>(bj, bi, pc, T);  // target j, source i
+            dual_block<WALL, PER, double>(bj, bi, pc, T);  // target j, source i
 #pragma unroll
             for (int aa = 0; aa < 3; ++aa) {
                 double v = bi.s * bj.ds * T[2 * 3 + aa].v;
@@ -155,13 +155,16 @@ static int adjoint_entry(rpbd_handle* h, int64_t n, const double* r, const doubl
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
     const unsigned grid = (unsigned)((n + 127) / 128);
-    const double a = h->p.a, sm = h->p.s_min;
+    const double a = h->p.a, sm = h->p.s_min, Lx = h->p.Lx, Ly = h->p.Ly;
+    const bool per = Lx > 0.0;
     if (f32) {
-        if (h->p.wall) adjoint_kernel<true, float><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, inv8pieta, grad);
-        else adjoint_kernel<false, float><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, inv8pieta, grad);
+        if (per) adjoint_kernel<true, true, float><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
+        else if (h->p.wall) adjoint_kernel<true, false, float><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
+        else adjoint_kernel<false, false, float><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
     } else {
-        if (h->p.wall) adjoint_kernel<true, double><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, inv8pieta, grad);
-        else adjoint_kernel<false, double><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, inv8pieta, grad);
+        if (per) adjoint_kernel<true, true, double><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
+        else if (h->p.wall) adjoint_kernel<true, false, double><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
+        else adjoint_kernel<false, false, double><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
     }
     count_launch();
     RPBD_LAUNCH_CHECK(h);
@@ -188,8 +191,10 @@ int rpbd_mobility_divergence(rpbd_handle* h, int64_t n, const double* r, double*
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
     const unsigned grid = (unsigned)((n + 127) / 128);
-    if (h->p.wall) divergence_kernel<true><<<grid, 128, 0, st>>>(n, r, h->p.a, h->p.s_min, inv8pieta, div);
-    else divergence_kernel<false><<<grid, 128, 0, st>>>(n, r, h->p.a, h->p.s_min, inv8pieta, div);
+    const double Lx = h->p.Lx, Ly = h->p.Ly;
+    if (Lx > 0.0) divergence_kernel<true, true><<<grid, 128, 0, st>>>(n, r, h->p.a, h->p.s_min, Lx, Ly, inv8pieta, div);
+    else if (h->p.wall) divergence_kernel<true, false><<<grid, 128, 0, st>>>(n, r, h->p.a, h->p.s_min, Lx, Ly, inv8pieta, div);
+    else divergence_kernel<false, false><<<grid, 128, 0, st>>>(n, r, h->p.a, h->p.s_min, Lx, Ly, inv8pieta, div);
     count_launch();
     RPBD_LAUNCH_CHECK(h);
     return RPBD_OK;

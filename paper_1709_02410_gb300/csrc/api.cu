@@ -100,6 +100,7 @@ int rpbd_create(rpbd_handle** out, const rpbd_params* p)
     if (!out || !p) return RPBD_BAD_ARG;
     *out = nullptr;
     if (!(p->eta > 0) || !(p->a > 0) || !(p->kT >= 0) || !(p->s_min > 0) || p->s_min > 1) return RPBD_BAD_ARG;
+    if (!(p->Lx >= 0) || !(p->Ly >= 0) || ((p->Lx > 0) != (p->Ly > 0)) || (p->Lx > 0 && !p->wall)) return RPBD_BAD_ARG;
     rpbd_handle* h = new (std::nothrow) rpbd_handle();
     if (!h) return RPBD_NO_MEM;
     h->p = *p;

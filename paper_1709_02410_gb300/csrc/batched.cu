@@ -455,6 +455,7 @@ int batched_apply_impl(rpbd_handle* h, int n_sys, const int64_t* off, const doub
                        bool io_double, const int* active, cudaStream_t st)
 {
     if (n_sys <= 0) return set_error(h, RPBD_BAD_ARG, "batched: n_sys <= 0");
+    if (h->p.Lx > 0.0) return set_error(h, RPBD_BAD_ARG, "batched: systems are open in x, y (no periodic cell)");
     if (k < 1 || k > 16) return set_error(h, RPBD_BAD_ARG, "batched: k must be in 1..16");
     for (int s = 0; s < n_sys; ++s)
         if (off[s + 1] < off[s] || (off[s + 1] - off[s]) > (int64_t)1 << 30)

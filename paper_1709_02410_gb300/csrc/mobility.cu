@@ -161,7 +161,7 @@ __global__ void pack_kernel(int64_t n, int64_t n_pad, int k, const double* __res
 // ---------------------------------------------------------------------------
 // 2. pair kernel
 
-template <class R, int K, int BT, int TS, int NST, bool WALL>
+template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
 __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, int64_t n_pad, int tiles_per_chunk,
                                           int n_tiles, PairConst<R> pc, typename PartialT<R>::type* __restrict__ partial,
                                           int* __restrict__ err_flag)
@@ -244,7 +244,7 @@ __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, 
                 }
                 const R dz = zi - zj;
                 R Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz;
-                pair_block<R, R, WALL>(dx, dy, dz, zi, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
+                pair_block_images<R, R, WALL, PER>(dx, dy, dz, zi, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
 #pragma unroll
                 for (int m = 0; m < K; ++m) {
                     // three FMA chains: 9 FMA per right-hand side
@@ -281,30 +281,30 @@ __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, 
     }
 }
 
-template <class R, int K, int BT, int TS, int NST, bool WALL>
+template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
 __global__ void __launch_bounds__(BT) pair_kernel(const R* __restrict__ rec, int64_t n, int64_t n_pad,
                                                   int tiles_per_chunk, int n_tiles, PairConst<R> pc,
                                                   typename PartialT<R>::type* __restrict__ partial,
                                                   int* __restrict__ err_flag)
 {
-    pair_body<R, K, BT, TS, NST, WALL>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag);
+    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag);
 }
 
 // FP32, 16 right-hand sides: registers capped so five CTAs share an SM
-template <class R, int K, int BT, int TS, int NST, bool WALL>
+template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
 __global__ void __launch_bounds__(BT, 5) pair_kernel_k16(const R* __restrict__ rec, int64_t n, int64_t n_pad,
                                                          int tiles_per_chunk, int n_tiles, PairConst<R> pc,
                                                          typename PartialT<R>::type* __restrict__ partial,
                                                          int* __restrict__ err_flag)
 {
-    pair_body<R, K, BT, TS, NST, WALL>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag);
+    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag);
 }
 
-template <class R, int K, int BT, int TS, int NST, bool WALL>
+template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
 static auto pick_pair_kernel()
 {
-    if constexpr (sizeof(R) == 4 && K == 16) return pair_kernel_k16<R, K, BT, TS, NST, WALL>;
-    else return pair_kernel<R, K, BT, TS, NST, WALL>;
+    if constexpr (sizeof(R) == 4 && K == 16) return pair_kernel_k16<R, K, BT, TS, NST, WALL, PER>;
+    else return pair_kernel<R, K, BT, TS, NST, WALL, PER>;
 }
 
 // ---------------------------------------------------------------------------
@@ -339,7 +339,7 @@ constexpr Tile default_tile()
     else return Tile{128, 32, 3};
 }
 
-template <class R, int K, bool WALL, class In, class Out>
+template <class R, int K, bool WALL, bool PER, class In, class Out>
 static int apply_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
 {
     constexpr Tile T = default_tile<R, K>();
@@ -366,12 +366,12 @@ static int apply_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out*
     RPBD_TRY(ensure_t(h, BUF_SCALE, (size_t)n_pad, &scale));
     RPBD_TRY(ensure_t(h, BUF_PARTIAL, (size_t)n_chunks * 3 * K * n_pad, &partial));
 
-    const PairConst<R> pc = PairConst<R>::make(h->p.a);
+    const PairConst<R> pc = PairConst<R>::make(h->p.a, h->p.Lx, h->p.Ly);
     pack_kernel<R, K, In><<<(unsigned)((n_pad + 255) / 256), 256, 0, st>>>(n, n_pad, k, r, F, h->p.a, h->p.wall,
                                                                            h->p.s_min, rec, scale); count_launch();
     RPBD_LAUNCH_CHECK(h);
     const size_t smem = (size_t)NST * TS * LEN * sizeof(R) + NST * sizeof(uint64_t);
-    auto kern = pick_pair_kernel<R, K, BT, TS, NST, WALL>();
+    auto kern = pick_pair_kernel<R, K, BT, TS, NST, WALL, PER>();
     static bool attr_set = false;
     if (!attr_set) {
         RPBD_CU(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -389,14 +389,14 @@ static int apply_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out*
     return RPBD_OK;
 }
 
-template <class R, bool WALL, class In, class Out>
+template <class R, bool WALL, bool PER, class In, class Out>
 static int apply_dispatch(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
 {
-    if (k <= 1) return apply_k<R, 1, WALL>(h, n, r, F, U, k, st);
-    if (k <= 2) return apply_k<R, 2, WALL>(h, n, r, F, U, k, st);
-    if (k <= 4) return apply_k<R, 4, WALL>(h, n, r, F, U, k, st);
-    if (k <= 8) return apply_k<R, 8, WALL>(h, n, r, F, U, k, st);
-    return apply_k<R, 16, WALL>(h, n, r, F, U, k, st);
+    if (k <= 1) return apply_k<R, 1, WALL, PER>(h, n, r, F, U, k, st);
+    if (k <= 2) return apply_k<R, 2, WALL, PER>(h, n, r, F, U, k, st);
+    if (k <= 4) return apply_k<R, 4, WALL, PER>(h, n, r, F, U, k, st);
+    if (k <= 8) return apply_k<R, 8, WALL, PER>(h, n, r, F, U, k, st);
+    return apply_k<R, 16, WALL, PER>(h, n, r, F, U, k, st);
 }
 
 template <class In, class Out>
@@ -404,11 +404,14 @@ static int apply_typed(rpbd_handle* h, int64_t n, const double* r, const In* F, 
                        cudaStream_t st)
 {
     const bool wall = h->p.wall != 0;
+    const bool per = h->p.Lx > 0.0;  // periodic runs only with the wall (as in Sec. 4.2)
     if (dtype == RPBD_F32)
-        return wall ? apply_dispatch<float, true>(h, n, r, F, U, k, st)
-                    : apply_dispatch<float, false>(h, n, r, F, U, k, st);
-    return wall ? apply_dispatch<double, true>(h, n, r, F, U, k, st)
-                : apply_dispatch<double, false>(h, n, r, F, U, k, st);
+        return per ? apply_dispatch<float, true, true>(h, n, r, F, U, k, st)
+                   : wall ? apply_dispatch<float, true, false>(h, n, r, F, U, k, st)
+                          : apply_dispatch<float, false, false>(h, n, r, F, U, k, st);
+    return per ? apply_dispatch<double, true, true>(h, n, r, F, U, k, st)
+               : wall ? apply_dispatch<double, true, false>(h, n, r, F, U, k, st)
+                      : apply_dispatch<double, false, false>(h, n, r, F, U, k, st);
 }
 
 int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* F, void* U, int k, int dtype,
@@ -516,7 +519,7 @@ static int apply(int sm_count, const rpbd_params& p, int64_t n, const double* r,
     const size_t smem = (size_t)NST * TS * LEN * sizeof(float) + NST * sizeof(uint64_t);
     static_assert((size_t)NST * TS * Rec<float, 16>::LEN * sizeof(float) + NST * sizeof(uint64_t) <= 48 * 1024,
                   "the no-alloc kernels must fit the default dynamic shared memory limit");
-    pair_kernel<float, K, BT, TS, NST, WALL><<<dim3((unsigned)tgt_tiles, (unsigned)n_chunks), BT, smem, st>>>(
+    pair_kernel<float, K, BT, TS, NST, WALL, false><<<dim3((unsigned)tgt_tiles, (unsigned)n_chunks), BT, smem, st>>>(
         rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, flag);
     count_launch();
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * p.eta);
@@ -545,6 +548,7 @@ extern "C" int rpbd_mobility_apply_f32_noalloc(const rpbd_params* p, int64_t n, 
 {
     using namespace rpbd::noalloc;
     if (!p || !(p->eta > 0) || !(p->a > 0) || !(p->s_min > 0) || p->s_min > 1) return RPBD_BAD_ARG;
+    if (p->Lx != 0.0 || p->Ly != 0.0) return RPBD_BAD_ARG;  // open systems only
     if (n < 0 || k < 1) return RPBD_BAD_ARG;
     if (n > NOALLOC_MAX_N || k > 16) return RPBD_TOO_LARGE;  // beyond the fixed scratch array
     if (n == 0) return RPBD_OK;

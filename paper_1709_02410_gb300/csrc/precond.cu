@@ -21,9 +21,10 @@ namespace rpbd {
 constexpr int PREC_THREADS = 128;
 constexpr int PREC_MAX_M = 96;  // 3 * nper <= 96
 
-template <bool WALL>
+template <bool WALL, bool PER>
 __global__ void __launch_bounds__(PREC_THREADS) prec_build_kernel(int nper, int64_t n, const double* __restrict__ r,
                                                                   const double* __restrict__ q, double a, double s_min,
+                                                                  double Lx, double Ly,
                                                                   double inv8pieta, double* __restrict__ gL,
                                                                   double* __restrict__ gLinv, double* __restrict__ gMinv,
                                                                   double* __restrict__ gMinvK, double* __restrict__ gN,
@@ -58,13 +59,13 @@ __global__ void __launch_bounds__(PREC_THREADS) prec_build_kernel(int nper, int6
     }
     __syncthreads();
     // 1. dense M(pp)
-    const PairConst<double> pc = PairConst<double>::make(a);
+    const PairConst<double> pc = PairConst<double>::make(a, Lx, Ly);
     for (int pr = tid; pr < nper * nper; pr += blockDim.x) {
         const int bi = pr / nper, bj = pr % nper;
         const double* ti = bx + 5 * bi;
         const double* tj = bx + 5 * bj;
         double M[9];
-        pair_block<double, double, WALL>(ti[0] - tj[0], ti[1] - tj[1], ti[2] - tj[2], ti[2], tj[2], pc, M[0], M[1],
+        pair_block_images<double, double, WALL, PER>(ti[0] - tj[0], ti[1] - tj[1], ti[2] - tj[2], ti[2], tj[2], pc, M[0], M[1],
                                          M[2], M[4], M[5], M[6], M[7], M[8]);
         M[3] = M[1];
         const double sc = ti[3] * tj[3] * inv8pieta;
@@ -289,20 +290,25 @@ int precond_build_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, co
     static bool attr = false;
     if (!attr) {
         const int mx = (2 * PREC_MAX_M * PREC_MAX_M + 6 * PREC_MAX_M + 5 * 32) * (int)sizeof(double);
-        RPBD_CU(h, cudaFuncSetAttribute(prec_build_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
-        RPBD_CU(h, cudaFuncSetAttribute(prec_build_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        RPBD_CU(h, cudaFuncSetAttribute(prec_build_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        RPBD_CU(h, cudaFuncSetAttribute(prec_build_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
+        RPBD_CU(h, cudaFuncSetAttribute(prec_build_kernel<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         const int mx2 = (PREC_MAX_M * PREC_MAX_M + 7 * PREC_MAX_M) * (int)sizeof(double);
         RPBD_CU(h, cudaFuncSetAttribute(prec_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx2));
         RPBD_CU(h, cudaFuncSetAttribute(prec_saddle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx2));
         attr = true;
     }
     RPBD_CU(h, cudaMemsetAsync(h->dev_flag, 0, sizeof(int), st));
-    if (h->p.wall)
-        prec_build_kernel<true><<<(unsigned)nb, PREC_THREADS, smem, st>>>(nper, n, r, q, h->p.a, h->p.s_min, inv8pieta,
-                                                                         L, Li, Mi, MK, N, h->dev_flag);
+    const double Lx = h->p.Lx, Ly = h->p.Ly;
+    if (Lx > 0.0)
+        prec_build_kernel<true, true><<<(unsigned)nb, PREC_THREADS, smem, st>>>(nper, n, r, q, h->p.a, h->p.s_min, Lx, Ly,
+                                                                              inv8pieta, L, Li, Mi, MK, N, h->dev_flag);
+    else if (h->p.wall)
+        prec_build_kernel<true, false><<<(unsigned)nb, PREC_THREADS, smem, st>>>(nper, n, r, q, h->p.a, h->p.s_min, Lx,
+                                                                               Ly, inv8pieta, L, Li, Mi, MK, N, h->dev_flag);
     else
-        prec_build_kernel<false><<<(unsigned)nb, PREC_THREADS, smem, st>>>(nper, n, r, q, h->p.a, h->p.s_min,
-                                                                          inv8pieta, L, Li, Mi, MK, N, h->dev_flag);
+        prec_build_kernel<false, false><<<(unsigned)nb, PREC_THREADS, smem, st>>>(nper, n, r, q, h->p.a, h->p.s_min, Lx,
+                                                                                Ly, inv8pieta, L, Li, Mi, MK, N, h->dev_flag);
     count_launch();
     RPBD_LAUNCH_CHECK(h);
     h->prec_nb = nb;

@@ -148,7 +148,7 @@ __device__ __forceinline__ void load_rec(const float* rj, float& xh, float& yh, 
     for (int q = 0; q < 3 * K; ++q) f[q] = tail[1 + q];
 }
 
-template <int K, bool WALL, int UNR, int MINB>
+template <int K, bool WALL, bool PER, int UNR, int MINB>
 __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__ rec, int64_t n, int64_t n_pad,
                                                  const SymItem* __restrict__ items, int n_home_tiles, PairConst<float> pc,
                                                  float* __restrict__ partial, int* __restrict__ err_flag)
@@ -195,7 +195,7 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
                 load_rec<K>(st + jj * LEN, xh, yh, xl, yl, zj, f);
                 const float dx = (hxh - xh) + (hxl - xl), dy = (hyh - yh) + (hyl - yl);
                 float Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz;
-                pair_block<float, float, WALL>(dx, dy, hz - zj, hz, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
+                pair_block_images<float, float, WALL, PER>(dx, dy, hz - zj, hz, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
 #pragma unroll
                 for (int m = 0; m < K; ++m) {
                     const float fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
                 load_rec<K>(st + v * LEN, xh, yh, xl, yl, zj, f);
                 const float dx = (hxh - xh) + (hxl - xl), dy = (hyh - yh) + (hyl - yl);
                 float Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz;
-                pair_block<float, float, WALL>(dx, dy, hz - zj, hz, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
+                pair_block_images<float, float, WALL, PER>(dx, dy, hz - zj, hz, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
 #pragma unroll
                 for (int m = 0; m < K; ++m) {
                     const float fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
@@ -331,7 +331,7 @@ static int get_items(rpbd_handle* h, int64_t n, int64_t n_pad, SymItem** d_items
     return RPBD_OK;
 }
 
-template <int K, bool WALL, class In, class Out>
+template <int K, bool WALL, bool PER, class In, class Out>
 static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
 {
     constexpr int LEN = Rec<K>::LEN;
@@ -349,15 +349,15 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
                                                                         h->p.s_min, rec, scale);
     count_launch();
     const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
-    const PairConst<float> pc = PairConst<float>::make(h->p.a);
+    const PairConst<float> pc = PairConst<float>::make(h->p.a, h->p.Lx, h->p.Ly);
     if (h->profile) prof_begin(h, st);
     // variant -1: the measured default per K (k = 1: unroll 4; otherwise unroll 2)
     const int var = h->sym_variant >= 0 ? h->sym_variant : (K == 1 ? 3 : 0);
     switch (var) {  // tuning variants: (visitor-loop unroll, min CTAs per SM), see SymVar
-    case 1: sym_kernel<K, WALL, SymVar<K, 1>::UNR, SymVar<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
-    case 2: sym_kernel<K, WALL, SymVar<K, 2>::UNR, SymVar<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
-    case 3: sym_kernel<K, WALL, SymVar<K, 3>::UNR, SymVar<K, 3>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
-    default: sym_kernel<K, WALL, SymVar<K, 0>::UNR, SymVar<K, 0>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    case 1: sym_kernel<K, WALL, PER, SymVar<K, 1>::UNR, SymVar<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    case 2: sym_kernel<K, WALL, PER, SymVar<K, 2>::UNR, SymVar<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    case 3: sym_kernel<K, WALL, PER, SymVar<K, 3>::UNR, SymVar<K, 3>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    default: sym_kernel<K, WALL, PER, SymVar<K, 0>::UNR, SymVar<K, 0>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
     }
     count_launch();
     if (h->profile) prof_end(h, st, 3 /* symmetric FP32 */, K, (double)n * (double)n);
@@ -371,13 +371,19 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
 
 }  // namespace sym
 
+template <int K, class In, class Out>
+static int sym_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
+{
+    if (h->p.Lx > 0.0) return sym::run<K, true, true>(h, n, r, F, U, k, st);
+    return h->p.wall ? sym::run<K, true, false>(h, n, r, F, U, k, st) : sym::run<K, false, false>(h, n, r, F, U, k, st);
+}
+
 template <class In, class Out>
 static int sym_dispatch(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
 {
-    const bool w = h->p.wall != 0;
-    if (k <= 1) return w ? sym::run<1, true>(h, n, r, F, U, k, st) : sym::run<1, false>(h, n, r, F, U, k, st);
-    if (k <= 2) return w ? sym::run<2, true>(h, n, r, F, U, k, st) : sym::run<2, false>(h, n, r, F, U, k, st);
-    return w ? sym::run<4, true>(h, n, r, F, U, k, st) : sym::run<4, false>(h, n, r, F, U, k, st);
+    if (k <= 1) return sym_k<1>(h, n, r, F, U, k, st);
+    if (k <= 2) return sym_k<2>(h, n, r, F, U, k, st);
+    return sym_k<4>(h, n, r, F, U, k, st);
 }
 
 int sym_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* F, void* U, int k, bool io_double,

@@ -44,9 +44,15 @@ struct PairConst {
     R k_self;    // 4 / (3 a)
     R k_ovl;     // 3 / (8 a^2)
     R inv8a2;    // 1 / (8 a^2)
-    __host__ __device__ static PairConst make(double a)
+    R Lx, Ly;    // pseudo-periodic cell (used by pair_block_images only)
+    R iLx, iLy;  // 1 / Lx, 1 / Ly
+    __host__ __device__ static PairConst make(double a, double Lx = 0.0, double Ly = 0.0)
     {
         PairConst c;
+        c.Lx = R(Lx);
+        c.Ly = R(Ly);
+        c.iLx = R(Lx > 0.0 ? 1.0 / Lx : 0.0);
+        c.iLy = R(Ly > 0.0 ? 1.0 / Ly : 0.0);
         c.a2 = R(a * a);
         c.a23 = R(2.0 * a * a / 3.0);
         c.two_a2 = R(2.0 * a * a);
@@ -135,6 +141,36 @@ __device__ __forceinline__ void pair_block(T dx, T dy, T dz, T zi, T zj, const P
     Mzx = dx * gz;
     Mzy = dy * gz;
     Mzz = alpha + c2 * dz * dz + b3 * Rz * Rz + (cR + dR) * Rz + E * Rinv;
+}
+
+__device__ __forceinline__ float rint_(float x) { return rintf(x); }
+__device__ __forceinline__ double rint_(double x) { return rint(x); }
+
+// Pseudo-periodic pair block (Sec. 4.2): the separation is reduced to the
+// minimum image in x and y, and that image plus its 8 nearest periodic
+// images are summed.  PER = false is the plain block.  The self block arises
+// from the unshifted image of i = j (zero separation).
+template <class T, class K, bool WALL, bool PER>
+__device__ __forceinline__ void pair_block_images(T dx, T dy, T dz, T zi, T zj, const PairConst<K>& c, T& Mxx, T& Mxy,
+                                                  T& Mxz, T& Myy, T& Myz, T& Mzx, T& Mzy, T& Mzz)
+{
+    if (!PER) {
+        pair_block<T, K, WALL>(dx, dy, dz, zi, zj, c, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
+        return;
+    }
+    dx = dx - c.Lx * K(rint_(val_(dx) * c.iLx));
+    dy = dy - c.Ly * K(rint_(val_(dy) * c.iLy));
+    Mxx = Mxy = Mxz = Myy = Myz = Mzx = Mzy = Mzz = T(K(0));
+#pragma unroll
+    for (int a = -1; a <= 1; ++a) {
+#pragma unroll
+        for (int b = -1; b <= 1; ++b) {
+            T xx, xy, xz, yy, yz, zx, zy, zz;
+            pair_block<T, K, WALL>(dx + K(a) * c.Lx, dy + K(b) * c.Ly, dz, zi, zj, c, xx, xy, xz, yy, yz, zx, zy, zz);
+            Mxx = Mxx + xx; Mxy = Mxy + xy; Mxz = Mxz + xz; Myy = Myy + yy;
+            Myz = Myz + yz; Mzx = Mzx + zx; Mzy = Mzy + zy; Mzz = Mzz + zz;
+        }
+    }
 }
 
 // Forward-mode dual number with NP partials (device), scalar S (float or double).
