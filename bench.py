@@ -37,7 +37,7 @@ F_GEOM = 116                 # algorithmic flops of one pair block (FMA = 2), se
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/pair_kernel_f32_k*_boomerangs_65535.md); None when not captured
-NCU_TRAFFIC = {"f32_k16": 20269312 + 342761728, "f32sym_k1": 2672640 + 154834944}
+NCU_TRAFFIC = {"f32_k16": 20269312 + 342761728, "f32sym_k1": 158624512}
 
 
 def f_pair(k, symmetric=False):
