@@ -273,6 +273,22 @@ int rpbd_step_emt(rpbd_handle* h, int64_t nb, int nper, const double* shape, dou
                   double* theta, const rpbd_forces* forces, const rpbd_step_params* sp,
                   rpbd_stats* stats /* host, 3 entries */, void* stream);
 
+/* One Euler-Maruyama RFD step (Algorithm 3, App. A): mobility problems with
+ * random force W^FT at Q+- = Q +- delta/2 [L_p W^f; W^tau], Lanczos, one solve
+ * at Q^n, Q^{n+1} = Q^n + dt (U^n + (U+ - U-)/delta).  Random draws as EM-T
+ * (sid 2 for (W^f, W^tau), sid 1 for W).  stats (host, 4 entries): solve at
+ * Q+, solve at Q-, Lanczos, solve at Q^n. */
+int rpbd_step_emrfd(rpbd_handle* h, int64_t nb, int nper, const double* shape, double* q,
+                    double* theta, const rpbd_forces* forces, const rpbd_step_params* sp,
+                    rpbd_stats* stats /* host, 4 entries */, void* stream);
+/* One Trapezoidal Traction step (Sec. 3.2): D^F and D^S as in step 1 of
+ * Algorithm 1 without the U^RFD term, then the predictor-corrector of
+ * Algorithm 2 (corrector slip 2 D^S + ..., force F~ - 2 D^F).  Random draws as
+ * EM-T.  stats (host, 4 entries): RFD solve, Lanczos, predictor, corrector. */
+int rpbd_step_tt(rpbd_handle* h, int64_t nb, int nper, const double* shape, double* q,
+                 double* theta, const rpbd_forces* forces, const rpbd_step_params* sp,
+                 rpbd_stats* stats /* host, 4 entries */, void* stream);
+
 /* Blob forces [3][n] of the force model (gravity + wall repulsion) at r. */
 int rpbd_blob_forces(rpbd_handle* h, int64_t n, const double* r, const rpbd_forces* forces,
                      double* f, void* stream);

@@ -1,7 +1,8 @@
 """Oracle time steps (FP64).  TEST INFRASTRUCTURE.
 
-Algorithm 1 (EM-T, Sec. 3.1) and Algorithm 2 (T-S, Sec. 3.2) written in the
-paper's order and notation.  Random vectors are inputs; the caller draws them
+Algorithm 1 (EM-T, Sec. 3.1), Algorithm 2 (T-S, Sec. 3.2), Algorithm 3
+(EM-RFD, App. A) and the trapezoidal-traction variant T-T (Sec. 3.2) written
+in the paper's order and notation.  Random vectors are inputs; the caller draws them
 (from oracle.philox to match the CUDA library's internal draws).
 
 Solvers: mode="dense" uses the exact Schur solution (eq. sysDense) and the
@@ -141,3 +142,56 @@ def step_emt(q, theta, shape, prm, fm, dt, delta, Lp, Wf, Wt, W, solver: Solver,
     # 4: Euler-Maruyama update
     qn, tn = _displace(q, theta, Un, dt)
     return qn, tn, dict(lamR=lamR, UR=UR, DF=DF, DS=DS, MhW=MhW, Un=Un)
+
+
+def step_emrfd(q, theta, shape, prm, fm, dt, delta, Lp, Wf, Wt, W, solver: Solver, kT):
+    """Algorithm 3 (EM-RFD, App. A): RFD on N with two solves at Q+-."""
+    nper = shape.shape[0]
+    r = rigid.blob_positions(q, theta, shape)
+    # 1a: W^FT = kT [W^f / L_p; W^tau]
+    WFT = kT * np.concatenate([Wf / Lp, Wt], axis=1)
+    # 1b: Q+- = Q +- delta/2 [L_p W^f; W^tau]
+    dQ = np.concatenate([Lp * Wf, Wt], axis=1)
+    qp, tp = _displace(q, theta, dQ, +0.5 * delta)
+    qm, tm = _displace(q, theta, dQ, -0.5 * delta)
+    rp = rigid.blob_positions(qp, tp, shape)
+    rm = rigid.blob_positions(qm, tm, shape)
+    # 1c: two mobility problems with force W^FT
+    _, Up = solver.saddle(rp, qp, nper, prm, None, WFT)
+    _, Um = solver.saddle(rm, qm, nper, prm, None, WFT)
+    # 2: M^{1/2} W
+    MhW = solver.sqrtM(r, q, nper, prm, W)
+    c = np.sqrt(2.0 * kT / dt)
+    # 3: slip c M^{1/2} W, force F^n
+    Fn = body_forces(r, q, nper, fm)
+    _, Un = solver.saddle(r, q, nper, prm, c * MhW, Fn)
+    # 4: Q^{n+1} = Q^n + dt (U^n + (U+ - U-) / delta)
+    qn, tn = _displace(q, theta, Un + (Up - Um) / delta, dt)
+    return qn, tn, dict(Up=Up, Um=Um, MhW=MhW, Un=Un)
+
+
+def step_tt(q, theta, shape, prm, fm, dt, delta, Lp, Wf, Wt, W, solver: Solver, kT):
+    """Trapezoidal Traction (T-T, Sec. 3.2): D^F and D^S as in step 1 of
+    Algorithm 1 without the U^RFD term, then the predictor-corrector of
+    Algorithm 2 (steps 3-6) with those drifts."""
+    nper = shape.shape[0]
+    r = rigid.blob_positions(q, theta, shape)
+    WFT = kT * np.concatenate([Wf / Lp, Wt], axis=1)
+    lamR, UR = solver.saddle(r, q, nper, prm, None, WFT)
+    dQ = np.concatenate([Lp * Wf, Wt], axis=1)
+    qp, tp = _displace(q, theta, dQ, +0.5 * delta)
+    qm, tm = _displace(q, theta, dQ, -0.5 * delta)
+    rp = rigid.blob_positions(qp, tp, shape)
+    rm = rigid.blob_positions(qm, tm, shape)
+    DF = (rigid.KT_apply(rp, qp, lamR, nper) - rigid.KT_apply(rm, qm, lamR, nper)) / delta
+    DS = (mobility.apply(rp, lamR, prm) - mobility.apply(rm, lamR, prm)) / delta
+    MhW = solver.sqrtM(r, q, nper, prm, W)
+    c = np.sqrt(2.0 * kT / dt)
+    Fn = body_forces(r, q, nper, fm)
+    _, Un = solver.saddle(r, q, nper, prm, c * MhW, Fn)
+    qt, tt = _displace(q, theta, Un, dt)
+    rt = rigid.blob_positions(qt, tt, shape)
+    Ft = body_forces(rt, qt, nper, fm)
+    _, Ut = solver.saddle(rt, qt, nper, prm, 2.0 * DS + c * MhW, Ft - 2.0 * DF)
+    qn, tn = _displace(q, theta, 0.5 * (Un + Ut), dt)
+    return qn, tn, dict(DF=DF, DS=DS, MhW=MhW, Un=Un, Ut=Ut)

@@ -61,6 +61,10 @@ SIGNATURES = [
                           C.POINTER(Stats), _P]),
     ("rpbd_step_emt", _I, [_P, _I64, _I, _P, _P, _P, C.POINTER(Forces), C.POINTER(StepParams),
                            C.POINTER(Stats), _P]),
+    ("rpbd_step_emrfd", _I, [_P, _I64, _I, _P, _P, _P, C.POINTER(Forces), C.POINTER(StepParams),
+                             C.POINTER(Stats), _P]),
+    ("rpbd_step_tt", _I, [_P, _I64, _I, _P, _P, _P, C.POINTER(Forces), C.POINTER(StepParams),
+                          C.POINTER(Stats), _P]),
     ("rpbd_blob_forces", _I, [_P, _I64, _P, C.POINTER(Forces), _P, _P]),
     ("rpbd_mobility_apply_batched", _I, [_P, _I, _P, _P, _P, _P, _I, _P]),
     ("rpbd_autotune_batched", _I, [_P, _I, _P, _P, _I, C.POINTER(C.c_double), _P]),

@@ -247,6 +247,12 @@ class Handle:
     def step_emt(self, shape, q, theta, forces, sp):
         return self._step(self.lib.rpbd_step_emt, 3, shape, q, theta, forces, sp)
 
+    def step_emrfd(self, shape, q, theta, forces, sp):
+        return self._step(self.lib.rpbd_step_emrfd, 4, shape, q, theta, forces, sp)
+
+    def step_tt(self, shape, q, theta, forces, sp):
+        return self._step(self.lib.rpbd_step_tt, 4, shape, q, theta, forces, sp)
+
     def blob_forces(self, r, forces: Forces, out=None):
         out = torch.empty_like(r) if out is None else out
         self._check(self.lib.rpbd_blob_forces(self.h, r.shape[1], _ptr(r), C.byref(forces), _ptr(out), _stream()),

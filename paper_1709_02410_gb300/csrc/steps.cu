@@ -1,6 +1,7 @@
-// Random finite difference drift (Sec. 3) and the two time integrators:
-// Euler-Maruyama Traction (Algorithm 1, Sec. 3.1) and Trapezoidal Slip
-// (Algorithm 2, Sec. 3.2).  Every saddle solve is the GMRES of krylov.cu with
+// Random finite difference drift (Sec. 3) and the time integrators:
+// Euler-Maruyama Traction (Algorithm 1, Sec. 3.1), Trapezoidal Slip
+// (Algorithm 2, Sec. 3.2), Euler-Maruyama RFD (Algorithm 3, App. A) and the
+// Trapezoidal Traction variant (Sec. 3.2).  Every saddle solve is the GMRES of krylov.cu with
 // the body-block preconditioner built at the configuration it solves at; the
 // Brownian slip M^{1/2} W is the preconditioned Lanczos of krylov.cu.
 #include <cuda_runtime.h>
@@ -237,6 +238,116 @@ int step_emt_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, dou
     return RPBD_OK;
 }
 
+int step_emrfd_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, double* q, double* theta,
+                    const rpbd_forces* f, const rpbd_step_params* sp, rpbd_stats* stats, cudaStream_t st)
+{
+    RPBD_TRY(check_step_args(h, nb, nper, shape, q, theta, f, sp));
+    const int64_t n = nb * nper;
+    double* base;
+    RPBD_TRY(ensure_t(h, BUF_STEP, StepBufs::count(n, nb), &base));
+    StepBufs B;
+    B.carve(base, n, nb);
+    const double kT = h->p.kT, d = sp->delta, L = sp->Lp;
+    const double c = std::sqrt(2.0 * kT / sp->dt);
+    rpbd_stats dummy[4];
+    rpbd_stats* S = stats ? stats : dummy;
+    launch_blobs(nb, nper, shape, q, theta, B.r, st);
+    RPBD_TRY(check_finite(h, 3 * n, B.r, st));
+    // 1a: W^FT = kT [W^f / L; W^tau], dQ = [L W^f; W^tau]
+    launch_normals(sp->seed, sp->step, 2, 6 * nb, B.Wb, st);
+    launch_normals(sp->seed, sp->step, 1, 3 * n, B.W, st);
+    emt_random_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(nb, B.Wb, kT, L, B.b6a, B.dQ);
+    count_launch();
+    RPBD_LAUNCH_CHECK(h);
+    // 1b: Q+- = Q +- delta/2 dQ
+    launch_advance(nb, q, theta, B.dQ, 0.5 * d, B.qp, B.tp, st);
+    launch_advance(nb, q, theta, B.dQ, -0.5 * d, B.qm, B.tm, st);
+    launch_blobs(nb, nper, shape, B.qp, B.tp, B.rp, st);
+    launch_blobs(nb, nper, shape, B.qm, B.tm, B.rm, st);
+    // 1c: mobility problems with force W^FT at Q+ and Q- (preconditioner built at each)
+    RPBD_TRY(solve(h, nb, nper, B.rp, B.qp, nullptr, B.b6a, B.lam, B.Ut, sp, 1, &S[0], st));
+    RPBD_TRY(solve(h, nb, nper, B.rm, B.qm, nullptr, B.b6a, B.lam, B.b6b, sp, 1, &S[1], st));
+    // (U+ - U-) / delta
+    diff_scale_kernel<<<g1(6 * nb), 256, 0, st>>>(6 * nb, B.Ut, B.b6b, 1.0 / d, B.DF);
+    count_launch();
+    // 2: M^{1/2} W at Q^n
+    RPBD_TRY(precond_build_impl(h, nb, nper, B.r, q, st));
+    {
+        int s = lanczos_impl(h, n, B.r, B.W, B.MhW, sp->tol_lanczos, sp->max_iter_lanczos, sp->dtype, 1, &S[2], st);
+        if (s != RPBD_OK && s != RPBD_NOT_CONVERGED) return s;
+    }
+    // 3: slip c M^{1/2} W, force F^n
+    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, B.fb, B.FT, st));
+    launch_scale_copy(3 * n, c, B.MhW, B.slip, st);
+    RPBD_TRY(solve(h, nb, nper, B.r, q, B.slip, B.FT, B.lam, B.Un, sp, 0, &S[3], st));
+    // 4: Q^{n+1} = Q^n + dt (U^n + (U+ - U-) / delta)
+    launch_axpby(6 * nb, 1.0, B.Un, 1.0, B.DF, B.b6a, st);
+    launch_advance(nb, q, theta, B.b6a, sp->dt, q, theta, st);
+    RPBD_LAUNCH_CHECK(h);
+    for (int i = 0; i < 4; ++i)
+        if (S[i].status != RPBD_OK) return RPBD_NOT_CONVERGED;
+    return RPBD_OK;
+}
+
+int step_tt_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, double* q, double* theta,
+                 const rpbd_forces* f, const rpbd_step_params* sp, rpbd_stats* stats, cudaStream_t st)
+{
+    RPBD_TRY(check_step_args(h, nb, nper, shape, q, theta, f, sp));
+    const int64_t n = nb * nper;
+    double* base;
+    RPBD_TRY(ensure_t(h, BUF_STEP, StepBufs::count(n, nb), &base));
+    StepBufs B;
+    B.carve(base, n, nb);
+    const double kT = h->p.kT, d = sp->delta, L = sp->Lp;
+    const double c = std::sqrt(2.0 * kT / sp->dt);
+    rpbd_stats dummy[4];
+    rpbd_stats* S = stats ? stats : dummy;
+    launch_blobs(nb, nper, shape, q, theta, B.r, st);
+    RPBD_TRY(check_finite(h, 3 * n, B.r, st));
+    // traction RFD as in step 1 of Algorithm 1
+    launch_normals(sp->seed, sp->step, 2, 6 * nb, B.Wb, st);
+    launch_normals(sp->seed, sp->step, 1, 3 * n, B.W, st);
+    emt_random_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(nb, B.Wb, kT, L, B.b6a, B.dQ);
+    count_launch();
+    RPBD_LAUNCH_CHECK(h);
+    RPBD_TRY(solve(h, nb, nper, B.r, q, nullptr, B.b6a, B.lam, B.Un, sp, 1, &S[0], st));
+    launch_advance(nb, q, theta, B.dQ, 0.5 * d, B.qp, B.tp, st);
+    launch_advance(nb, q, theta, B.dQ, -0.5 * d, B.qm, B.tm, st);
+    launch_blobs(nb, nper, shape, B.qp, B.tp, B.rp, st);
+    launch_blobs(nb, nper, shape, B.qm, B.tm, B.rm, st);
+    // D^F and D^S without the U^RFD term (the trapezoidal corrector supplies it)
+    launch_KT(nb, nper, B.rp, B.qp, B.lam, B.b6a, st);
+    launch_KT(nb, nper, B.rm, B.qm, B.lam, B.b6b, st);
+    diff_scale_kernel<<<g1(6 * nb), 256, 0, st>>>(6 * nb, B.b6a, B.b6b, 1.0 / d, B.DF);
+    count_launch();
+    RPBD_TRY(mobility_apply_impl(h, n, B.rp, B.lam, B.t1, 1, sp->dtype, true, st));
+    RPBD_TRY(mobility_apply_impl(h, n, B.rm, B.lam, B.t2, 1, sp->dtype, true, st));
+    diff_scale_kernel<<<g1(3 * n), 256, 0, st>>>(3 * n, B.t1, B.t2, 1.0 / d, B.DS);
+    count_launch();
+    RPBD_LAUNCH_CHECK(h);
+    {
+        int s = lanczos_impl(h, n, B.r, B.W, B.MhW, sp->tol_lanczos, sp->max_iter_lanczos, sp->dtype, 1, &S[1], st);
+        if (s != RPBD_OK && s != RPBD_NOT_CONVERGED) return s;
+    }
+    // predictor, as step 3 of Algorithm 2
+    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, B.fb, B.FT, st));
+    launch_scale_copy(3 * n, c, B.MhW, B.slip, st);
+    RPBD_TRY(solve(h, nb, nper, B.r, q, B.slip, B.FT, B.lam, B.Un, sp, 0, &S[2], st));
+    launch_advance(nb, q, theta, B.Un, sp->dt, B.qt, B.tt, st);
+    launch_blobs(nb, nper, shape, B.qt, B.tt, B.rt, st);
+    // corrector at Q~ with 2 D^S and 2 D^F
+    RPBD_TRY(body_forces(h, nb, nper, B.rt, B.qt, *f, B.fb, B.FT, st));
+    launch_axpby(6 * nb, 1.0, B.FT, -2.0, B.DF, B.FT, st);
+    launch_axpby(3 * n, 2.0, B.DS, c, B.MhW, B.slip, st);
+    RPBD_TRY(solve(h, nb, nper, B.rt, B.qt, B.slip, B.FT, B.lam, B.Ut, sp, 1, &S[3], st));
+    launch_axpby(6 * nb, 0.5, B.Un, 0.5, B.Ut, B.b6a, st);
+    launch_advance(nb, q, theta, B.b6a, sp->dt, q, theta, st);
+    RPBD_LAUNCH_CHECK(h);
+    for (int i = 0; i < 4; ++i)
+        if (S[i].status != RPBD_OK) return RPBD_NOT_CONVERGED;
+    return RPBD_OK;
+}
+
 }  // namespace rpbd
 
 using namespace rpbd;
@@ -266,6 +377,20 @@ int rpbd_step_emt(rpbd_handle* h, int64_t nb, int nper, const double* shape, dou
 {
     if (!h) return RPBD_BAD_ARG;
     return step_emt_impl(h, nb, nper, shape, q, theta, forces, sp, stats, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rpbd_step_emrfd(rpbd_handle* h, int64_t nb, int nper, const double* shape, double* q, double* theta,
+                    const rpbd_forces* forces, const rpbd_step_params* sp, rpbd_stats* stats, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    return step_emrfd_impl(h, nb, nper, shape, q, theta, forces, sp, stats, reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rpbd_step_tt(rpbd_handle* h, int64_t nb, int nper, const double* shape, double* q, double* theta,
+                 const rpbd_forces* forces, const rpbd_step_params* sp, rpbd_stats* stats, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    return step_tt_impl(h, nb, nper, shape, q, theta, forces, sp, stats, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

@@ -23,16 +23,13 @@ def sp(seed=77, step=3, dt=0.01, delta=1e-4, L=1.0):
     return StepParams(dt, delta, L, 1e-12, 1e-12, 300, 60, 80, F64, seed, step)
 
 
-@pytest.mark.parametrize("kind", ["ts", "emt"])
+@pytest.mark.parametrize("kind", ["ts", "emt", "emrfd", "tt"])
 def test_step_matches_oracle(kind):
     s = synth.boomerang_suspension(4, 4.0, 31)
     p = sp()
     h = handle_for(s)
     q, th = to_dev(s.q), to_dev(s.theta)
-    if kind == "ts":
-        stats, status = h.step_ts(to_dev(s.shape), q, th, forces(), p)
-    else:
-        stats, status = h.step_emt(to_dev(s.shape), q, th, forces(), p)
+    stats, status = getattr(h, "step_" + kind)(to_dev(s.shape), q, th, forces(), p)
     assert status == 0, stats
     n = s.n
     W = philox.normals(3 * n, p.seed, p.step, 1).reshape(3, n)
@@ -43,8 +40,9 @@ def test_step_matches_oracle(kind):
                                    synth.KT)
     else:
         Wb = philox.normals(6 * s.nb, p.seed, p.step, 2).reshape(s.nb, 6)
-        qo, tho, _ = steps.step_emt(s.q, s.theta, s.shape, oracle_params(s), FM, p.dt, p.delta, p.Lp, Wb[:, :3],
-                                    Wb[:, 3:], W, sol, synth.KT)
+        fn = {"emt": steps.step_emt, "emrfd": steps.step_emrfd, "tt": steps.step_tt}[kind]
+        qo, tho, _ = fn(s.q, s.theta, s.shape, oracle_params(s), FM, p.dt, p.delta, p.Lp, Wb[:, :3], Wb[:, 3:], W,
+                        sol, synth.KT)
     dq = q.cpu().numpy() - s.q
     np.testing.assert_allclose(q.cpu().numpy(), qo, rtol=0, atol=1e-7 * np.abs(qo - s.q).max() + 1e-12)
     np.testing.assert_allclose(th.cpu().numpy(), tho, rtol=0, atol=1e-7 * np.abs(tho - s.theta).max() + 1e-12)

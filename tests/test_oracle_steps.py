@@ -18,12 +18,17 @@ def two_bodies():
 
 def one_step(kind, s, prm, fm, dt, kT=0.0):
     z3 = np.zeros((3, s.n))
+    zb = np.zeros((s.nb, 3))
     sol = steps.Solver("dense")
+    args = (s.q, s.theta, s.shape, prm, fm, dt, 1e-6, 14.7 * s.a)
     if kind == "ts":
-        q, th, _ = steps.step_ts(s.q, s.theta, s.shape, prm, fm, dt, 1e-6, 14.7 * s.a, z3, z3, sol, kT)
+        q, th, _ = steps.step_ts(*args, z3, z3, sol, kT)
+    elif kind == "emt":
+        q, th, _ = steps.step_emt(*args, zb, zb, z3, sol, kT)
+    elif kind == "emrfd":
+        q, th, _ = steps.step_emrfd(*args, zb, zb, z3, sol, kT)
     else:
-        zb = np.zeros((s.nb, 3))
-        q, th, _ = steps.step_emt(s.q, s.theta, s.shape, prm, fm, dt, 1e-6, 14.7 * s.a, zb, zb, z3, sol, kT)
+        q, th, _ = steps.step_tt(*args, zb, zb, z3, sol, kT)
     return rigid.blob_positions(q, th, s.shape)
 
 
@@ -42,8 +47,14 @@ def test_deterministic_orders():
     ref = {dt: reference(s, prm, fm, dt, 32) for dt in (T, T / 2)}
     e_ts = [np.abs(one_step("ts", s, prm, fm, dt) - ref[dt]).max() for dt in (T, T / 2)]
     e_em = [np.abs(one_step("emt", s, prm, fm, dt) - ref[dt]).max() for dt in (T, T / 2)]
+    e_rfd = [np.abs(one_step("emrfd", s, prm, fm, dt) - ref[dt]).max() for dt in (T, T / 2)]
+    e_tt = [np.abs(one_step("tt", s, prm, fm, dt) - ref[dt]).max() for dt in (T, T / 2)]
     assert 6.5 < e_ts[0] / e_ts[1] < 10.0      # local error O(dt^3)
+    assert 6.5 < e_tt[0] / e_tt[1] < 10.0
     assert 3.4 < e_em[0] / e_em[1] < 4.6       # local error O(dt^2)
+    assert 3.4 < e_rfd[0] / e_rfd[1] < 4.6
+    # deterministically EM-T and EM-RFD are the same Euler rule
+    np.testing.assert_allclose(e_rfd, e_em, rtol=1e-6)
 
 
 def test_first_velocity_is_N_F():
