@@ -14,8 +14,9 @@
 //    running sum of M^T F_i and hands it to lane l - 1 by one shuffle per
 //    component after every step -- after 32 steps every visitor's sum over
 //    the warp's 32 homes is back in lane (visitor index);
-//  * the four warps' visitor sums are added in shared memory and stored as
-//    one partial per (home tile, visitor); home sums are stored per chunk;
+//  * the four warps' visitor sums are added in shared memory (double-
+//    buffered, so one barrier per tile) and stored as one partial per (home
+//    tile, visitor); home sums are stored per chunk;
 //  * pairs inside a home tile (and the self block) are done by a diagonal
 //    item in the plain one-direction form.
 // A reduce kernel adds, for blob i, the visitor partials of every home tile
@@ -157,8 +158,8 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
     constexpr uint32_t TILE_BYTES = VT * LEN * sizeof(float);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* stage = reinterpret_cast<float*>(smem_raw);
-    float* red = reinterpret_cast<float*>(smem_raw + NST * TILE_BYTES);  // [4 warps][VT][3K]
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + NST * TILE_BYTES + 4 * VT * 3 * K * sizeof(float));
+    float* red = reinterpret_cast<float*>(smem_raw + NST * TILE_BYTES);  // [2 buffers][4 warps][VT][3K]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + NST * TILE_BYTES + 2 * 4 * VT * 3 * K * sizeof(float));
     const SymItem it = items[blockIdx.x];
     const bool diag = it.slot == 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -235,26 +236,29 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
             }
             // lane l now holds visitor l's sum over this warp's homes
 #pragma unroll
-            for (int q = 0; q < 3 * K; ++q) red[(warp * VT + lane) * 3 * K + q] = vacc[q];
-        }
-        if (!diag) {
-            __syncthreads();
-            if (ok) {
-                const int64_t vbase = (int64_t)it.v0 + (int64_t)t * VT;
-                for (int e = tid; e < VT * 3 * K; e += HT) {
-                    const int vl = e / (3 * K), q = e % (3 * K);
-                    const int64_t vg = vbase + vl;
-                    if (vg < n) {
-                        const float sum = red[(0 * VT + vl) * 3 * K + q] + red[(1 * VT + vl) * 3 * K + q] +
-                                          red[(2 * VT + vl) * 3 * K + q] + red[(3 * VT + vl) * 3 * K + q];
-                        partial[((int64_t)it.home * 3 * K + q) * n_pad + vg] = sum;
-                    }
-                }
-            }
+            float* rb = red + (t & 1) * (4 * VT * 3 * K);  // double-buffered: one barrier per tile
+#pragma unroll
+            for (int q = 0; q < 3 * K; ++q) rb[(warp * VT + lane) * 3 * K + q] = vacc[q];
         }
         if (__syncthreads_or(!ok)) {
             bad = true;
             break;
+        }
+        if (!diag) {
+            // add the four warps' visitor sums of this tile; the next tile writes
+            // the other buffer, and the one after that comes only after the
+            // next barrier, which every thread reaches after finishing here
+            const float* rb = red + (t & 1) * (4 * VT * 3 * K);
+            const int64_t vbase = (int64_t)it.v0 + (int64_t)t * VT;
+            for (int e = tid; e < VT * 3 * K; e += HT) {
+                const int vl = e / (3 * K), q = e % (3 * K);
+                const int64_t vg = vbase + vl;
+                if (vg < n) {
+                    const float sum = rb[(0 * VT + vl) * 3 * K + q] + rb[(1 * VT + vl) * 3 * K + q] +
+                                      rb[(2 * VT + vl) * 3 * K + q] + rb[(3 * VT + vl) * 3 * K + q];
+                    partial[((int64_t)it.home * 3 * K + q) * n_pad + vg] = sum;
+                }
+            }
         }
         if (tid == 0 && t + NST < it.ntile) {
             fence_proxy_async();
@@ -348,7 +352,7 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     pack_kernel<K, In><<<(unsigned)((n_pad + 255) / 256), 256, 0, st>>>(n, n_pad, k, r, F, h->p.a, h->p.wall,
                                                                         h->p.s_min, rec, scale);
     count_launch();
-    const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
+    const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 2 * 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
     const PairConst<float> pc = PairConst<float>::make(h->p.a, h->p.Lx, h->p.Ly);
     if (h->profile) prof_begin(h, st);
     // variant -1: the measured default per K (k = 1: unroll 4; otherwise unroll 2)
