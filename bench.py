@@ -37,13 +37,19 @@ F_GEOM = 116                 # algorithmic flops of one pair block (FMA = 2), se
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/pair_kernel_f32_k*_boomerangs_65535.md); None when not captured
-NCU_TRAFFIC = {"f32_k16": 20269312 + 342761728, "f32sym_k1": 158624512}
+NCU_TRAFFIC = {"f32_k16": 20269312 + 342761728, "f32symf_k1": 158856704}
 
 
-def f_pair(k, symmetric=False):
+F_ASSEMBLY = 12             # flops of forming the 9 entries from the block's 5 scalars
+
+
+def f_pair(k, symmetric=False, factored=False):
     """Algorithmic flops per ordered pair: one block (F_GEOM) and 9 FMA per
-    right-hand side; the symmetric kernel forms one block per unordered pair."""
-    return (F_GEOM / 2 if symmetric else F_GEOM) + 18 * k
+    right-hand side; the symmetric kernel forms one block per unordered pair;
+    the factored form skips assembling the 9 entries (still 18 flops per
+    right-hand side)."""
+    g = F_GEOM - (F_ASSEMBLY if factored else 0)
+    return (g / 2 if symmetric else g) + 18 * k
 
 
 def parse():
@@ -195,7 +201,7 @@ def run_ours(args, rank, world, local):
     t_local = sum(ms_steps) / 1e3
     # per-variant pair-kernel time from the library's own events
     prof = {}
-    for dt, name in ((1, "f32"), (0, "f64"), (3, "f32sym")):
+    for dt, name in ((1, "f32"), (0, "f64"), (3, "f32sym"), (4, "f32symf")):
         for k in (1, 2, 4, 8, 16):
             ms, nl, pr = C.c_double(), C.c_longlong(), C.c_double()
             lib.rpbd_profile_read(h.h, dt, k, C.byref(ms), C.byref(nl), C.byref(pr), 0)
@@ -233,7 +239,7 @@ def run_ours(args, rank, world, local):
     e2e_t = time.perf_counter() - e0
     lib.rpbd_profile_enable(h.h, 0)
     e2e_pairs = 0.0
-    for dt in (1, 0, 3):
+    for dt in (1, 0, 3, 4):
         for k in (1, 2, 4, 8, 16):
             ms, nl, pr = C.c_double(), C.c_longlong(), C.c_double()
             lib.rpbd_profile_read(h.h, dt, k, C.byref(ms), C.byref(nl), C.byref(pr), 0)
@@ -272,7 +278,7 @@ def run_ours(args, rank, world, local):
     extra["f32_k16"] = dict(s_per_launch=t16, pairs_per_s=N * N / t16, matvecs_per_s=K_RHS / t16,
                             tflops=N * N * f_pair(16) / t16 / 1e12)
     extra["f32_k1_symmetric"] = dict(s_per_launch=t32k1, pairs_per_s=N * N / t32k1,
-                                     tflops=N * N * f_pair(1, True) / t32k1 / 1e12)
+                                     tflops=N * N * f_pair(1, True, True) / t32k1 / 1e12)
     h.set_symmetric(False)
     t32k1d = time_launch(lambda: h.mobility_apply(r, F1f, out=U1f), 3)
     h.set_symmetric(True)
@@ -294,12 +300,15 @@ def run_ours(args, rank, world, local):
             name, d = dom
             k = int(name.split("_k")[1])
             sym = name.startswith("f32sym")
+            fac = name.startswith("f32symf")
             avg = d["ms"] / d["launches"] / 1e3
-            flops = d["pairs"] / d["launches"] * f_pair(k, sym)
+            flops = d["pairs"] / d["launches"] * f_pair(k, sym, fac)
             ach = flops / avg / 1e12
             roof = {"bound": "alu", "kernel": f"pair_kernel<{name}>", "achieved": ach, "peak": FP32_PEAK_TFLOPS,
                     "unit": "TFLOP/s", "frac": ach / FP32_PEAK_TFLOPS, "traffic": NCU_TRAFFIC.get(name),
-                    "flops_per_pair": f_pair(k, sym), "avg_launch_ms": avg * 1e3,
+                    "flops_per_pair": f_pair(k, sym, fac), "avg_launch_ms": avg * 1e3,
+                    "one_direction_equivalent_tflops":
+                        d["pairs"] / d["launches"] * f_pair(k) / avg / 1e12,
                     "share_of_step": d["ms"] / (t_local * 1e3)}
         # accuracy vs the FP64 oracle on sampled rows (outside the timed region)
         acc = {}

@@ -320,7 +320,8 @@ long long rpbd_launch_count(void);
 int rpbd_profile_enable(rpbd_handle* h, int on);
 /* Sum of the recorded pair-kernel durations for (kind, k-variant), their
  * launch count and pairs (n^2 per launch); kind: RPBD_F64, RPBD_F32 (one-direction
- * kernel), 2 (batched FP32), 3 (symmetric FP32).  Synchronises the device.  reset
+ * kernel), 2 (batched FP32), 3 (symmetric FP32), 4 (symmetric FP32 applying the
+ * block in factored form: k <= 2, open cell).  Synchronises the device.  reset
  * != 0 drops every record afterwards. */
 int rpbd_profile_read(rpbd_handle* h, int dtype, int k, double* ms, long long* launches, double* pairs,
                       int reset);

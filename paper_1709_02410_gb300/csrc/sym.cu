@@ -164,6 +164,8 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
     const bool diag = it.slot == 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t i = (int64_t)it.home * HT + tid;  // home blob (i < n_pad always)
+    // one or two right-hand sides in an open cell: skip assembling the block
+    constexpr bool FACTORED = K <= 2 && !PER;
 
     if (tid == 0) {
 #pragma unroll
@@ -216,19 +218,43 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
                 float xh, yh, xl, yl, zj, f[3 * K];
                 load_rec<K>(st + v * LEN, xh, yh, xl, yl, zj, f);
                 const float dx = (hxh - xh) + (hxl - xl), dy = (hyh - yh) + (hyl - yl);
-                float Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz;
-                pair_block_images<float, float, WALL, PER>(dx, dy, hz - zj, hz, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
+                if constexpr (FACTORED) {
+                    // apply the block in factored form, both directions (no
+                    // assembly of the 9 entries)
+                    float al, be, gxx, gzz, Mzz;
+                    pair_factors<float, float, WALL>(dx, dy, hz - zj, hz, zj, pc, al, be, gxx, gzz, Mzz);
 #pragma unroll
-                for (int m = 0; m < K; ++m) {
-                    const float fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
-                    acc[3 * m + 0] = fmaf(Mxz, fz, fmaf(Mxy, fy, fmaf(Mxx, fx, acc[3 * m + 0])));
-                    acc[3 * m + 1] = fmaf(Myz, fz, fmaf(Myy, fy, fmaf(Mxy, fx, acc[3 * m + 1])));
-                    acc[3 * m + 2] = fmaf(Mzz, fz, fmaf(Mzy, fy, fmaf(Mzx, fx, acc[3 * m + 2])));
-                    const float gx = hf[3 * m], gy = hf[3 * m + 1], gz = hf[3 * m + 2];
-                    // M^T applied to the home force
-                    vacc[3 * m + 0] = fmaf(Mzx, gz, fmaf(Mxy, gy, fmaf(Mxx, gx, vacc[3 * m + 0])));
-                    vacc[3 * m + 1] = fmaf(Mzy, gz, fmaf(Myy, gy, fmaf(Mxy, gx, vacc[3 * m + 1])));
-                    vacc[3 * m + 2] = fmaf(Mzz, gz, fmaf(Myz, gy, fmaf(Mxz, gx, vacc[3 * m + 2])));
+                    for (int m = 0; m < K; ++m) {
+                        const float fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
+                        const float P = fmaf(dy, fy, dx * fx);
+                        const float Q = fmaf(be, P, gxx * fz);
+                        acc[3 * m + 0] = fmaf(dx, Q, fmaf(al, fx, acc[3 * m + 0]));
+                        acc[3 * m + 1] = fmaf(dy, Q, fmaf(al, fy, acc[3 * m + 1]));
+                        acc[3 * m + 2] = fmaf(Mzz, fz, fmaf(gzz, P, acc[3 * m + 2]));
+                        // M^T applied to the home force
+                        const float hx = hf[3 * m], hy = hf[3 * m + 1], hzf = hf[3 * m + 2];
+                        const float Pt = fmaf(dy, hy, dx * hx);
+                        const float Qt = fmaf(be, Pt, gzz * hzf);
+                        vacc[3 * m + 0] = fmaf(dx, Qt, fmaf(al, hx, vacc[3 * m + 0]));
+                        vacc[3 * m + 1] = fmaf(dy, Qt, fmaf(al, hy, vacc[3 * m + 1]));
+                        vacc[3 * m + 2] = fmaf(Mzz, hzf, fmaf(gxx, Pt, vacc[3 * m + 2]));
+                    }
+                } else {
+                    float Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz;
+                    pair_block_images<float, float, WALL, PER>(dx, dy, hz - zj, hz, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx,
+                                                               Mzy, Mzz);
+#pragma unroll
+                    for (int m = 0; m < K; ++m) {
+                        const float fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
+                        acc[3 * m + 0] = fmaf(Mxz, fz, fmaf(Mxy, fy, fmaf(Mxx, fx, acc[3 * m + 0])));
+                        acc[3 * m + 1] = fmaf(Myz, fz, fmaf(Myy, fy, fmaf(Mxy, fx, acc[3 * m + 1])));
+                        acc[3 * m + 2] = fmaf(Mzz, fz, fmaf(Mzy, fy, fmaf(Mzx, fx, acc[3 * m + 2])));
+                        const float gx = hf[3 * m], gy = hf[3 * m + 1], gz = hf[3 * m + 2];
+                        // M^T applied to the home force
+                        vacc[3 * m + 0] = fmaf(Mzx, gz, fmaf(Mxy, gy, fmaf(Mxx, gx, vacc[3 * m + 0])));
+                        vacc[3 * m + 1] = fmaf(Mzy, gz, fmaf(Myy, gy, fmaf(Mxy, gx, vacc[3 * m + 1])));
+                        vacc[3 * m + 2] = fmaf(Mzz, gz, fmaf(Myz, gy, fmaf(Mxz, gx, vacc[3 * m + 2])));
+                    }
                 }
                 // hand the visitor sums to the lane that takes that visitor next
 #pragma unroll
@@ -364,7 +390,8 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     default: sym_kernel<K, WALL, PER, SymVar<K, 0>::UNR, SymVar<K, 0>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
     }
     count_launch();
-    if (h->profile) prof_end(h, st, 3 /* symmetric FP32 */, K, (double)n * (double)n);
+    if (h->profile) prof_end(h, st, (K <= 2 && !PER) ? 4 /* symmetric, factored */ : 3 /* symmetric */, K,
+                             (double)n * (double)n);
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
     reduce_kernel<float, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_home, CHUNK, partial,
                                                                            scale, inv8pieta, U);

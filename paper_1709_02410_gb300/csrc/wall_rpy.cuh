@@ -69,12 +69,14 @@ __device__ __forceinline__ double rsqrt_(double x) { return rsqrt(x); }
 __device__ __forceinline__ float val_(float x) { return x; }
 __device__ __forceinline__ double val_(double x) { return x; }
 
-// Block entries, 8 pi eta times M_ij.  T is float, double or a dual number;
-// K is the plain scalar type of the constants.
+// The five scalars that determine the block (8 pi eta times M_ij):
+//   M = [[alpha + beta dx^2, beta dx dy, dx gx], [beta dx dy, alpha + beta dy^2, dy gx],
+//        [dx gz, dy gz, Mzz]].
+// T is float, double or a dual number; K is the plain scalar type of the
+// constants.
 template <class T, class K, bool WALL>
-__device__ __forceinline__ void pair_block(T dx, T dy, T dz, T zi, T zj, const PairConst<K>& c,
-                                           T& Mxx, T& Mxy, T& Mxz, T& Myy, T& Myz, T& Mzx,
-                                           T& Mzy, T& Mzz)
+__device__ __forceinline__ void pair_factors(T dx, T dy, T dz, T zi, T zj, const PairConst<K>& c, T& alpha, T& beta,
+                                             T& gx, T& gz, T& Mzz)
 {
     T rho2 = dx * dx + dy * dy;
     T r2 = rho2 + dz * dz;
@@ -96,14 +98,10 @@ __device__ __forceinline__ void pair_block(T dx, T dy, T dz, T zi, T zj, const P
         }
     }
     if (!WALL) {
-        T g = c2 * dz;
-        Mxx = c1 + c2 * dx * dx;
-        Mxy = c2 * dx * dy;
-        Myy = c1 + c2 * dy * dy;
-        Mxz = dx * g;
-        Myz = dy * g;
-        Mzx = Mxz;
-        Mzy = Myz;
+        alpha = c1;
+        beta = c2;
+        gx = c2 * dz;
+        gz = gx;
         Mzz = c1 + c2 * dz * dz;
         return;
     }
@@ -126,13 +124,24 @@ __device__ __forceinline__ void pair_block(T dx, T dy, T dz, T zi, T zj, const P
     T D = K(2) * t - K(20.0 / 3.0) * ez * s4;
     T E = K(-4) * t2 - K(4) * ez2 * s2 + s4 * (K(20) * ez2 - K(8.0 / 3.0));
     T b3 = B * Rinv * Rinv2;
-    T alpha = c1 + A * Rinv;
-    T beta = c2 + b3;
+    alpha = c1 + A * Rinv;
+    beta = c2 + b3;
     T cR = C * Rinv2;
     T dR = D * Rinv2;
     T g0 = c2 * dz + b3 * Rz;
-    T gx = g0 + cR;
-    T gz = g0 + dR;
+    gx = g0 + cR;
+    gz = g0 + dR;
+    Mzz = alpha + c2 * dz * dz + b3 * Rz * Rz + (cR + dR) * Rz + E * Rinv;
+}
+
+// Block entries, 8 pi eta times M_ij (Mxy = Myx).
+template <class T, class K, bool WALL>
+__device__ __forceinline__ void pair_block(T dx, T dy, T dz, T zi, T zj, const PairConst<K>& c,
+                                           T& Mxx, T& Mxy, T& Mxz, T& Myy, T& Myz, T& Mzx,
+                                           T& Mzy, T& Mzz)
+{
+    T alpha, beta, gx, gz;
+    pair_factors<T, K, WALL>(dx, dy, dz, zi, zj, c, alpha, beta, gx, gz, Mzz);
     Mxx = alpha + beta * dx * dx;
     Mxy = beta * dx * dy;
     Myy = alpha + beta * dy * dy;
@@ -140,7 +149,6 @@ __device__ __forceinline__ void pair_block(T dx, T dy, T dz, T zi, T zj, const P
     Myz = dy * gx;
     Mzx = dx * gz;
     Mzy = dy * gz;
-    Mzz = alpha + c2 * dz * dz + b3 * Rz * Rz + (cR + dR) * Rz + E * Rinv;
 }
 
 __device__ __forceinline__ float rint_(float x) { return rintf(x); }
