@@ -288,6 +288,7 @@ def run_ours(args, rank, world, local):
     extra["speedup_f32_k16_vs_f64_k1_per_rhs"] = (t64 * K_RHS) / t16
     extra["speedup_f32_k1_vs_f64_k1"] = t64 / t32k1
 
+    rows = measure_rows(h, r, shape, q0, th0, T, time_launch) if rank == 0 else None
     batched = measure_batched(h.lib, dev, T) if rank == 0 else None
     rollers = measure_rollers(dev, T) if (rank == 0 and not args.no_rollers) else None
 
@@ -358,11 +359,44 @@ def run_ours(args, rank, world, local):
             "autotune_k1": {"choice": tuned[0], "ms_per_launch": tuned[1],
                             "legend": "0: one-direction kernel; 1 + v: symmetric kernel variant v"},
             "matvec": extra,
+            "rows": rows,
             "batched_c4": batched,
             "ts_step_rollers_c3": rollers,
             "accuracy": acc,
             "wall_s_timed": wall,
         }
+    return out
+
+
+# ---------------------------------------------------------------------------
+# every step of the hot path timed alone on the bench suspension
+
+def measure_rows(h, r, shape, q, th, T, time_launch):
+    import torch
+    import paper_1709_02410_gb300 as P
+    from paper_1709_02410_gb300 import synth
+    n = r.shape[1]
+    W = T(synth.gaussian(400, (3, n)))
+    u = T(synth.gaussian(401, (3, n)))
+    FT = T(synth.gaussian(402, (NB, 6)) * 1e-2)
+    out = {}
+    out["a1_blob_geometry_s"] = time_launch(lambda: h.blobs_from_bodies(shape, q, th, out=r), 5)
+    out["a3_precond_build_s"] = time_launch(lambda: h.precond_build(NPER, r, q), 3)
+    st = {}
+
+    def lz():
+        st["l"] = h.lanczos_sqrt_apply(r, W, 1e-4, 80, dtype=P.F32)[1]
+    out["a4_lanczos_tol1e-4_s"] = time_launch(lz, 2)
+    out["a4_lanczos_iterations"] = st["l"]["iterations"]
+
+    def gm():
+        st["g"] = h.gmres_rigid_solve(NPER, r, q, W, FT, tol=1e-6, max_iter=300, restart=100, dtype=P.F32,
+                                      build_precond=False)[2]
+    out["a5_gmres_tol1e-6_s"] = time_launch(gm, 2)
+    out["a5_gmres_iterations"] = st["g"]["iterations"]
+    out["a6_rfd_drift_s"] = time_launch(lambda: h.rfd_drift(r, W, 1e-3, dtype=P.F32), 3)
+    out["a7_adjoint_f32_s"] = time_launch(lambda: h.mobility_adjoint(r, u, W, dtype=P.F32), 1)
+    out["a7_adjoint_f32_pairs_per_s"] = n * n / out["a7_adjoint_f32_s"]
     return out
 
 
