@@ -31,19 +31,38 @@ class ForceModel:
     wall_b: float = 1.0          # Yukawa (Debye) length
     h_floor: float = 0.1         # repulsion evaluated at max(z, h_floor)
     torque: tuple = (0.0, 0.0, 0.0)
+    steric_gamma: float = 0.0    # blob-blob Yukawa between blobs of different bodies
+    steric_b: float = 1.0
+    r_floor: float = 0.1         # blob-blob repulsion evaluated at max(r, r_floor)
+    r_cut: float = 0.0           # pairs farther than r_cut are skipped (0: no cut)
 
 
-def blob_forces(r, fm: ForceModel):
+def blob_forces(r, fm: ForceModel, nper=None):
+    """Per-blob forces (Sec. 4.1): gravity, the Yukawa wall repulsion on the
+    blob height, and (when steric_gamma != 0, nper given) the Yukawa
+    repulsion U = gamma exp(-r/b)/r between blobs of different bodies."""
     f = np.zeros_like(r)
     h = np.maximum(r[2], fm.h_floor)
     if fm.wall_gamma != 0.0:
         f[2] += fm.wall_gamma * np.exp(-h / fm.wall_b) * (1.0 / (fm.wall_b * h) + 1.0 / (h * h))
     f[2] -= fm.weight
+    if fm.steric_gamma != 0.0 and nper is not None:
+        n = r.shape[1]
+        body = np.arange(n) // nper
+        for i in range(n):
+            d = r[:, [i]] - r                      # from every blob j to blob i
+            dist = np.sqrt(np.sum(d * d, axis=0))
+            mask = body != body[i]
+            if fm.r_cut > 0:
+                mask &= dist <= fm.r_cut
+            re = np.maximum(dist[mask], fm.r_floor)
+            mag = fm.steric_gamma * np.exp(-re / fm.steric_b) * (1.0 / (fm.steric_b * re) + 1.0 / (re * re))
+            f[:, i] += np.sum(d[:, mask] / np.maximum(dist[mask], 1e-300) * mag, axis=1)
     return f
 
 
 def body_forces(r, q, nper, fm: ForceModel):
-    FT = rigid.KT_apply(r, q, blob_forces(r, fm), nper)
+    FT = rigid.KT_apply(r, q, blob_forces(r, fm, nper), nper)
     FT[:, 3:] += np.asarray(fm.torque)
     return FT
 

@@ -77,3 +77,30 @@ def test_iterative_matches_dense_step():
     qi, ti, _ = steps.step_ts(*args, steps.Solver("iterative", 1e-12, 1e-12), synth.KT)
     np.testing.assert_allclose(qi, qd, rtol=1e-9, atol=1e-9)
     np.testing.assert_allclose(ti, td, rtol=1e-9, atol=1e-9)
+
+
+def test_steric_forces_are_a_gradient_and_balance():
+    """Blob-blob Yukawa forces: minus the gradient of sum gamma e^{-r/b}/r over
+    pairs of different bodies (central differences), and they sum to zero."""
+    s = synth.boomerang_suspension(3, 2.0, 33)
+    r = rigid.blob_positions(s.q, s.theta, s.shape)
+    fm = steps.ForceModel(steric_gamma=0.096, steric_b=0.162, r_floor=1e-3)
+    f = steps.blob_forces(r, fm, s.nper)
+    body = np.arange(s.n) // s.nper
+
+    def energy(rr):
+        e = 0.0
+        for i in range(s.n):
+            for j in range(i + 1, s.n):
+                if body[i] != body[j]:
+                    d = np.linalg.norm(rr[:, i] - rr[:, j])
+                    e += 0.096 * np.exp(-d / 0.162) / d
+        return e
+    h = 1e-6
+    for i in (0, 7, 20, 44):
+        for c in range(3):
+            rp, rm = r.copy(), r.copy()
+            rp[c, i] += h
+            rm[c, i] -= h
+            assert abs(-(energy(rp) - energy(rm)) / (2 * h) - f[c, i]) < 1e-6 * max(1.0, np.abs(f).max())
+    np.testing.assert_allclose(f.sum(axis=1), 0.0, atol=1e-10 * np.abs(f).max())
