@@ -71,13 +71,19 @@ typedef struct rpbd_stats {
 
 /* Deterministic forces for the time steps (Sec. 4): per-blob gravity -weight z^,
  * blob-wall Yukawa repulsion gamma exp(-h/b)/h evaluated at h = max(z, h_floor),
- * and a constant torque on every body. */
+ * a constant torque on every body, and (steric_gamma != 0) the blob-blob
+ * Yukawa repulsion steric_gamma exp(-r/steric_b)/r between blobs of different
+ * bodies, evaluated at max(r, r_floor) and skipped beyond r_cut (0: no cut). */
 typedef struct rpbd_forces {
     double weight;
     double wall_gamma;
     double wall_b;
     double h_floor;
     double torque[3];
+    double steric_gamma;
+    double steric_b;
+    double r_floor;
+    double r_cut;
 } rpbd_forces;
 
 /* Time-step controls (Algorithms 1 and 2). */
@@ -289,9 +295,13 @@ int rpbd_step_tt(rpbd_handle* h, int64_t nb, int nper, const double* shape, doub
                  double* theta, const rpbd_forces* forces, const rpbd_step_params* sp,
                  rpbd_stats* stats /* host, 4 entries */, void* stream);
 
-/* Blob forces [3][n] of the force model (gravity + wall repulsion) at r. */
-int rpbd_blob_forces(rpbd_handle* h, int64_t n, const double* r, const rpbd_forces* forces,
-                     double* f, void* stream);
+/* Blob forces [3][n] of the force model at r (gravity, wall repulsion and,
+ * with nper > 0 bodies of nper consecutive blobs, the blob-blob repulsion,
+ * an all-pairs O(n^2) sum computed in `dtype` arithmetic from FP64
+ * separations).  BAD_ARG when steric_gamma != 0 and nper does not divide n,
+ * steric_b <= 0 or r_floor <= 0. */
+int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const rpbd_forces* forces,
+                     int dtype, double* f, void* stream);
 
 /* ---- options -------------------------------------------------------------- */
 

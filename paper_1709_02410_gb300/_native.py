@@ -25,7 +25,8 @@ class Stats(C.Structure):
 
 class Forces(C.Structure):
     _fields_ = [("weight", C.c_double), ("wall_gamma", C.c_double), ("wall_b", C.c_double),
-                ("h_floor", C.c_double), ("torque", C.c_double * 3)]
+                ("h_floor", C.c_double), ("torque", C.c_double * 3), ("steric_gamma", C.c_double),
+                ("steric_b", C.c_double), ("r_floor", C.c_double), ("r_cut", C.c_double)]
 
 
 class StepParams(C.Structure):
@@ -65,7 +66,7 @@ SIGNATURES = [
                              C.POINTER(Stats), _P]),
     ("rpbd_step_tt", _I, [_P, _I64, _I, _P, _P, _P, C.POINTER(Forces), C.POINTER(StepParams),
                           C.POINTER(Stats), _P]),
-    ("rpbd_blob_forces", _I, [_P, _I64, _P, C.POINTER(Forces), _P, _P]),
+    ("rpbd_blob_forces", _I, [_P, _I64, _I, _P, C.POINTER(Forces), _I, _P, _P]),
     ("rpbd_mobility_apply_batched", _I, [_P, _I, _P, _P, _P, _P, _I, _P]),
     ("rpbd_autotune_batched", _I, [_P, _I, _P, _P, _I, C.POINTER(C.c_double), _P]),
     ("rpbd_lanczos_sqrt_apply_batched", _I, [_P, _I, _P, _P, _P, _P, _P, _P, _D, _I, _I, _I, _P, _P]),

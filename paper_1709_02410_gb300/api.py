@@ -253,8 +253,8 @@ class Handle:
     def step_tt(self, shape, q, theta, forces, sp):
         return self._step(self.lib.rpbd_step_tt, 4, shape, q, theta, forces, sp)
 
-    def blob_forces(self, r, forces: Forces, out=None):
+    def blob_forces(self, r, forces: Forces, nper=0, dtype=F64, out=None):
         out = torch.empty_like(r) if out is None else out
-        self._check(self.lib.rpbd_blob_forces(self.h, r.shape[1], _ptr(r), C.byref(forces), _ptr(out), _stream()),
-                    "blob_forces")
+        self._check(self.lib.rpbd_blob_forces(self.h, r.shape[1], nper, _ptr(r), C.byref(forces), dtype,
+                                              _ptr(out), _stream()), "blob_forces")
         return out

@@ -304,11 +304,15 @@ int rpbd_philox_normals(rpbd_handle* h, uint64_t seed, uint32_t step, uint32_t s
     return RPBD_OK;
 }
 
-int rpbd_blob_forces(rpbd_handle* h, int64_t n, const double* r, const rpbd_forces* f, double* out, void* stream)
+int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const rpbd_forces* f, int dtype,
+                     double* out, void* stream)
 {
     if (!h) return RPBD_BAD_ARG;
     if (n < 0 || !r || !f || !out) return set_error(h, RPBD_BAD_ARG, "blob_forces: bad arguments");
-    launch_blob_forces(n, r, *f, out, S(stream));
+    if (f->steric_gamma != 0.0 && (nper <= 0 || n % nper != 0 || !(f->steric_b > 0) || !(f->r_floor > 0)))
+        return set_error(h, RPBD_BAD_ARG, "blob_forces: steric forces need nper | n, steric_b > 0, r_floor > 0");
+    if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "blob_forces: bad dtype");
+    launch_blob_forces(n, nper, r, *f, dtype, out, S(stream));
     RPBD_LAUNCH_CHECK(h);
     return RPBD_OK;
 }

@@ -153,10 +153,77 @@ __global__ void blob_forces_kernel(int64_t n, const double* __restrict__ r, rpbd
     out[2 * n + i] = fz;
 }
 
-void launch_blob_forces(int64_t n, const double* r, const rpbd_forces& f, double* out, cudaStream_t st)
+// Blob-blob Yukawa repulsion between blobs of different bodies (Sec. 4.1,
+// U = gamma exp(-r/b)/r), added to out.  Separations are formed in FP64 and
+// the force in T; pairs beyond r_cut (when > 0) are skipped; the force is
+// evaluated at max(r, r_floor).  Sources are staged through shared memory.
+constexpr int STERIC_T = 256;
+__device__ __forceinline__ float steric_exp(float x) { return expf(x); }
+__device__ __forceinline__ double steric_exp(double x) { return exp(x); }
+__device__ __forceinline__ float steric_sqrt(float x) { return sqrtf(x); }
+__device__ __forceinline__ double steric_sqrt(double x) { return sqrt(x); }
+
+template <typename T>
+__global__ void __launch_bounds__(STERIC_T) steric_kernel(int64_t n, int nper, const double* __restrict__ r, T gamma,
+                                                          T b, T rfloor, T rcut2, double* __restrict__ out)
+{
+    __shared__ double sx[STERIC_T], sy[STERIC_T], sz[STERIC_T];
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t ii = i < n ? i : n - 1;
+    const double xi = r[ii], yi = r[n + ii], zi = r[2 * n + ii];
+    const int64_t b0 = (ii / nper) * nper, b1 = b0 + nper;  // own body's blobs
+    const T invb = T(1) / b;
+    T fx = 0, fy = 0, fz = 0;
+    for (int64_t t0 = 0; t0 < n; t0 += STERIC_T) {
+        const int64_t j = t0 + threadIdx.x;
+        if (j < n) {
+            sx[threadIdx.x] = r[j];
+            sy[threadIdx.x] = r[n + j];
+            sz[threadIdx.x] = r[2 * n + j];
+        }
+        __syncthreads();
+        const int cnt = (int)((n - t0) < STERIC_T ? (n - t0) : STERIC_T);
+        for (int jj = 0; jj < cnt; ++jj) {
+            const int64_t jg = t0 + jj;
+            if (jg >= b0 && jg < b1) continue;
+            const T dx = (T)(xi - sx[jj]), dy = (T)(yi - sy[jj]), dz = (T)(zi - sz[jj]);
+            const T r2 = dx * dx + dy * dy + dz * dz;
+            if (rcut2 > T(0) && r2 > rcut2) continue;
+            const T rr = steric_sqrt(r2);
+            const T re = rr > rfloor ? rr : rfloor;
+            const T mag = gamma * steric_exp(-re * invb) * (invb / re + T(1) / (re * re));
+            const T inv = rr > T(0) ? T(1) / rr : T(0);
+            fx += dx * inv * mag;
+            fy += dy * inv * mag;
+            fz += dz * inv * mag;
+        }
+        __syncthreads();
+    }
+    if (i < n) {
+        out[i] += fx;
+        out[n + i] += fy;
+        out[2 * n + i] += fz;
+    }
+}
+
+template <typename T>
+static void launch_steric(int64_t n, int nper, const double* r, const rpbd_forces& f, double* out, cudaStream_t st)
+{
+    const T rc2 = f.r_cut > 0.0 ? (T)(f.r_cut * f.r_cut) : T(0);
+    steric_kernel<T><<<(unsigned)((n + STERIC_T - 1) / STERIC_T), STERIC_T, 0, st>>>(
+        n, nper, r, (T)f.steric_gamma, (T)f.steric_b, (T)f.r_floor, rc2, out);
+    count_launch();
+}
+
+void launch_blob_forces(int64_t n, int nper, const double* r, const rpbd_forces& f, int dtype, double* out,
+                        cudaStream_t st)
 {
     if (n <= 0) return;
     blob_forces_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, r, f, out); count_launch();
+    if (f.steric_gamma != 0.0 && nper > 0) {
+        if (dtype == RPBD_F32) launch_steric<float>(n, nper, r, f, out, st);
+        else launch_steric<double>(n, nper, r, f, out, st);
+    }
 }
 
 // ---------------------------------------------------------------------------

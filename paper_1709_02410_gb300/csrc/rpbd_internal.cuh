@@ -143,7 +143,7 @@ void launch_blobs(int64_t nb, int nper, const double* shape, const double* q,
                   const double* theta, double* r, cudaStream_t st);
 void launch_normals(uint64_t seed, uint32_t step, uint32_t sid, int64_t n, double* out,
                     cudaStream_t st);
-void launch_blob_forces(int64_t n, const double* r, const rpbd_forces& f, double* out,
+void launch_blob_forces(int64_t n, int nper, const double* r, const rpbd_forces& f, int dtype, double* out,
                         cudaStream_t st);
 // q += s * U[:, :3]; theta = Rotate(theta, s * U[:, 3:])
 void launch_advance(int64_t nb, const double* q0, const double* th0, const double* U, double s,

@@ -90,9 +90,9 @@ struct StepBufs {
 };
 
 static int body_forces(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const rpbd_forces& f,
-                       double* fb, double* FT, cudaStream_t st)
+                       int dtype, double* fb, double* FT, cudaStream_t st)
 {
-    launch_blob_forces(nb * nper, r, f, fb, st);
+    launch_blob_forces(nb * nper, nper, r, f, dtype, fb, st);
     launch_KT(nb, nper, r, q, fb, FT, st);
     add_torque_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(nb, f.torque[0], f.torque[1], f.torque[2], FT); count_launch();
     RPBD_LAUNCH_CHECK(h);
@@ -107,6 +107,8 @@ static int check_step_args(rpbd_handle* h, int64_t nb, int nper, const double* s
     if (!(sp->dt > 0) || !(sp->delta > 0) || !(sp->Lp > 0) || !(sp->tol_gmres > 0) || !(sp->tol_lanczos > 0))
         return set_error(h, RPBD_BAD_ARG, "step: dt, delta, Lp and tolerances must be > 0");
     if (sp->dtype != RPBD_F32 && sp->dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "step: bad dtype");
+    if (f->steric_gamma != 0.0 && (!(f->steric_b > 0) || !(f->r_floor > 0)))
+        return set_error(h, RPBD_BAD_ARG, "step: steric forces need steric_b > 0 and r_floor > 0");
     return RPBD_OK;
 }
 
@@ -160,14 +162,14 @@ int step_ts_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, doub
         if (s != RPBD_OK && s != RPBD_NOT_CONVERGED) return s;
     }
     // 3: predictor solve, slip c M^{1/2} W, force F^n
-    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, B.fb, B.FT, st));
+    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, sp->dtype, B.fb, B.FT, st));
     launch_scale_copy(3 * n, c, B.MhW, B.slip, st);
     RPBD_TRY(solve(h, nb, nper, B.r, q, B.slip, B.FT, B.lam, B.Un, sp, 0, &S[2], st));
     // 4: Q~ = Q^n + dt U^n
     launch_advance(nb, q, theta, B.Un, sp->dt, B.qt, B.tt, st);
     launch_blobs(nb, nper, shape, B.qt, B.tt, B.rt, st);
     // 5: corrector at Q~: slip 2 D^S + c M^{1/2} W, force F~ - 2 D^F
-    RPBD_TRY(body_forces(h, nb, nper, B.rt, B.qt, *f, B.fb, B.FT, st));
+    RPBD_TRY(body_forces(h, nb, nper, B.rt, B.qt, *f, sp->dtype, B.fb, B.FT, st));
     launch_axpby(6 * nb, 1.0, B.FT, -2.0, B.DF, B.FT, st);
     launch_axpby(3 * n, 2.0, B.DS, c, B.MhW, B.slip, st);
     RPBD_TRY(solve(h, nb, nper, B.rt, B.qt, B.slip, B.FT, B.lam, B.Ut, sp, 1, &S[3], st));
@@ -226,7 +228,7 @@ int step_emt_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, dou
         if (s != RPBD_OK && s != RPBD_NOT_CONVERGED) return s;
     }
     // 3: slip D^S + c M^{1/2} W, force F^n - D^F
-    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, B.fb, B.FT, st));
+    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, sp->dtype, B.fb, B.FT, st));
     launch_axpby(6 * nb, 1.0, B.FT, -1.0, B.DF, B.FT, st);
     launch_axpby(3 * n, 1.0, B.DS, c, B.MhW, B.slip, st);
     RPBD_TRY(solve(h, nb, nper, B.r, q, B.slip, B.FT, B.lam, B.Un, sp, 0, &S[2], st));
@@ -277,7 +279,7 @@ int step_emrfd_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, d
         if (s != RPBD_OK && s != RPBD_NOT_CONVERGED) return s;
     }
     // 3: slip c M^{1/2} W, force F^n
-    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, B.fb, B.FT, st));
+    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, sp->dtype, B.fb, B.FT, st));
     launch_scale_copy(3 * n, c, B.MhW, B.slip, st);
     RPBD_TRY(solve(h, nb, nper, B.r, q, B.slip, B.FT, B.lam, B.Un, sp, 0, &S[3], st));
     // 4: Q^{n+1} = Q^n + dt (U^n + (U+ - U-) / delta)
@@ -330,13 +332,13 @@ int step_tt_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, doub
         if (s != RPBD_OK && s != RPBD_NOT_CONVERGED) return s;
     }
     // predictor, as step 3 of Algorithm 2
-    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, B.fb, B.FT, st));
+    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, sp->dtype, B.fb, B.FT, st));
     launch_scale_copy(3 * n, c, B.MhW, B.slip, st);
     RPBD_TRY(solve(h, nb, nper, B.r, q, B.slip, B.FT, B.lam, B.Un, sp, 0, &S[2], st));
     launch_advance(nb, q, theta, B.Un, sp->dt, B.qt, B.tt, st);
     launch_blobs(nb, nper, shape, B.qt, B.tt, B.rt, st);
     // corrector at Q~ with 2 D^S and 2 D^F
-    RPBD_TRY(body_forces(h, nb, nper, B.rt, B.qt, *f, B.fb, B.FT, st));
+    RPBD_TRY(body_forces(h, nb, nper, B.rt, B.qt, *f, sp->dtype, B.fb, B.FT, st));
     launch_axpby(6 * nb, 1.0, B.FT, -2.0, B.DF, B.FT, st);
     launch_axpby(3 * n, 2.0, B.DS, c, B.MhW, B.slip, st);
     RPBD_TRY(solve(h, nb, nper, B.rt, B.qt, B.slip, B.FT, B.lam, B.Ut, sp, 1, &S[3], st));
