@@ -397,6 +397,10 @@ def measure_rows(h, r, shape, q, th, T, time_launch):
     out["a6_rfd_drift_s"] = time_launch(lambda: h.rfd_drift(r, W, 1e-3, dtype=P.F32), 3)
     out["a7_adjoint_f32_s"] = time_launch(lambda: h.mobility_adjoint(r, u, W, dtype=P.F32), 1)
     out["a7_adjoint_f32_pairs_per_s"] = n * n / out["a7_adjoint_f32_s"]
+    # blob forces with the blob-blob Yukawa repulsion of Sec. 4.1 (gamma = 0.096, b = 0.162 um), no cut-off
+    fst = P.Forces(1.57e-11 * 9.81e6, 0.096, 0.162, 0.1, (0.0, 0.0, 0.0), 0.096, 0.162, 0.1, 0.0)
+    fb = torch.empty_like(r)
+    out["f4_steric_forces_f32_s"] = time_launch(lambda: h.blob_forces(r, fst, nper=NPER, dtype=P.F32, out=fb), 3)
     return out
 
 

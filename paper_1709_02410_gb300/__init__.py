@@ -7,3 +7,4 @@ in csrc/).  This package is a thin binding: torch tensors supply device
 memory and streams, and every call goes straight to the library.
 """
 from .api import Handle, RpbdError, F32, F64  # noqa: F401
+from ._native import Forces, StepParams  # noqa: F401

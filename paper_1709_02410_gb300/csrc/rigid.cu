@@ -10,6 +10,8 @@
 //  - Philox4x32-10 (Salmon et al., SC'11) + Box-Muller normals
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "rpbd_internal.cuh"
 
 namespace rpbd {
@@ -154,48 +156,75 @@ __global__ void blob_forces_kernel(int64_t n, const double* __restrict__ r, rpbd
 }
 
 // Blob-blob Yukawa repulsion between blobs of different bodies (Sec. 4.1,
-// U = gamma exp(-r/b)/r), added to out.  Separations are formed in FP64 and
-// the force in T; pairs beyond r_cut (when > 0) are skipped; the force is
-// evaluated at max(r, r_floor).  Sources are staged through shared memory.
+// U = gamma exp(-r/b)/r), added to out.  The force is evaluated at
+// max(r, r_floor); pairs beyond r_cut (when > 0) and coincident blobs are
+// skipped.  One thread per target blob; source tiles are staged through shared
+// memory.  FP64: FP64 throughout.  FP32: positions split into hi + lo floats
+// so separations keep FP64-level accuracy (as in the pair kernels), force in
+// FP32 with one rsqrt and one exp per pair.
 constexpr int STERIC_T = 256;
-__device__ __forceinline__ float steric_exp(float x) { return expf(x); }
-__device__ __forceinline__ double steric_exp(double x) { return exp(x); }
-__device__ __forceinline__ float steric_sqrt(float x) { return sqrtf(x); }
-__device__ __forceinline__ double steric_sqrt(double x) { return sqrt(x); }
 
 template <typename T>
 __global__ void __launch_bounds__(STERIC_T) steric_kernel(int64_t n, int nper, const double* __restrict__ r, T gamma,
                                                           T b, T rfloor, T rcut2, double* __restrict__ out)
 {
-    __shared__ double sx[STERIC_T], sy[STERIC_T], sz[STERIC_T];
+    constexpr bool F32 = std::is_same<T, float>::value;
+    constexpr int NS = F32 ? 6 : 3;  // per-source components staged
+    __shared__ T sm[NS][STERIC_T];
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t ii = i < n ? i : n - 1;
-    const double xi = r[ii], yi = r[n + ii], zi = r[2 * n + ii];
+    T ti[NS];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const double v = r[c * n + ii];
+        ti[c] = (T)v;
+        if constexpr (F32) ti[3 + c] = (float)(v - (double)ti[c]);
+    }
     const int64_t b0 = (ii / nper) * nper, b1 = b0 + nper;  // own body's blobs
-    const T invb = T(1) / b;
+    const T invb = T(1) / b, ifl = T(1) / rfloor;
+    const T rfl2 = rfloor * rfloor;
     T fx = 0, fy = 0, fz = 0;
     for (int64_t t0 = 0; t0 < n; t0 += STERIC_T) {
         const int64_t j = t0 + threadIdx.x;
         if (j < n) {
-            sx[threadIdx.x] = r[j];
-            sy[threadIdx.x] = r[n + j];
-            sz[threadIdx.x] = r[2 * n + j];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const double v = r[c * n + j];
+                const T h = (T)v;
+                sm[c][threadIdx.x] = h;
+                if constexpr (F32) sm[3 + c][threadIdx.x] = (float)(v - (double)h);
+            }
         }
         __syncthreads();
         const int cnt = (int)((n - t0) < STERIC_T ? (n - t0) : STERIC_T);
         for (int jj = 0; jj < cnt; ++jj) {
             const int64_t jg = t0 + jj;
             if (jg >= b0 && jg < b1) continue;
-            const T dx = (T)(xi - sx[jj]), dy = (T)(yi - sy[jj]), dz = (T)(zi - sz[jj]);
+            T dx = ti[0] - sm[0][jj], dy = ti[1] - sm[1][jj], dz = ti[2] - sm[2][jj];
+            if constexpr (F32) {
+                dx += ti[3] - sm[3][jj];
+                dy += ti[4] - sm[4][jj];
+                dz += ti[5] - sm[5][jj];
+            }
             const T r2 = dx * dx + dy * dy + dz * dz;
-            if (rcut2 > T(0) && r2 > rcut2) continue;
-            const T rr = steric_sqrt(r2);
-            const T re = rr > rfloor ? rr : rfloor;
-            const T mag = gamma * steric_exp(-re * invb) * (invb / re + T(1) / (re * re));
-            const T inv = rr > T(0) ? T(1) / rr : T(0);
-            fx += dx * inv * mag;
-            fy += dy * inv * mag;
-            fz += dz * inv * mag;
+            if ((rcut2 > T(0) && r2 > rcut2) || !(r2 > T(0))) continue;
+            T inv, rr;
+            if constexpr (F32) {
+                inv = rsqrtf(r2);
+                rr = r2 * inv;
+            } else {
+                rr = sqrt(r2);
+                inv = 1.0 / rr;
+            }
+            const bool fl = r2 < rfl2;
+            const T re = fl ? rfloor : rr, ire = fl ? ifl : inv;
+            T e;
+            if constexpr (F32) e = expf(-re * invb);
+            else e = exp(-re * invb);
+            const T c = gamma * e * ire * (invb + ire) * inv;
+            fx += dx * c;
+            fy += dy * c;
+            fz += dz * c;
         }
         __syncthreads();
     }
