@@ -288,7 +288,7 @@ def run_ours(args, rank, world, local):
     extra["speedup_f32_k16_vs_f64_k1_per_rhs"] = (t64 * K_RHS) / t16
     extra["speedup_f32_k1_vs_f64_k1"] = t64 / t32k1
 
-    rows = measure_rows(h, r, shape, q0, th0, T, time_launch) if rank == 0 else None
+    row_times = measure_rows(h, r, shape, q0, th0, T, time_launch) if rank == 0 else None
     batched = measure_batched(h.lib, dev, T) if rank == 0 else None
     rollers = measure_rollers(dev, T) if (rank == 0 and not args.no_rollers) else None
 
@@ -346,7 +346,8 @@ def run_ours(args, rank, world, local):
             "config": {"workload": "boomerangs_65535: 4369 L-bodies x 15 blobs, T-S step + k=16 FP32 batch",
                        "n_blobs": N, "n_bodies": NB, "k_rhs": K_RHS, "gmres_tol": 1e-6, "gmres_restart": 100,
                        "lanczos_tol": 1e-4,
-                       "rfd_delta": 1e-3, "l2": "flushed (256 MB write) before every timed step",
+                       "rfd_delta": 1e-3, "gmres_x0": "corrector starts from the predictor's solution",
+                       "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "steps_per_s": args.steps / t_max * world,
             "e2e": {"value": e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -359,7 +360,7 @@ def run_ours(args, rank, world, local):
             "autotune_k1": {"choice": tuned[0], "ms_per_launch": tuned[1],
                             "legend": "0: one-direction kernel; 1 + v: symmetric kernel variant v"},
             "matvec": extra,
-            "rows": rows,
+            "rows": row_times,
             "batched_c4": batched,
             "ts_step_rollers_c3": rollers,
             "accuracy": acc,

@@ -99,6 +99,10 @@ typedef struct rpbd_step_params {
     int dtype;          /* RPBD_F32 or RPBD_F64 pair arithmetic */
     uint64_t seed;      /* Philox key */
     uint32_t step;      /* step counter (Philox counter word 1) */
+    int cold_start;     /* 0 (default): a solve that follows one with a nearby operator and
+                           right-hand side (T-S / T-T corrector after the predictor, EM-RFD
+                           solve at Q- after Q+) starts GMRES from that solution; 1: every
+                           solve starts from zero */
 } rpbd_step_params;
 
 /* ---- handle ------------------------------------------------------------ */
@@ -208,11 +212,14 @@ int rpbd_lanczos_sqrt_apply(rpbd_handle* h, int64_t n, const double* r, const do
  * restarted GMRES with the body-block preconditioner built on the same r, q
  * (built here when build_precond != 0).  slip [3][n] or NULL (zero); FT
  * [nb][6] or NULL (zero); lambda [3][n] and U [nb][6] outputs.  Stops on
- * the relative residual |b - A x|/|b| <= tol. */
+ * the relative residual |b - A x|/|b| <= tol.  warm_start != 0: lambda and U
+ * hold the initial guess x0 on entry (the stopping test is still relative to
+ * |b|); otherwise x0 = 0 and their contents are ignored. */
 int rpbd_gmres_rigid_solve(rpbd_handle* h, int64_t nb, int nper, const double* r,
                            const double* q, const double* slip, const double* FT,
                            double* lambda, double* U, double tol, int max_iter, int restart,
-                           int dtype, int build_precond, rpbd_stats* stats, void* stream);
+                           int dtype, int build_precond, int warm_start, rpbd_stats* stats,
+                           void* stream);
 
 /* ---- a6: random finite difference drift (Sec. 3, eq. RFDcenter) -------- */
 

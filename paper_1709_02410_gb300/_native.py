@@ -32,7 +32,8 @@ class Forces(C.Structure):
 class StepParams(C.Structure):
     _fields_ = [("dt", C.c_double), ("delta", C.c_double), ("Lp", C.c_double), ("tol_gmres", C.c_double),
                 ("tol_lanczos", C.c_double), ("max_iter_gmres", C.c_int), ("restart", C.c_int),
-                ("max_iter_lanczos", C.c_int), ("dtype", C.c_int), ("seed", C.c_uint64), ("step", C.c_uint32)]
+                ("max_iter_lanczos", C.c_int), ("dtype", C.c_int), ("seed", C.c_uint64), ("step", C.c_uint32),
+                ("cold_start", C.c_int)]
 
 
 # (name, restype, argtypes)
@@ -54,7 +55,7 @@ SIGNATURES = [
     ("rpbd_precond_build", _I, [_P, _I64, _I, _P, _P, _P]),
     ("rpbd_precond_apply", _I, [_P, _I, _P, _P, _P]),
     ("rpbd_lanczos_sqrt_apply", _I, [_P, _I64, _P, _P, _P, _D, _I, _I, _I, C.POINTER(Stats), _P]),
-    ("rpbd_gmres_rigid_solve", _I, [_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _I, _I, _I,
+    ("rpbd_gmres_rigid_solve", _I, [_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _I, _I, _I, _I,
                                     C.POINTER(Stats), _P]),
     ("rpbd_rfd_drift", _I, [_P, _I64, _P, _P, _D, _P, _I, _P]),
     ("rpbd_philox_normals", _I, [_P, _U64, _U32, _U32, _I64, _P, _P]),

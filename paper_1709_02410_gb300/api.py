@@ -165,15 +165,19 @@ class Handle:
 
     # ---- a5
     def gmres_rigid_solve(self, nper, r, q, slip=None, FT=None, tol=1e-6, max_iter=200, restart=50, dtype=F64,
-                          build_precond=True):
+                          build_precond=True, x0=None):
+        """x0 = (lambda0, U0): initial guess (GMRES warm start); default zero."""
         nb = q.shape[0]
         n = nb * nper
-        lam = torch.empty((3, n), dtype=torch.float64, device=r.device)
-        U = torch.empty((nb, 6), dtype=torch.float64, device=r.device)
+        if x0 is None:
+            lam = torch.empty((3, n), dtype=torch.float64, device=r.device)
+            U = torch.empty((nb, 6), dtype=torch.float64, device=r.device)
+        else:
+            lam, U = x0[0].clone(), x0[1].clone()
         st = Stats()
         s = self.lib.rpbd_gmres_rigid_solve(self.h, nb, nper, _ptr(r), _ptr(q), _ptr(slip), _ptr(FT), _ptr(lam),
                                             _ptr(U), tol, max_iter, restart, dtype, int(bool(build_precond)),
-                                            C.byref(st), _stream())
+                                            int(x0 is not None), C.byref(st), _stream())
         if s not in (0, -4):
             self._check(s, "gmres_rigid_solve")
         return lam, U, st.as_dict()

@@ -460,7 +460,7 @@ struct SaddleOp {
 
 int gmres_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* slip,
                const double* FT, double* lambda, double* U, double tol, int max_iter, int restart, int dtype,
-               int build_precond, rpbd_stats* stats, cudaStream_t st)
+               int build_precond, int warm, rpbd_stats* stats, cudaStream_t st)
 {
     if (nb <= 0 || nper <= 0) return set_error(h, RPBD_BAD_ARG, "gmres: no bodies");
     if (restart < 1 || restart > 200 || max_iter < 1) return set_error(h, RPBD_BAD_ARG, "gmres: bad restart/max_iter");
@@ -486,14 +486,23 @@ int gmres_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const doub
     else RPBD_CU(h, cudaMemsetAsync(b, 0, sizeof(double) * 3 * n, st));
     if (FT) launch_scale_copy(6 * nb, -1.0, FT, b + 3 * n, st);
     else RPBD_CU(h, cudaMemsetAsync(b + 3 * n, 0, sizeof(double) * 6 * nb, st));
-    RPBD_CU(h, cudaMemsetAsync(x, 0, sizeof(double) * len, st));
     SaddleOp A{h, nb, n, nper, r, q, dtype, st};
     const unsigned g = vgrid(len);
+    bool first = true;
+    if (warm) {
+        // x0 = [lambda; U] as given; |b| is the scale of the stopping test, as for x0 = 0
+        RPBD_CU(h, cudaMemcpyAsync(x, lambda, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
+        RPBD_CU(h, cudaMemcpyAsync(x + 3 * n, U, sizeof(double) * 6 * nb, cudaMemcpyDeviceToDevice, st));
+        RPBD_TRY(multidot(h, len, b, 0, 1, b, &sc[0], 0, S.partial(), st));
+        gmres_start_kernel<<<1, 1, 0, st>>>(mdim, &sc[0], S.g(), &sc[1], 1, &sc[2]); count_launch();
+        first = false;
+    } else {
+        RPBD_CU(h, cudaMemsetAsync(x, 0, sizeof(double) * len, st));
+    }
     int total = 0, matvecs = 0, status = RPBD_NOT_CONVERGED;
     double res = 1.0;
-    bool first = true;
     for (;;) {
-        // r0 = b - A x  (x = 0 on the first cycle)
+        // r0 = b - A x  (x = 0 on a cold first cycle)
         if (first) {
             launch_scale_copy(len, 1.0, b, w, st);
         } else {
@@ -510,6 +519,7 @@ int gmres_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const doub
             double bn;
             RPBD_TRY(read_scalar(h, &sc[1], &bn, st));
             if (!(bn > 0.0)) {  // zero right-hand side: zero solution
+                if (warm) RPBD_CU(h, cudaMemsetAsync(x, 0, sizeof(double) * len, st));
                 status = RPBD_OK;
                 res = 0.0;
                 break;
@@ -572,14 +582,14 @@ int rpbd_lanczos_sqrt_apply(rpbd_handle* h, int64_t n, const double* r, const do
 
 int rpbd_gmres_rigid_solve(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* slip,
                            const double* FT, double* lambda, double* U, double tol, int max_iter, int restart,
-                           int dtype, int build_precond, rpbd_stats* stats, void* stream)
+                           int dtype, int build_precond, int warm_start, rpbd_stats* stats, void* stream)
 {
     if (!h) return RPBD_BAD_ARG;
     if (!r || !q || !lambda || !U) return set_error(h, RPBD_BAD_ARG, "gmres: null pointer");
     if (!(tol > 0)) return set_error(h, RPBD_BAD_ARG, "gmres: tol must be > 0");
     if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "gmres: bad dtype");
-    return gmres_impl(h, nb, nper, r, q, slip, FT, lambda, U, tol, max_iter, restart, dtype, build_precond, stats,
-                      reinterpret_cast<cudaStream_t>(stream));
+    return gmres_impl(h, nb, nper, r, q, slip, FT, lambda, U, tol, max_iter, restart, dtype, build_precond,
+                      warm_start ? 1 : 0, stats, reinterpret_cast<cudaStream_t>(stream));
 }
 
 }  // extern "C"

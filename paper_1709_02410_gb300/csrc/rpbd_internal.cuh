@@ -165,7 +165,7 @@ int lanczos_impl(rpbd_handle* h, int64_t n, const double* r, const double* W, do
                  cudaStream_t st);
 int gmres_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q,
                const double* slip, const double* FT, double* lambda, double* U, double tol,
-               int max_iter, int restart, int dtype, int build_precond, rpbd_stats* stats,
+               int max_iter, int restart, int dtype, int build_precond, int warm, rpbd_stats* stats,
                cudaStream_t st);
 int precond_build_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q,
                        cudaStream_t st);

@@ -112,12 +112,18 @@ static int check_step_args(rpbd_handle* h, int64_t nb, int nper, const double* s
     return RPBD_OK;
 }
 
+// Saddle solve of a step.  warm_from (when not null and warm starts are on)
+// holds the body velocities of an earlier solve whose blob tractions are
+// still in lam; that solution is the initial guess.
 static int solve(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* slip,
                  const double* FT, double* lam, double* U, const rpbd_step_params* sp, int build, rpbd_stats* stt,
-                 cudaStream_t st)
+                 cudaStream_t st, const double* warm_from = nullptr)
 {
+    const int warm = (warm_from && !sp->cold_start) ? 1 : 0;
+    if (warm && warm_from != U)
+        RPBD_CU(h, cudaMemcpyAsync(U, warm_from, sizeof(double) * 6 * nb, cudaMemcpyDeviceToDevice, st));
     int s = gmres_impl(h, nb, nper, r, q, slip, FT, lam, U, sp->tol_gmres, sp->max_iter_gmres, sp->restart, sp->dtype,
-                       build, stt, st);
+                       build, warm, stt, st);
     return (s == RPBD_NOT_CONVERGED) ? RPBD_OK : s;  // reported through stats
 }
 
@@ -172,7 +178,7 @@ int step_ts_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, doub
     RPBD_TRY(body_forces(h, nb, nper, B.rt, B.qt, *f, sp->dtype, B.fb, B.FT, st));
     launch_axpby(6 * nb, 1.0, B.FT, -2.0, B.DF, B.FT, st);
     launch_axpby(3 * n, 2.0, B.DS, c, B.MhW, B.slip, st);
-    RPBD_TRY(solve(h, nb, nper, B.rt, B.qt, B.slip, B.FT, B.lam, B.Ut, sp, 1, &S[3], st));
+    RPBD_TRY(solve(h, nb, nper, B.rt, B.qt, B.slip, B.FT, B.lam, B.Ut, sp, 1, &S[3], st, B.Un));
     // 6: Q^{n+1} = Q^n + dt/2 (U^n + U~)
     launch_axpby(6 * nb, 0.5, B.Un, 0.5, B.Ut, B.b6a, st);
     launch_advance(nb, q, theta, B.b6a, sp->dt, q, theta, st);
@@ -268,7 +274,7 @@ int step_emrfd_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, d
     launch_blobs(nb, nper, shape, B.qm, B.tm, B.rm, st);
     // 1c: mobility problems with force W^FT at Q+ and Q- (preconditioner built at each)
     RPBD_TRY(solve(h, nb, nper, B.rp, B.qp, nullptr, B.b6a, B.lam, B.Ut, sp, 1, &S[0], st));
-    RPBD_TRY(solve(h, nb, nper, B.rm, B.qm, nullptr, B.b6a, B.lam, B.b6b, sp, 1, &S[1], st));
+    RPBD_TRY(solve(h, nb, nper, B.rm, B.qm, nullptr, B.b6a, B.lam, B.b6b, sp, 1, &S[1], st, B.Ut));
     // (U+ - U-) / delta
     diff_scale_kernel<<<g1(6 * nb), 256, 0, st>>>(6 * nb, B.Ut, B.b6b, 1.0 / d, B.DF);
     count_launch();
@@ -341,7 +347,7 @@ int step_tt_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, doub
     RPBD_TRY(body_forces(h, nb, nper, B.rt, B.qt, *f, sp->dtype, B.fb, B.FT, st));
     launch_axpby(6 * nb, 1.0, B.FT, -2.0, B.DF, B.FT, st);
     launch_axpby(3 * n, 2.0, B.DS, c, B.MhW, B.slip, st);
-    RPBD_TRY(solve(h, nb, nper, B.rt, B.qt, B.slip, B.FT, B.lam, B.Ut, sp, 1, &S[3], st));
+    RPBD_TRY(solve(h, nb, nper, B.rt, B.qt, B.slip, B.FT, B.lam, B.Ut, sp, 1, &S[3], st, B.Un));
     launch_axpby(6 * nb, 0.5, B.Un, 0.5, B.Ut, B.b6a, st);
     launch_advance(nb, q, theta, B.b6a, sp->dt, q, theta, st);
     RPBD_LAUNCH_CHECK(h);

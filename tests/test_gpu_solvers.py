@@ -108,6 +108,36 @@ def test_gmres_restarts_and_null_inputs():
     assert float(U0.abs().max()) == 0.0 and st0["iterations"] == 0
 
 
+def test_gmres_warm_start():
+    """Initial guess x0: the stopping test stays relative to |b|, so a start at
+    the converged answer takes no iteration, a start near it takes fewer than
+    a cold start, and the answers agree with the dense Schur solution."""
+    s = small(8, 21)
+    r = positions(s)
+    rng = np.random.default_rng(22)
+    slip = rng.standard_normal((3, s.n))
+    FT = rng.standard_normal((s.nb, 6)) * 1e-2
+    lam_d, U_d, _ = saddle.dense_solution(r, s.q, s.nper, oracle_params(s), slip, FT)
+    h = handle_for(s)
+    args = (s.nper, to_dev(r), to_dev(s.q), to_dev(slip), to_dev(FT))
+    lam, U, st = h.gmres_rigid_solve(*args, tol=1e-10, max_iter=200, restart=30)
+    assert st["status"] == 0 and rel2(U.cpu().numpy(), U_d) <= 1e-8
+    # start at the answer: converged before the first iteration, x0 unchanged
+    lam1, U1, st1 = h.gmres_rigid_solve(*args, tol=1e-8, max_iter=200, restart=30, x0=(lam, U))
+    assert st1["status"] == 0 and st1["iterations"] == 0
+    assert float((U1 - U).abs().max()) == 0.0
+    # start near the answer (1e-4 perturbation): fewer iterations, same answer
+    p_lam = lam * (1 + 1e-4 * to_dev(rng.standard_normal(lam.shape)))
+    p_U = U * (1 + 1e-4 * to_dev(rng.standard_normal(U.shape)))
+    lam2, U2, st2 = h.gmres_rigid_solve(*args, tol=1e-10, max_iter=200, restart=30, x0=(p_lam, p_U))
+    assert st2["status"] == 0 and st2["iterations"] < st["iterations"]
+    assert rel2(U2.cpu().numpy(), U_d) <= 1e-8
+    assert rel2(lam2.cpu().numpy(), lam_d) <= 1e-7
+    # a zero right-hand side still gives zero, whatever x0
+    lam3, U3, st3 = h.gmres_rigid_solve(s.nper, to_dev(r), to_dev(s.q), None, None, tol=1e-8, x0=(lam, U))
+    assert float(U3.abs().max()) == 0.0 and float(lam3.abs().max()) == 0.0
+
+
 def test_gmres_not_converged_reports_status():
     s = small(8, 15)
     r = positions(s)

@@ -19,14 +19,15 @@ def forces():
     return Forces(FM.weight, FM.wall_gamma, FM.wall_b, FM.h_floor, FM.torque)
 
 
-def sp(seed=77, step=3, dt=0.01, delta=1e-4, L=1.0):
-    return StepParams(dt, delta, L, 1e-12, 1e-12, 300, 60, 80, F64, seed, step)
+def sp(seed=77, step=3, dt=0.01, delta=1e-4, L=1.0, cold_start=0):
+    return StepParams(dt, delta, L, 1e-12, 1e-12, 300, 60, 80, F64, seed, step, cold_start)
 
 
+@pytest.mark.parametrize("cold_start", [0, 1])
 @pytest.mark.parametrize("kind", ["ts", "emt", "emrfd", "tt"])
-def test_step_matches_oracle(kind):
+def test_step_matches_oracle(kind, cold_start):
     s = synth.boomerang_suspension(4, 4.0, 31)
-    p = sp()
+    p = sp(cold_start=cold_start)
     h = handle_for(s)
     q, th = to_dev(s.q), to_dev(s.theta)
     stats, status = getattr(h, "step_" + kind)(to_dev(s.shape), q, th, forces(), p)
