@@ -49,7 +49,7 @@ struct Rec {
 template <int K, int V>
 struct SymVar {
     static constexpr int UNR = V == 1 ? 1 : (V == 3 ? 4 : 2);
-    static constexpr int MINB = K == 1 ? (V == 2 ? 10 : 8) : (K == 2 ? (V == 2 ? 8 : 7) : (V == 2 ? 5 : 4));
+    static constexpr int MINB = K == 1 ? (V == 2 ? 9 : 8) : (K == 2 ? (V == 2 ? 8 : 7) : (V == 2 ? 5 : 4));
 };
 
 struct SymItem {
