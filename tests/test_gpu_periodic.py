@@ -51,6 +51,8 @@ def test_periodic_adjoint_and_divergence():
     assert rel2(g, om.grad(r, u, F, prm)) <= 1e-11
     d = h.mobility_divergence(to_dev(r)).cpu().numpy()
     assert rel2(d, om.divergence(r, prm)) <= 1e-10
+    g32 = h.mobility_adjoint(to_dev(r), to_dev(u), to_dev(F), dtype=F32).cpu().numpy()
+    assert rel2(g32, om.grad(r, u, F, prm)) <= 1e-5
 
 
 def test_periodic_gmres():
