@@ -16,6 +16,7 @@
 #include <vector>
 
 #include "rpbd_internal.cuh"
+#include "tridiag_sqrt.cuh"
 
 namespace rpbd {
 
@@ -107,7 +108,7 @@ __global__ void blz_init_kernel(int n_sys, const double* __restrict__ W2, int* _
     }
 }
 
-// one warp per system: alpha_m, beta_m; T^{1/2} e_1 by cyclic Jacobi; stop test
+// one warp per system: alpha_m, beta_m; T^{1/2} e_1 (tridiag_sqrt.cuh); stop test
 __global__ void blz_sqrt_kernel(int m, int max_iter, double tol, int mdim, const double* __restrict__ H,
                                 const double* __restrict__ nrm2, const double* __restrict__ W2,
                                 double* __restrict__ alpha, double* __restrict__ beta, double* __restrict__ c,
@@ -119,8 +120,6 @@ __global__ void blz_sqrt_kernel(int m, int max_iter, double tol, int mdim, const
     const int lane = threadIdx.x;
     if (!active[s]) return;
     const int m1 = m + 1;
-    double* A = sm;
-    double* Q = sm + m1 * m1;
     double* al = alpha + s * mdim;
     double* be = beta + s * mdim;
     if (lane == 0) {
@@ -128,73 +127,15 @@ __global__ void blz_sqrt_kernel(int m, int max_iter, double tol, int mdim, const
         be[m] = sqrt(nrm2[s]);
     }
     __syncwarp();
-    for (int e = lane; e < m1 * m1; e += 32) {
-        const int i = e / m1, j = e % m1;
-        double v = 0.0;
-        if (i == j) v = al[i];
-        else if (j == i + 1) v = be[i];
-        else if (i == j + 1) v = be[j];
-        A[e] = v;
-        Q[e] = (i == j) ? 1.0 : 0.0;
-    }
-    __syncwarp();
-    double fro = 0.0;
-    for (int e = lane; e < m1 * m1; e += 32) fro += A[e] * A[e];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        double offd = 0.0;
-        for (int e = lane; e < m1 * m1; e += 32)
-            if (e / m1 != e % m1) offd += A[e] * A[e];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) offd += __shfl_xor_sync(0xffffffffu, offd, o);
-        if (offd <= 1e-32 * fro) break;
-        for (int p = 0; p < m1 - 1; ++p)
-            for (int q = p + 1; q < m1; ++q) {
-                const double apq = A[p * m1 + q];
-                const double app = A[p * m1 + p], aqq = A[q * m1 + q];
-                if (!(fabs(apq) > 1e-300) || fabs(apq) < 1e-19 * sqrt(fabs(app * aqq))) continue;
-                const double tau = (aqq - app) / (2.0 * apq);
-                const double t = tau != 0.0 ? copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau)) : 1.0;
-                const double cc = 1.0 / sqrt(1.0 + t * t), sn = t * cc;
-                __syncwarp();
-                for (int k = lane; k < m1; k += 32) {
-                    if (k != p && k != q) {
-                        const double akp = A[k * m1 + p], akq = A[k * m1 + q];
-                        const double np = cc * akp - sn * akq, nq = sn * akp + cc * akq;
-                        A[k * m1 + p] = np;
-                        A[p * m1 + k] = np;
-                        A[k * m1 + q] = nq;
-                        A[q * m1 + k] = nq;
-                    }
-                    const double vkp = Q[k * m1 + p], vkq = Q[k * m1 + q];
-                    Q[k * m1 + p] = cc * vkp - sn * vkq;
-                    Q[k * m1 + q] = sn * vkp + cc * vkq;
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    A[p * m1 + p] = app - t * apq;
-                    A[q * m1 + q] = aqq + t * apq;
-                    A[p * m1 + q] = 0.0;
-                    A[q * m1 + p] = 0.0;
-                }
-                __syncwarp();
-            }
-    }
-    __syncwarp();
-    double nc = 0.0, nd = 0.0;
     double* cs = c + s * mdim;
+    tridiag_sqrt_e1(m1, al, be, sm, cs);
+    double nc = 0.0, nd = 0.0;
     double* cp = cprev + s * mdim;
     for (int i = lane; i < m1; i += 32) {
-        double v = 0.0;
-        for (int k = 0; k < m1; ++k) {
-            const double lam = A[k * m1 + k];
-            v += Q[i * m1 + k] * sqrt(lam > 0.0 ? lam : 0.0) * Q[k];
-        }
+        const double v = cs[i];
         const double prev = i < m1 - 1 ? cp[i] : 0.0;
         nc += v * v;
         nd += (v - prev) * (v - prev);
-        cs[i] = v;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -303,7 +244,7 @@ static int blz_body(rpbd_handle* h, int n_sys, const int64_t* off, int64_t n, co
         seg_dot_kernel<<<dim3(n_sys, 1), 256, 0, st>>>(n, B.doff, B.w, 0, B.w, B.nrm2, 1, B.active);
         count_launch();
         const int m1 = m + 1;
-        blz_sqrt_kernel<<<n_sys, 32, 2 * m1 * m1 * sizeof(double), st>>>(m, max_iter, tol, mdim, B.H1, B.nrm2, B.W2,
+        blz_sqrt_kernel<<<n_sys, 32, tridiag_sqrt_smem_doubles(m1) * sizeof(double), st>>>(m, max_iter, tol, mdim, B.H1, B.nrm2, B.W2,
                                                                          B.alpha, B.beta, B.c, B.cprev, B.change,
                                                                          B.active, B.iters);
         count_launch();
@@ -378,7 +319,7 @@ int rpbd_lanczos_sqrt_apply_batched(rpbd_handle* h, int n_sys, const int64_t* of
     static bool attr = false;
     if (!attr) {
         RPBD_CU(h, cudaFuncSetAttribute(blz_sqrt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        2 * BLZ_MAX * BLZ_MAX * (int)sizeof(double)));
+                                        tridiag_sqrt_smem_doubles(BLZ_MAX) * (int)sizeof(double)));
         attr = true;
     }
     BlzBufs B;
