@@ -221,6 +221,19 @@ int rpbd_gmres_rigid_solve(rpbd_handle* h, int64_t nb, int nper, const double* r
                            int dtype, int build_precond, int warm_start, rpbd_stats* stats,
                            void* stream);
 
+/* nsys (1..4) saddle problems at the same r, q (same M, K and preconditioner),
+ * each as in rpbd_gmres_rigid_solve with x0 = 0.  Their GMRES processes are
+ * advanced in lockstep, so each iteration's matvecs go out as one multi-RHS
+ * launch and the residuals come back with one synchronisation.  slip, FT,
+ * lambda and U are HOST arrays of nsys DEVICE pointers (slip[s], FT[s] may be
+ * NULL: zero); stats (host, may be NULL) receives nsys records.  Returns
+ * RPBD_NOT_CONVERGED when any process stopped at max_iter. */
+int rpbd_gmres_rigid_solve_multi(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q,
+                                 int nsys, const double* const* slip, const double* const* FT,
+                                 double* const* lambda, double* const* U, double tol, int max_iter,
+                                 int restart, int dtype, int build_precond, rpbd_stats* stats,
+                                 void* stream);
+
 /* ---- a6: random finite difference drift (Sec. 3, eq. RFDcenter) -------- */
 
 /* drift[3][n] = (1/delta) [M(r + delta/2 W) - M(r - delta/2 W)] W; its mean
@@ -314,16 +327,18 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
 
 /* value != 0 (default): FP32 matvecs with k <= 4 use the symmetric kernel,
  * which forms each unordered pair's block once and applies it both ways
- * (M_ji = M_ij^T, Sec. 2.1); 0: the one-direction kernel for every k. */
+ * (M_ji = M_ij^T, Sec. 2.1); 0: the one-direction kernel for every k.  Sets
+ * every right-hand-side class (see rpbd_autotune). */
 #define RPBD_OPT_SYMMETRIC 1
 /* -1 (default): per-k default; 0..3: loop-unroll / occupancy variant of the
- * symmetric kernel. */
+ * symmetric kernel, for every right-hand-side class. */
 #define RPBD_OPT_SYM_VARIANT 2
 int rpbd_set_option(rpbd_handle* h, int option, int value);
 
 /* Times the FP32 matvec kernels on n blobs at r (k right-hand sides, zero
  * forces): the one-direction kernel and, for k <= 4, every symmetric variant;
- * keeps the fastest in the handle and returns its index (0: one-direction,
+ * keeps the fastest in the handle for k's class (k = 1, k = 2, 3..4; other
+ * classes keep their setting) and returns its index (0: one-direction,
  * 1 + v: symmetric variant v) or a negative status.  *best_ms (host, may be
  * NULL) receives its time per launch.  Synchronises the stream. */
 int rpbd_autotune(rpbd_handle* h, int64_t n, const double* r, int k, double* best_ms, void* stream);

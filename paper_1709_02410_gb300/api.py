@@ -182,6 +182,28 @@ class Handle:
             self._check(s, "gmres_rigid_solve")
         return lam, U, st.as_dict()
 
+    def gmres_rigid_solve_multi(self, nper, r, q, problems, tol=1e-6, max_iter=200, restart=50, dtype=F64,
+                                build_precond=True):
+        """problems: list of 1..4 (slip, FT) pairs (either None) at the same
+        positions; solved in lockstep with shared multi-RHS matvecs.  Returns a
+        list of (lambda, U, stats)."""
+        nb = q.shape[0]
+        n = nb * nper
+        ns = len(problems)
+        outs = [(torch.empty((3, n), dtype=torch.float64, device=r.device),
+                 torch.empty((nb, 6), dtype=torch.float64, device=r.device)) for _ in range(ns)]
+        arr = C.c_void_p * ns
+        slips = arr(*[_ptr(p[0]) for p in problems])
+        fts = arr(*[_ptr(p[1]) for p in problems])
+        lams = arr(*[_ptr(o[0]) for o in outs])
+        us = arr(*[_ptr(o[1]) for o in outs])
+        st = (Stats * ns)()
+        s = self.lib.rpbd_gmres_rigid_solve_multi(self.h, nb, nper, _ptr(r), _ptr(q), ns, slips, fts, lams, us, tol,
+                                                  max_iter, restart, dtype, int(bool(build_precond)), st, _stream())
+        if s not in (0, -4):
+            self._check(s, "gmres_rigid_solve_multi")
+        return [(o[0], o[1], st[i].as_dict()) for i, o in enumerate(outs)]
+
     # ---- a6
     def rfd_drift(self, r, W, delta, dtype=F64, out=None):
         n = r.shape[1]

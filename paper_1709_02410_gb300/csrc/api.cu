@@ -159,10 +159,12 @@ int rpbd_set_option(rpbd_handle* h, int option, int value)
 {
     if (!h) return RPBD_BAD_ARG;
     switch (option) {
-    case RPBD_OPT_SYMMETRIC: h->use_sym = value != 0; return RPBD_OK;
+    case RPBD_OPT_SYMMETRIC:
+        for (int c = 0; c < 3; ++c) h->use_sym[c] = value != 0;
+        return RPBD_OK;
     case RPBD_OPT_SYM_VARIANT:
         if (value < -1 || value > 3) return set_error(h, RPBD_BAD_ARG, "symmetric variant must be -1..3");
-        h->sym_variant = value;
+        for (int c = 0; c < 3; ++c) h->sym_variant[c] = value;
         return RPBD_OK;
     default: return set_error(h, RPBD_BAD_ARG, "unknown option");
     }
@@ -220,9 +222,10 @@ int rpbd_autotune(rpbd_handle* h, int64_t n, const double* r, int k, double* bes
     int best_c = -1;
     const bool prof = h->profile;
     h->profile = false;
+    const int cls = sym_class(k);
     for (int c = -1; c < ncand - 1; ++c) {
-        h->use_sym = c >= 0;
-        if (c >= 0) h->sym_variant = c;
+        h->use_sym[cls] = c >= 0;
+        if (c >= 0) h->sym_variant[cls] = c;
         int s = mobility_apply_impl(h, n, r, F, U, k, RPBD_F32, false, st);
         if (s != RPBD_OK) { h->profile = prof; return s; }
         RPBD_CU(h, cudaEventRecord(e0, st));
@@ -239,8 +242,8 @@ int rpbd_autotune(rpbd_handle* h, int64_t n, const double* r, int k, double* bes
     h->profile = prof;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    h->use_sym = best_c >= 0;
-    h->sym_variant = best_c >= 0 ? best_c : 0;
+    h->use_sym[cls] = best_c >= 0;
+    h->sym_variant[cls] = best_c >= 0 ? best_c : -1;
     if (best_ms) *best_ms = best;
     return best_c + 1;
 }
@@ -312,7 +315,7 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
     if (f->steric_gamma != 0.0 && (nper <= 0 || n % nper != 0 || !(f->steric_b > 0) || !(f->r_floor > 0)))
         return set_error(h, RPBD_BAD_ARG, "blob_forces: steric forces need nper | n, steric_b > 0, r_floor > 0");
     if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "blob_forces: bad dtype");
-    launch_blob_forces(n, nper, r, *f, dtype, out, S(stream));
+    RPBD_TRY(launch_blob_forces(h, n, nper, r, *f, dtype, out, S(stream)));
     RPBD_LAUNCH_CHECK(h);
     return RPBD_OK;
 }

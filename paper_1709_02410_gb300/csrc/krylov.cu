@@ -3,7 +3,7 @@
 //  Lanczos M^{1/2} W (Sec. 2.2): Lanczos on G = L^-1 M L^-T (L the block
 //    Cholesky preconditioner) from v_1 = W/|W| with full (classical, twice)
 //    reorthogonalisation; f(G) W ~ |W| V_m T_m^{1/2} e_1, T_m^{1/2} e_1 from a
-//    one-warp cyclic Jacobi eigendecomposition of the tridiagonal T_m; stop
+//    one-warp (round-robin parallel) Jacobi eigendecomposition of T_m; stop
 //    when |y_m - y_{m-1}| / |y_m| < tol (evaluated in the small space, V is
 //    orthonormal); output L y_m.
 //  GMRES (Sec. 2.1, eq. saddle): right-preconditioned restarted GMRES(m) on
@@ -19,6 +19,7 @@
 #include <cmath>
 
 #include "rpbd_internal.cuh"
+#include "tridiag_sqrt.cuh"
 
 namespace rpbd {
 
@@ -213,82 +214,20 @@ __global__ void lanczos_coef_kernel(int m, const double* __restrict__ h, const d
     beta[m] = sqrt(nrm2[0]);
 }
 
-// One warp: eigendecomposition of the (m+1) x (m+1) tridiagonal T by cyclic
-// Jacobi, c = T^{1/2} e_1, change = |c - [c_prev; 0]| / |c|.
+// One warp: c = T^{1/2} e_1 of the (m+1) x (m+1) tridiagonal T
+// (tridiag_sqrt.cuh), change = |c - [c_prev; 0]| / |c|.
 __global__ void lanczos_sqrt_kernel(int m1, const double* __restrict__ alpha, const double* __restrict__ beta,
                                     double* __restrict__ c, double* __restrict__ c_prev, double* __restrict__ change)
 {
     extern __shared__ double sm[];
-    double* A = sm;            // m1 x m1 row-major
-    double* Q = sm + m1 * m1;  // eigenvectors, columns
     const int lane = threadIdx.x;
-    for (int e = lane; e < m1 * m1; e += 32) {
-        const int i = e / m1, j = e % m1;
-        double v = 0.0;
-        if (i == j) v = alpha[i];
-        else if (j == i + 1) v = beta[i];
-        else if (i == j + 1) v = beta[j];
-        A[e] = v;
-        Q[e] = (i == j) ? 1.0 : 0.0;
-    }
-    __syncwarp();
-    double fro = 0.0;
-    for (int e = lane; e < m1 * m1; e += 32) fro += A[e] * A[e];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) fro += __shfl_xor_sync(0xffffffffu, fro, o);
-    for (int sweep = 0; sweep < 60; ++sweep) {
-        double off = 0.0;
-        for (int e = lane; e < m1 * m1; e += 32) {
-            const int i = e / m1, j = e % m1;
-            if (i != j) off += A[e] * A[e];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) off += __shfl_xor_sync(0xffffffffu, off, o);
-        if (off <= 1e-32 * fro) break;
-        for (int p = 0; p < m1 - 1; ++p)
-            for (int qq = p + 1; qq < m1; ++qq) {
-                const double apq = A[p * m1 + qq];
-                const double app = A[p * m1 + p], aqq = A[qq * m1 + qq];
-                if (!(fabs(apq) > 1e-300) || fabs(apq) < 1e-19 * sqrt(fabs(app * aqq))) continue;
-                const double tau = (aqq - app) / (2.0 * apq);
-                const double t = tau != 0.0 ? copysign(1.0, tau) / (fabs(tau) + sqrt(1.0 + tau * tau)) : 1.0;
-                const double cc = 1.0 / sqrt(1.0 + t * t), s = t * cc;
-                __syncwarp();
-                for (int k = lane; k < m1; k += 32) {
-                    if (k != p && k != qq) {
-                        const double akp = A[k * m1 + p], akq = A[k * m1 + qq];
-                        const double np = cc * akp - s * akq, nq = s * akp + cc * akq;
-                        A[k * m1 + p] = np;
-                        A[p * m1 + k] = np;
-                        A[k * m1 + qq] = nq;
-                        A[qq * m1 + k] = nq;
-                    }
-                    const double vkp = Q[k * m1 + p], vkq = Q[k * m1 + qq];
-                    Q[k * m1 + p] = cc * vkp - s * vkq;
-                    Q[k * m1 + qq] = s * vkp + cc * vkq;
-                }
-                __syncwarp();
-                if (lane == 0) {
-                    A[p * m1 + p] = app - t * apq;
-                    A[qq * m1 + qq] = aqq + t * apq;
-                    A[p * m1 + qq] = 0.0;
-                    A[qq * m1 + p] = 0.0;
-                }
-                __syncwarp();
-            }
-    }
-    __syncwarp();
+    tridiag_sqrt_e1(m1, alpha, beta, sm, c);
     double nc = 0.0, nd = 0.0;
     for (int i = lane; i < m1; i += 32) {
-        double v = 0.0;
-        for (int k = 0; k < m1; ++k) {
-            const double lam = A[k * m1 + k];
-            v += Q[i * m1 + k] * sqrt(lam > 0.0 ? lam : 0.0) * Q[k];  // Q[0 * m1 + k]
-        }
+        const double v = c[i];
         const double prev = i < m1 - 1 ? c_prev[i] : 0.0;
         nc += v * v;
         nd += (v - prev) * (v - prev);
-        c[i] = v;
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -366,7 +305,7 @@ int lanczos_impl(rpbd_handle* h, int64_t n, const double* r, const double* W, do
     static bool attr = false;
     if (!attr) {
         RPBD_CU(h, cudaFuncSetAttribute(lanczos_sqrt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                        2 * LANCZOS_MAX * LANCZOS_MAX * (int)sizeof(double)));
+                                        tridiag_sqrt_smem_doubles(LANCZOS_MAX + 1) * (int)sizeof(double)));
         attr = true;
     }
     RPBD_CU(h, cudaMemsetAsync(h->dev_flag, 0, sizeof(int), st));
@@ -404,7 +343,9 @@ int lanczos_impl(rpbd_handle* h, int64_t n, const double* r, const double* W, do
         RPBD_TRY(multidot(h, len, w, 0, 1, w, &sc[1], 0, S.partial(), st));
         lanczos_coef_kernel<<<1, 1, 0, st>>>(m, S.hcol(), &sc[1], alpha, beta); count_launch();
         const int m1 = m + 1;
-        lanczos_sqrt_kernel<<<1, 32, 2 * m1 * m1 * sizeof(double), st>>>(m1, alpha, beta, cvec, cprev, &sc[2]); count_launch();
+        lanczos_sqrt_kernel<<<1, 32, tridiag_sqrt_smem_doubles(m1) * sizeof(double), st>>>(m1, alpha, beta, cvec, cprev,
+                                                                                           &sc[2]);
+        count_launch();
         normalize_kernel<<<g, 256, 0, st>>>(len, w, &sc[1], V + (int64_t)(m + 1) * len); count_launch();
         RPBD_LAUNCH_CHECK(h);
         double cur[3];
@@ -431,136 +372,226 @@ int lanczos_impl(rpbd_handle* h, int64_t n, const double* r, const double* W, do
 
 // ---------------------------------------------------------------------------
 // GMRES on the saddle system
+//
+// Each GMRES process is a small state machine; a driver advances several
+// processes that share the positions (same M, K and preconditioner) in
+// lockstep, so that their matvecs go out as one multi-RHS launch (k =
+// number of processes needing one), and reads every process's residual with
+// one host synchronisation per iteration.
 
-struct SaddleOp {
-    rpbd_handle* h;
-    int64_t nb, n;
-    int nper;
-    const double* r;
-    const double* q;
-    int dtype;
-    cudaStream_t st;
-    // out = A x: [M lam - K U; -K^T lam]
-    int apply(const double* x, double* out)
-    {
-        const double* lam = x;
-        const double* U = x + 3 * n;
-        RPBD_TRY(mobility_apply_impl(h, n, r, lam, out, 1, dtype, true, st));
-        K_sub_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nb, nper, r, q, U, out); count_launch();
-        launch_KT(nb, nper, r, q, lam, out + 3 * n, st);
-        negate_kernel<<<vgrid(6 * nb), 256, 0, st>>>(6 * nb, out + 3 * n); count_launch();
-        RPBD_LAUNCH_CHECK(h);
-        return RPBD_OK;
-    }
-    int precond(const double* x, double* out)
-    {
-        return precond_saddle_impl(h, x, x + 3 * n, out, out + 3 * n, st);
-    }
+// out = [M lam - K U; -K^T lam] given Mlam = M lam already in out[0:3n]
+static void saddle_finish(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* x,
+                          double* out, cudaStream_t st)
+{
+    const int64_t n = nb * nper;
+    K_sub_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(nb, nper, r, q, x + 3 * n, out); count_launch();
+    launch_KT(nb, nper, r, q, x, out + 3 * n, st);
+    negate_kernel<<<vgrid(6 * nb), 256, 0, st>>>(6 * nb, out + 3 * n); count_launch();
+}
+
+struct GmresProc {
+    GmresProblem pb;
+    double *V, *x, *b, *w, *z, *sc;
+    Small S{nullptr, 0};
+    enum Phase { NEED_RESID, NEED_ARNOLDI, READ_START, READ_ITER, DONE } phase = DONE;
+    int j = 0, total = 0, matvecs = 0, status = RPBD_NOT_CONVERGED;
+    double res = 1.0;
+    const double* req = nullptr;  // vector whose saddle product is wanted
 };
 
-int gmres_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* slip,
-               const double* FT, double* lambda, double* U, double tol, int max_iter, int restart, int dtype,
-               int build_precond, int warm, rpbd_stats* stats, cudaStream_t st)
+int gmres_multi_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, int nsys,
+                     const GmresProblem* probs, int restart, int dtype, int build_precond, rpbd_stats* stats,
+                     cudaStream_t st)
 {
     if (nb <= 0 || nper <= 0) return set_error(h, RPBD_BAD_ARG, "gmres: no bodies");
-    if (restart < 1 || restart > 200 || max_iter < 1) return set_error(h, RPBD_BAD_ARG, "gmres: bad restart/max_iter");
+    if (restart < 1 || restart > 200) return set_error(h, RPBD_BAD_ARG, "gmres: bad restart");
+    if (nsys < 1 || nsys > 4) return set_error(h, RPBD_BAD_ARG, "gmres: 1..4 systems");
+    for (int s = 0; s < nsys; ++s)
+        if (probs[s].max_iter < 1 || !probs[s].lambda || !probs[s].U)
+            return set_error(h, RPBD_BAD_ARG, "gmres: bad max_iter or null output");
     const int64_t n = nb * nper;
     if (build_precond) RPBD_TRY(precond_build_impl(h, nb, nper, r, q, st));
     if (!h->prec_valid || h->prec_nb != nb || h->prec_nper != nper)
         return set_error(h, RPBD_BAD_ARG, "gmres: preconditioner not built for these bodies");
     const int64_t len = 3 * n + 6 * nb;
     const int mdim = restart;
-    double *V, *vec, *sm;
-    RPBD_TRY(ensure_t(h, BUF_KRYLOV, (size_t)(mdim + 1) * len, &V));
-    RPBD_TRY(ensure_t(h, BUF_VEC, (size_t)4 * len, &vec));
-    RPBD_TRY(ensure_t(h, BUF_SMALL, Small::count(mdim), &sm));
-    Small S{sm, mdim};
-    double* x = vec;
-    double* b = vec + len;
-    double* w = vec + 2 * len;
-    double* z = vec + 3 * len;
-    double* sc = S.scal();  // [0] |.|^2, [1] bnorm, [2] residual estimate
-    RPBD_CU(h, cudaMemsetAsync(h->dev_flag, 0, sizeof(int), st));
-    // b = [-slip; -FT]
-    if (slip) launch_scale_copy(3 * n, -1.0, slip, b, st);
-    else RPBD_CU(h, cudaMemsetAsync(b, 0, sizeof(double) * 3 * n, st));
-    if (FT) launch_scale_copy(6 * nb, -1.0, FT, b + 3 * n, st);
-    else RPBD_CU(h, cudaMemsetAsync(b + 3 * n, 0, sizeof(double) * 6 * nb, st));
-    SaddleOp A{h, nb, n, nper, r, q, dtype, st};
+    double *Vall, *vall, *small, *mv = nullptr;
+    RPBD_TRY(ensure_t(h, BUF_KRYLOV, (size_t)nsys * (mdim + 1) * len, &Vall));
+    RPBD_TRY(ensure_t(h, BUF_VEC, (size_t)nsys * 4 * len, &vall));
+    RPBD_TRY(ensure_t(h, BUF_SMALL, (size_t)nsys * Small::count(mdim), &small));
+    if (nsys > 1) RPBD_TRY(ensure_t(h, BUF_GMRES_MV, (size_t)2 * nsys * 3 * n, &mv));
+    GmresProc P[4];
     const unsigned g = vgrid(len);
-    bool first = true;
-    if (warm) {
-        // x0 = [lambda; U] as given; |b| is the scale of the stopping test, as for x0 = 0
-        RPBD_CU(h, cudaMemcpyAsync(x, lambda, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
-        RPBD_CU(h, cudaMemcpyAsync(x + 3 * n, U, sizeof(double) * 6 * nb, cudaMemcpyDeviceToDevice, st));
-        RPBD_TRY(multidot(h, len, b, 0, 1, b, &sc[0], 0, S.partial(), st));
-        gmres_start_kernel<<<1, 1, 0, st>>>(mdim, &sc[0], S.g(), &sc[1], 1, &sc[2]); count_launch();
-        first = false;
-    } else {
-        RPBD_CU(h, cudaMemsetAsync(x, 0, sizeof(double) * len, st));
-    }
-    int total = 0, matvecs = 0, status = RPBD_NOT_CONVERGED;
-    double res = 1.0;
-    for (;;) {
-        // r0 = b - A x  (x = 0 on a cold first cycle)
-        if (first) {
-            launch_scale_copy(len, 1.0, b, w, st);
-        } else {
-            RPBD_TRY(A.apply(x, w));
-            ++matvecs;
-            launch_axpby(len, 1.0, b, -1.0, w, w, st);
-        }
-        RPBD_TRY(multidot(h, len, w, 0, 1, w, &sc[0], 0, S.partial(), st));
-        gmres_start_kernel<<<1, 1, 0, st>>>(mdim, &sc[0], S.g(), &sc[1], first ? 1 : 0, &sc[2]); count_launch();
-        normalize_kernel<<<g, 256, 0, st>>>(len, w, &sc[0], V); count_launch();
+    RPBD_CU(h, cudaMemsetAsync(h->dev_flag, 0, sizeof(int), st));
+
+    // r0 = w: |r0|, g, residual estimate, v_0 (first: |b| = |r0|)
+    auto begin_cycle = [&](GmresProc& p, int first) -> int {
+        RPBD_TRY(multidot(h, len, p.w, 0, 1, p.w, &p.sc[0], 0, p.S.partial(), st));
+        gmres_start_kernel<<<1, 1, 0, st>>>(mdim, &p.sc[0], p.S.g(), &p.sc[1], first, &p.sc[2]); count_launch();
+        normalize_kernel<<<g, 256, 0, st>>>(len, p.w, &p.sc[0], p.V); count_launch();
         RPBD_LAUNCH_CHECK(h);
-        RPBD_TRY(read_scalar(h, &sc[2], &res, st));
-        {
-            double bn;
-            RPBD_TRY(read_scalar(h, &sc[1], &bn, st));
-            if (!(bn > 0.0)) {  // zero right-hand side: zero solution
-                if (warm) RPBD_CU(h, cudaMemsetAsync(x, 0, sizeof(double) * len, st));
-                status = RPBD_OK;
-                res = 0.0;
-                break;
+        p.phase = GmresProc::READ_START;
+        return RPBD_OK;
+    };
+    // x += P^-1 V y over the cycle's jn Arnoldi vectors
+    auto end_cycle = [&](GmresProc& p, int jn) -> int {
+        gmres_backsolve_kernel<<<1, 1, 0, st>>>(jn, mdim, p.S.H(), p.S.g(), p.S.y()); count_launch();
+        lincomb_kernel<<<g, 256, 0, st>>>(len, p.V, len, jn, p.S.y(), 1.0, nullptr, p.w); count_launch();
+        RPBD_TRY(precond_saddle_impl(h, p.w, p.w + 3 * n, p.z, p.z + 3 * n, st));
+        add_kernel<<<g, 256, 0, st>>>(len, p.z, p.x); count_launch();
+        RPBD_LAUNCH_CHECK(h);
+        return RPBD_OK;
+    };
+    auto want_arnoldi = [&](GmresProc& p) -> int {
+        RPBD_TRY(precond_saddle_impl(h, p.V + (int64_t)p.j * len, p.V + (int64_t)p.j * len + 3 * n, p.z, p.z + 3 * n, st));
+        p.req = p.z;
+        p.phase = GmresProc::NEED_ARNOLDI;
+        return RPBD_OK;
+    };
+
+    for (int s = 0; s < nsys; ++s) {
+        GmresProc& p = P[s];
+        p.pb = probs[s];
+        p.V = Vall + (int64_t)s * (mdim + 1) * len;
+        p.x = vall + (int64_t)s * 4 * len;
+        p.b = p.x + len;
+        p.w = p.x + 2 * len;
+        p.z = p.x + 3 * len;
+        p.S = Small{small + (int64_t)s * Small::count(mdim), mdim};
+        p.sc = p.S.scal();  // [0] |.|^2, [1] |b|, [2] residual estimate
+        // b = [-slip; -FT]
+        if (p.pb.slip) launch_scale_copy(3 * n, -1.0, p.pb.slip, p.b, st);
+        else RPBD_CU(h, cudaMemsetAsync(p.b, 0, sizeof(double) * 3 * n, st));
+        if (p.pb.FT) launch_scale_copy(6 * nb, -1.0, p.pb.FT, p.b + 3 * n, st);
+        else RPBD_CU(h, cudaMemsetAsync(p.b + 3 * n, 0, sizeof(double) * 6 * nb, st));
+        if (p.pb.warm) {
+            // x0 = [lambda; U] as given; |b| is the scale of the stopping test, as for x0 = 0
+            RPBD_CU(h, cudaMemcpyAsync(p.x, p.pb.lambda, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
+            RPBD_CU(h, cudaMemcpyAsync(p.x + 3 * n, p.pb.U, sizeof(double) * 6 * nb, cudaMemcpyDeviceToDevice, st));
+            RPBD_TRY(multidot(h, len, p.b, 0, 1, p.b, &p.sc[0], 0, p.S.partial(), st));
+            gmres_start_kernel<<<1, 1, 0, st>>>(mdim, &p.sc[0], p.S.g(), &p.sc[1], 1, &p.sc[2]); count_launch();
+            p.req = p.x;
+            p.phase = GmresProc::NEED_RESID;
+        } else {
+            RPBD_CU(h, cudaMemsetAsync(p.x, 0, sizeof(double) * len, st));
+            launch_scale_copy(len, 1.0, p.b, p.w, st);
+            RPBD_TRY(begin_cycle(p, 1));
+        }
+    }
+
+    for (;;) {
+        // residuals of every process waiting for one: one synchronisation
+        int nread = 0;
+        for (int s = 0; s < nsys; ++s)
+            if (P[s].phase == GmresProc::READ_START || P[s].phase == GmresProc::READ_ITER) {
+                RPBD_CU(h, cudaMemcpyAsync(h->host_small + 2 * s, &P[s].sc[1], 2 * sizeof(double),
+                                           cudaMemcpyDeviceToHost, st));
+                ++nread;
+            }
+        if (nread) RPBD_CU(h, cudaStreamSynchronize(st));
+        for (int s = 0; s < nsys; ++s) {
+            GmresProc& p = P[s];
+            const double bn = h->host_small[2 * s], res = h->host_small[2 * s + 1];
+            if (p.phase == GmresProc::READ_START) {
+                p.res = res;
+                if (!(bn > 0.0)) {  // zero right-hand side: zero solution
+                    RPBD_CU(h, cudaMemsetAsync(p.x, 0, sizeof(double) * len, st));
+                    p.res = 0.0;
+                    p.status = RPBD_OK;
+                    p.phase = GmresProc::DONE;
+                } else if (res <= p.pb.tol) {
+                    p.status = RPBD_OK;
+                    p.phase = GmresProc::DONE;
+                } else if (p.total >= p.pb.max_iter) {
+                    p.phase = GmresProc::DONE;
+                } else {
+                    p.j = 0;
+                    RPBD_TRY(want_arnoldi(p));
+                }
+            } else if (p.phase == GmresProc::READ_ITER) {
+                p.res = res;
+                ++p.total;
+                const int jn = p.j + 1;
+                if (res <= p.pb.tol || jn == mdim || p.total >= p.pb.max_iter) {
+                    RPBD_TRY(end_cycle(p, jn));
+                    if (res <= p.pb.tol) {
+                        p.status = RPBD_OK;
+                        p.phase = GmresProc::DONE;
+                    } else if (p.total >= p.pb.max_iter) {
+                        p.phase = GmresProc::DONE;
+                    } else {
+                        p.req = p.x;  // restart: r0 = b - A x
+                        p.phase = GmresProc::NEED_RESID;
+                    }
+                } else {
+                    p.j = jn;
+                    RPBD_TRY(want_arnoldi(p));
+                }
             }
         }
-        first = false;
-        if (res <= tol) { status = RPBD_OK; break; }
-        if (total >= max_iter) break;
-        int j = 0;
-        for (; j < mdim && total < max_iter; ++j) {
-            const double* vj = V + (int64_t)j * len;
-            RPBD_TRY(A.precond(vj, z));
-            RPBD_TRY(A.apply(z, w));
-            ++matvecs;
-            RPBD_TRY(multidot(h, len, V, len, j + 1, w, S.hcol(), 0, S.partial(), st));
-            multiaxpy_kernel<<<g, 256, 0, st>>>(len, V, len, j + 1, S.hcol(), w); count_launch();
-            RPBD_TRY(multidot(h, len, V, len, j + 1, w, S.y(), 0, S.partial(), st));
-            multiaxpy_kernel<<<g, 256, 0, st>>>(len, V, len, j + 1, S.y(), w); count_launch();
-            add_kernel<<<1, 256, 0, st>>>(j + 1, S.y(), S.hcol()); count_launch();
-            RPBD_TRY(multidot(h, len, w, 0, 1, w, S.hcol() + j + 1, 0, S.partial(), st));
-            normalize_kernel<<<g, 256, 0, st>>>(len, w, S.hcol() + j + 1, V + (int64_t)(j + 1) * len); count_launch();
-            gmres_column_kernel<<<1, 1, 0, st>>>(j, mdim, S.hcol(), S.H(), S.cs(), S.sn(), S.g(), &sc[1], &sc[2]); count_launch();
-            RPBD_LAUNCH_CHECK(h);
-            ++total;
-            RPBD_TRY(read_scalar(h, &sc[2], &res, st));
-            if (res <= tol) { ++j; break; }
+        // one matvec for every process that needs one
+        int act[4], k = 0;
+        for (int s = 0; s < nsys; ++s)
+            if (P[s].phase == GmresProc::NEED_RESID || P[s].phase == GmresProc::NEED_ARNOLDI) act[k++] = s;
+        if (k == 0) break;
+        if (k == 1) {
+            GmresProc& p = P[act[0]];
+            RPBD_TRY(mobility_apply_impl(h, n, r, p.req, p.w, 1, dtype, true, st));
+        } else {
+            double* Fm = mv;
+            double* Um = mv + (int64_t)k * 3 * n;
+            for (int a = 0; a < k; ++a)
+                RPBD_CU(h, cudaMemcpyAsync(Fm + (int64_t)a * 3 * n, P[act[a]].req, sizeof(double) * 3 * n,
+                                           cudaMemcpyDeviceToDevice, st));
+            RPBD_TRY(mobility_apply_impl(h, n, r, Fm, Um, k, dtype, true, st));
+            for (int a = 0; a < k; ++a)
+                RPBD_CU(h, cudaMemcpyAsync(P[act[a]].w, Um + (int64_t)a * 3 * n, sizeof(double) * 3 * n,
+                                           cudaMemcpyDeviceToDevice, st));
         }
-        // x += P^-1 (V y)
-        gmres_backsolve_kernel<<<1, 1, 0, st>>>(j, mdim, S.H(), S.g(), S.y()); count_launch();
-        lincomb_kernel<<<g, 256, 0, st>>>(len, V, len, j, S.y(), 1.0, nullptr, w); count_launch();
-        RPBD_TRY(A.precond(w, z));
-        add_kernel<<<g, 256, 0, st>>>(len, z, x); count_launch();
-        RPBD_LAUNCH_CHECK(h);
-        if (res <= tol) { status = RPBD_OK; break; }
-        if (total >= max_iter) break;
+        for (int a = 0; a < k; ++a) {
+            GmresProc& p = P[act[a]];
+            saddle_finish(h, nb, nper, r, q, p.req, p.w, st);
+            ++p.matvecs;
+            if (p.phase == GmresProc::NEED_RESID) {
+                launch_axpby(len, 1.0, p.b, -1.0, p.w, p.w, st);
+                RPBD_TRY(begin_cycle(p, 0));
+            } else {
+                // Arnoldi: classical Gram-Schmidt twice, Givens, residual estimate
+                const int j = p.j;
+                RPBD_TRY(multidot(h, len, p.V, len, j + 1, p.w, p.S.hcol(), 0, p.S.partial(), st));
+                multiaxpy_kernel<<<g, 256, 0, st>>>(len, p.V, len, j + 1, p.S.hcol(), p.w); count_launch();
+                RPBD_TRY(multidot(h, len, p.V, len, j + 1, p.w, p.S.y(), 0, p.S.partial(), st));
+                multiaxpy_kernel<<<g, 256, 0, st>>>(len, p.V, len, j + 1, p.S.y(), p.w); count_launch();
+                add_kernel<<<1, 256, 0, st>>>(j + 1, p.S.y(), p.S.hcol()); count_launch();
+                RPBD_TRY(multidot(h, len, p.w, 0, 1, p.w, p.S.hcol() + j + 1, 0, p.S.partial(), st));
+                normalize_kernel<<<g, 256, 0, st>>>(len, p.w, p.S.hcol() + j + 1, p.V + (int64_t)(j + 1) * len);
+                count_launch();
+                gmres_column_kernel<<<1, 1, 0, st>>>(j, mdim, p.S.hcol(), p.S.H(), p.S.cs(), p.S.sn(), p.S.g(),
+                                                      &p.sc[1], &p.sc[2]);
+                count_launch();
+                RPBD_LAUNCH_CHECK(h);
+                p.phase = GmresProc::READ_ITER;
+            }
+        }
     }
     RPBD_TRY(check_flag(h, st));
-    RPBD_CU(h, cudaMemcpyAsync(lambda, x, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
-    RPBD_CU(h, cudaMemcpyAsync(U, x + 3 * n, sizeof(double) * 6 * nb, cudaMemcpyDeviceToDevice, st));
-    if (stats) *stats = rpbd_stats{total, matvecs + total, res, status};
-    return status == RPBD_OK ? RPBD_OK : RPBD_NOT_CONVERGED;
+    bool all_ok = true;
+    for (int s = 0; s < nsys; ++s) {
+        GmresProc& p = P[s];
+        RPBD_CU(h, cudaMemcpyAsync(p.pb.lambda, p.x, sizeof(double) * 3 * n, cudaMemcpyDeviceToDevice, st));
+        RPBD_CU(h, cudaMemcpyAsync(p.pb.U, p.x + 3 * n, sizeof(double) * 6 * nb, cudaMemcpyDeviceToDevice, st));
+        if (stats) stats[s] = rpbd_stats{p.total, p.matvecs, p.res, p.status};
+        all_ok = all_ok && p.status == RPBD_OK;
+    }
+    return all_ok ? RPBD_OK : RPBD_NOT_CONVERGED;
+}
+
+int gmres_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* slip,
+               const double* FT, double* lambda, double* U, double tol, int max_iter, int restart, int dtype,
+               int build_precond, int warm, rpbd_stats* stats, cudaStream_t st)
+{
+    const GmresProblem pb{slip, FT, lambda, U, tol, max_iter, warm};
+    return gmres_multi_impl(h, nb, nper, r, q, 1, &pb, restart, dtype, build_precond, stats, st);
 }
 
 }  // namespace rpbd
@@ -578,6 +609,25 @@ int rpbd_lanczos_sqrt_apply(rpbd_handle* h, int64_t n, const double* r, const do
     if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "lanczos: bad dtype");
     return lanczos_impl(h, n, r, W, out, tol, max_iter, dtype, use_precond, stats,
                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rpbd_gmres_rigid_solve_multi(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, int nsys,
+                                 const double* const* slip, const double* const* FT, double* const* lambda,
+                                 double* const* U, double tol, int max_iter, int restart, int dtype,
+                                 int build_precond, rpbd_stats* stats, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (!r || !q || nsys < 1 || nsys > 4 || !slip || !FT || !lambda || !U)
+        return set_error(h, RPBD_BAD_ARG, "gmres_multi: bad arguments");
+    if (!(tol > 0)) return set_error(h, RPBD_BAD_ARG, "gmres_multi: tol must be > 0");
+    if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "gmres_multi: bad dtype");
+    GmresProblem pb[4];
+    for (int s = 0; s < nsys; ++s) {
+        if (!lambda[s] || !U[s]) return set_error(h, RPBD_BAD_ARG, "gmres_multi: null output");
+        pb[s] = GmresProblem{slip[s], FT[s], lambda[s], U[s], tol, max_iter, 0};
+    }
+    return gmres_multi_impl(h, nb, nper, r, q, nsys, pb, restart, dtype, build_precond, stats,
+                            reinterpret_cast<cudaStream_t>(stream));
 }
 
 int rpbd_gmres_rigid_solve(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* slip,

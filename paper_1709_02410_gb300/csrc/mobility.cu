@@ -421,7 +421,7 @@ int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* 
     if (k < 1 || k > 16) return set_error(h, RPBD_BAD_ARG, "k must be in 1..16");
     if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "bad dtype");
     if (!r || !F || !U) return set_error(h, RPBD_BAD_ARG, "null pointer");
-    if (dtype == RPBD_F32 && k <= 4 && h->use_sym) return sym_apply_impl(h, n, r, F, U, k, io_double, st);
+    if (dtype == RPBD_F32 && k <= 4 && h->use_sym[sym_class(k)]) return sym_apply_impl(h, n, r, F, U, k, io_double, st);
     if (io_double || dtype == RPBD_F64)
         return apply_typed<double, double>(h, n, r, (const double*)F, (double*)U, k, dtype, st);
     return apply_typed<float, float>(h, n, r, (const float*)F, (float*)U, k, dtype, st);

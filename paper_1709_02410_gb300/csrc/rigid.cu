@@ -158,101 +158,144 @@ __global__ void blob_forces_kernel(int64_t n, const double* __restrict__ r, rpbd
 // Blob-blob Yukawa repulsion between blobs of different bodies (Sec. 4.1,
 // U = gamma exp(-r/b)/r), added to out.  The force is evaluated at
 // max(r, r_floor); pairs beyond r_cut (when > 0) and coincident blobs are
-// skipped.  One thread per target blob; source tiles are staged through shared
-// memory.  FP64: FP64 throughout.  FP32: positions split into hi + lo floats
-// so separations keep FP64-level accuracy (as in the pair kernels), force in
-// FP32 with one rsqrt and one exp per pair.
+// skipped.  One thread per target blob, sources split into chunks of
+// STERIC_CH (grid.y) so small suspensions still fill the GPU; each chunk's
+// sum goes to its own partial and a second kernel adds the chunks in a fixed
+// order (deterministic).  Source tiles are staged through shared memory.
+// FP64: FP64 throughout.  FP32: positions split into hi + lo floats so
+// separations keep FP64-level accuracy (as in the pair kernels), force in
+// FP32 with one rsqrt and one fast exp (__expf) per pair.
 constexpr int STERIC_T = 256;
+constexpr int STERIC_CH = 2048;
+
+// force on the target from one source at separation (dx, dy, dz), r2 = |d|^2
+template <typename T>
+__device__ __forceinline__ void steric_pair(T dx, T dy, T dz, T gamma, T invb, T rfloor, T ifl, T rfl2, T rcut2,
+                                            T& fx, T& fy, T& fz)
+{
+    const T r2 = dx * dx + dy * dy + dz * dz;
+    if ((rcut2 > T(0) && r2 > rcut2) || !(r2 > T(0))) return;
+    T inv, rr, e;
+    const bool fl = r2 < rfl2;
+    if constexpr (std::is_same<T, float>::value) {
+        inv = rsqrtf(r2);
+        rr = r2 * inv;
+        e = __expf(-(fl ? rfloor : rr) * invb);
+    } else {
+        rr = sqrt(r2);
+        inv = 1.0 / rr;
+        e = exp(-(fl ? rfloor : rr) * invb);
+    }
+    const T ire = fl ? ifl : inv;
+    const T c = gamma * e * ire * (invb + ire) * inv;
+    fx += dx * c;
+    fy += dy * c;
+    fz += dz * c;
+}
 
 template <typename T>
 __global__ void __launch_bounds__(STERIC_T) steric_kernel(int64_t n, int nper, const double* __restrict__ r, T gamma,
-                                                          T b, T rfloor, T rcut2, double* __restrict__ out)
+                                                          T b, T rfloor, T rcut2, T* __restrict__ part)
 {
     constexpr bool F32 = std::is_same<T, float>::value;
-    constexpr int NS = F32 ? 6 : 3;  // per-source components staged
-    __shared__ T sm[NS][STERIC_T];
+    // FP32: (x, y, z) hi and lo parts as two float4 per source; FP64: (x, y, z, 0)
+    using V4 = typename std::conditional<F32, float4, double4>::type;
+    __shared__ V4 sh[STERIC_T];
+    __shared__ float4 sl[F32 ? STERIC_T : 1];
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t ii = i < n ? i : n - 1;
-    T ti[NS];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const double v = r[c * n + ii];
-        ti[c] = (T)v;
-        if constexpr (F32) ti[3 + c] = (float)(v - (double)ti[c]);
-    }
+    const double xi = r[ii], yi = r[n + ii], zi = r[2 * n + ii];
+    const T txh = (T)xi, tyh = (T)yi, tzh = (T)zi;
+    const float txl = F32 ? (float)(xi - (double)txh) : 0.0f, tyl = F32 ? (float)(yi - (double)tyh) : 0.0f,
+                tzl = F32 ? (float)(zi - (double)tzh) : 0.0f;
     const int64_t b0 = (ii / nper) * nper, b1 = b0 + nper;  // own body's blobs
     const T invb = T(1) / b, ifl = T(1) / rfloor;
     const T rfl2 = rfloor * rfloor;
     T fx = 0, fy = 0, fz = 0;
-    for (int64_t t0 = 0; t0 < n; t0 += STERIC_T) {
+    const int64_t j0 = (int64_t)blockIdx.y * STERIC_CH;
+    const int64_t j1 = (j0 + STERIC_CH) < n ? (j0 + STERIC_CH) : n;
+    for (int64_t t0 = j0; t0 < j1; t0 += STERIC_T) {
         const int64_t j = t0 + threadIdx.x;
-        if (j < n) {
-#pragma unroll
-            for (int c = 0; c < 3; ++c) {
-                const double v = r[c * n + j];
-                const T h = (T)v;
-                sm[c][threadIdx.x] = h;
-                if constexpr (F32) sm[3 + c][threadIdx.x] = (float)(v - (double)h);
-            }
+        if (j < j1) {
+            const double x = r[j], y = r[n + j], z = r[2 * n + j];
+            V4 hv;
+            hv.x = (T)x;
+            hv.y = (T)y;
+            hv.z = (T)z;
+            hv.w = T(0);
+            sh[threadIdx.x] = hv;
+            if constexpr (F32)
+                sl[threadIdx.x] = make_float4((float)(x - (double)hv.x), (float)(y - (double)hv.y),
+                                              (float)(z - (double)hv.z), 0.0f);
         }
         __syncthreads();
-        const int cnt = (int)((n - t0) < STERIC_T ? (n - t0) : STERIC_T);
+        const int cnt = (int)((j1 - t0) < STERIC_T ? (j1 - t0) : STERIC_T);
+        // own-body sources of this tile: [lo, hi) in tile indices
+        const int64_t lo64 = b0 - t0, hi64 = b1 - t0;
+        const int lo = (int)(lo64 < 0 ? 0 : (lo64 > cnt ? cnt : lo64));
+        const int hi = (int)(hi64 < 0 ? 0 : (hi64 > cnt ? cnt : hi64));
         for (int jj = 0; jj < cnt; ++jj) {
-            const int64_t jg = t0 + jj;
-            if (jg >= b0 && jg < b1) continue;
-            T dx = ti[0] - sm[0][jj], dy = ti[1] - sm[1][jj], dz = ti[2] - sm[2][jj];
+            if (jj >= lo && jj < hi) continue;
+            const V4 sv = sh[jj];
+            T dx = txh - sv.x, dy = tyh - sv.y, dz = tzh - sv.z;
             if constexpr (F32) {
-                dx += ti[3] - sm[3][jj];
-                dy += ti[4] - sm[4][jj];
-                dz += ti[5] - sm[5][jj];
+                const float4 lv = sl[jj];
+                dx += txl - lv.x;
+                dy += tyl - lv.y;
+                dz += tzl - lv.z;
             }
-            const T r2 = dx * dx + dy * dy + dz * dz;
-            if ((rcut2 > T(0) && r2 > rcut2) || !(r2 > T(0))) continue;
-            T inv, rr;
-            if constexpr (F32) {
-                inv = rsqrtf(r2);
-                rr = r2 * inv;
-            } else {
-                rr = sqrt(r2);
-                inv = 1.0 / rr;
-            }
-            const bool fl = r2 < rfl2;
-            const T re = fl ? rfloor : rr, ire = fl ? ifl : inv;
-            T e;
-            if constexpr (F32) e = expf(-re * invb);
-            else e = exp(-re * invb);
-            const T c = gamma * e * ire * (invb + ire) * inv;
-            fx += dx * c;
-            fy += dy * c;
-            fz += dz * c;
+            steric_pair<T>(dx, dy, dz, gamma, invb, rfloor, ifl, rfl2, rcut2, fx, fy, fz);
         }
         __syncthreads();
     }
     if (i < n) {
-        out[i] += fx;
-        out[n + i] += fy;
-        out[2 * n + i] += fz;
+        T* o = part + (int64_t)blockIdx.y * 3 * n;
+        o[i] = fx;
+        o[n + i] = fy;
+        o[2 * n + i] = fz;
     }
 }
 
 template <typename T>
-static void launch_steric(int64_t n, int nper, const double* r, const rpbd_forces& f, double* out, cudaStream_t st)
+__global__ void steric_reduce_kernel(int64_t n, int nch, const T* __restrict__ part, double* __restrict__ out)
 {
-    const T rc2 = f.r_cut > 0.0 ? (T)(f.r_cut * f.r_cut) : T(0);
-    steric_kernel<T><<<(unsigned)((n + STERIC_T - 1) / STERIC_T), STERIC_T, 0, st>>>(
-        n, nper, r, (T)f.steric_gamma, (T)f.steric_b, (T)f.r_floor, rc2, out);
-    count_launch();
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double acc = 0.0;
+        for (int k = 0; k < nch; ++k) acc += (double)part[((int64_t)k * 3 + c) * n + i];
+        out[c * n + i] += acc;
+    }
 }
 
-void launch_blob_forces(int64_t n, int nper, const double* r, const rpbd_forces& f, int dtype, double* out,
-                        cudaStream_t st)
+template <typename T>
+static int launch_steric(rpbd_handle* h, int64_t n, int nper, const double* r, const rpbd_forces& f, double* out,
+                         cudaStream_t st)
 {
-    if (n <= 0) return;
+    const int nch = (int)((n + STERIC_CH - 1) / STERIC_CH);
+    T* part;
+    RPBD_TRY(ensure_t(h, BUF_AUX, (size_t)nch * 3 * n, &part));
+    const T rc2 = f.r_cut > 0.0 ? (T)(f.r_cut * f.r_cut) : T(0);
+    const dim3 grid((unsigned)((n + STERIC_T - 1) / STERIC_T), (unsigned)nch);
+    steric_kernel<T><<<grid, STERIC_T, 0, st>>>(n, nper, r, (T)f.steric_gamma, (T)f.steric_b, (T)f.r_floor, rc2,
+                                                part);
+    count_launch();
+    steric_reduce_kernel<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, nch, part, out);
+    count_launch();
+    return RPBD_OK;
+}
+
+int launch_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const rpbd_forces& f, int dtype,
+                       double* out, cudaStream_t st)
+{
+    if (n <= 0) return RPBD_OK;
     blob_forces_kernel<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, r, f, out); count_launch();
     if (f.steric_gamma != 0.0 && nper > 0) {
-        if (dtype == RPBD_F32) launch_steric<float>(n, nper, r, f, out, st);
-        else launch_steric<double>(n, nper, r, f, out, st);
+        if (dtype == RPBD_F32) RPBD_TRY(launch_steric<float>(h, n, nper, r, f, out, st));
+        else RPBD_TRY(launch_steric<double>(h, n, nper, r, f, out, st));
     }
+    return RPBD_OK;
 }
 
 // ---------------------------------------------------------------------------

@@ -65,6 +65,8 @@ enum Buf {
     BUF_BLZ,         // batched Lanczos: basis and vectors
     BUF_BLZ_SMALL,   // batched Lanczos: per-system scalars
     BUF_SYM_ITEMS,   // symmetric kernel: work items
+    BUF_GMRES_MV,    // lockstep GMRES: gathered multi-RHS matvec operands
+    BUF_SYM_SEG,     // symmetric kernel: segment sums of the visitor partials
     BUF_COUNT
 };
 
@@ -80,6 +82,8 @@ struct ProfRec {
 }  // namespace rpbd
 
 #include <vector>
+
+inline int sym_class(int k) { return k <= 1 ? 0 : (k == 2 ? 1 : 2); }
 
 struct rpbd_handle {
     rpbd_params p;
@@ -105,8 +109,11 @@ struct rpbd_handle {
     int batch_variant = -1;
     std::vector<rpbd::BatchGraph*> bgraphs;
     // symmetric FP32 kernel (k <= 4): on by default, work list cached per n
-    int use_sym = 1;
-    int sym_variant = -1;  // -1: default per k; 0..3: loop unroll / occupancy variants of the symmetric kernel
+    // symmetric-kernel choice per right-hand-side class (k = 1, k = 2, 3 <= k <= 4):
+    // use it (1) or the one-direction kernel (0); variant -1: default, 0..3:
+    // loop unroll / occupancy variants
+    int use_sym[3] = {1, 1, 1};
+    int sym_variant[3] = {-1, -1, -1};
     int64_t sym_plan_n = -1;
     int sym_n_items = 0, sym_n_home = 0, sym_max_slots = 0;
 };
@@ -143,8 +150,8 @@ void launch_blobs(int64_t nb, int nper, const double* shape, const double* q,
                   const double* theta, double* r, cudaStream_t st);
 void launch_normals(uint64_t seed, uint32_t step, uint32_t sid, int64_t n, double* out,
                     cudaStream_t st);
-void launch_blob_forces(int64_t n, int nper, const double* r, const rpbd_forces& f, int dtype, double* out,
-                        cudaStream_t st);
+int launch_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const rpbd_forces& f, int dtype,
+                       double* out, cudaStream_t st);
 // q += s * U[:, :3]; theta = Rotate(theta, s * U[:, 3:])
 void launch_advance(int64_t nb, const double* q0, const double* th0, const double* U, double s,
                     double* q1, double* th1, cudaStream_t st);
@@ -163,6 +170,22 @@ int precond_saddle_impl(rpbd_handle* h, const double* a, const double* b, double
 int lanczos_impl(rpbd_handle* h, int64_t n, const double* r, const double* W, double* out,
                  double tol, int max_iter, int dtype, int use_precond, rpbd_stats* stats,
                  cudaStream_t st);
+// One saddle problem for gmres_multi_impl: b = [-slip; -FT] (either may be
+// null: zero), outputs lambda [3][n], U [nb][6]; warm != 0: they hold x0.
+struct GmresProblem {
+    const double* slip;
+    const double* FT;
+    double* lambda;
+    double* U;
+    double tol;
+    int max_iter;
+    int warm;
+};
+// 1..4 GMRES processes on the same positions, advanced in lockstep so their
+// matvecs share one multi-RHS launch.
+int gmres_multi_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, int nsys,
+                     const GmresProblem* probs, int restart, int dtype, int build_precond, rpbd_stats* stats,
+                     cudaStream_t st);
 int gmres_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q,
                const double* slip, const double* FT, double* lambda, double* U, double tol,
                int max_iter, int restart, int dtype, int build_precond, int warm, rpbd_stats* stats,

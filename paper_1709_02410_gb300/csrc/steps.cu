@@ -92,7 +92,7 @@ struct StepBufs {
 static int body_forces(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const rpbd_forces& f,
                        int dtype, double* fb, double* FT, cudaStream_t st)
 {
-    launch_blob_forces(nb * nper, nper, r, f, dtype, fb, st);
+    RPBD_TRY(launch_blob_forces(h, nb * nper, nper, r, f, dtype, fb, st));
     launch_KT(nb, nper, r, q, fb, FT, st);
     add_torque_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(nb, f.torque[0], f.torque[1], f.torque[2], FT); count_launch();
     RPBD_LAUNCH_CHECK(h);
@@ -127,6 +127,22 @@ static int solve(rpbd_handle* h, int64_t nb, int nper, const double* r, const do
     return (s == RPBD_NOT_CONVERGED) ? RPBD_OK : s;  // reported through stats
 }
 
+// Two saddle solves at the same positions, preconditioner already built;
+// their GMRES iterations run in lockstep and share two-RHS matvecs.
+static int solve_pair(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, const double* slip0,
+                      const double* FT0, double* lam0, double* U0, const double* slip1, const double* FT1,
+                      double* lam1, double* U1, const rpbd_step_params* sp, rpbd_stats* st0, rpbd_stats* st1,
+                      cudaStream_t st)
+{
+    const GmresProblem pb[2] = {{slip0, FT0, lam0, U0, sp->tol_gmres, sp->max_iter_gmres, 0},
+                                {slip1, FT1, lam1, U1, sp->tol_gmres, sp->max_iter_gmres, 0}};
+    rpbd_stats s2[2] = {};
+    int s = gmres_multi_impl(h, nb, nper, r, q, 2, pb, sp->restart, sp->dtype, 0, s2, st);
+    *st0 = s2[0];
+    *st1 = s2[1];
+    return (s == RPBD_NOT_CONVERGED) ? RPBD_OK : s;  // reported through stats
+}
+
 int step_ts_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, double* q, double* theta,
                  const rpbd_forces* f, const rpbd_step_params* sp, rpbd_stats* stats, cudaStream_t st)
 {
@@ -147,8 +163,20 @@ int step_ts_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, doub
     launch_normals(sp->seed, sp->step, 1, 3 * n, B.W, st);
     launch_scale_copy(3 * n, L, B.Ws, B.WD, st);
     launch_scale_copy(3 * n, kT / L, B.Ws, B.WF, st);
-    // 1b: RFD displacement problem, slip W^D, no force
-    RPBD_TRY(solve(h, nb, nper, B.r, q, B.WD, nullptr, B.lam, B.dQ, sp, 1, &S[0], st));
+    // the preconditioner at Q^n serves the RFD solve, Lanczos and the predictor
+    RPBD_TRY(precond_build_impl(h, nb, nper, B.r, q, st));
+    // 2: M^{1/2} W
+    {
+        int s = lanczos_impl(h, n, B.r, B.W, B.MhW, sp->tol_lanczos, sp->max_iter_lanczos, sp->dtype, 1, &S[1], st);
+        if (s != RPBD_OK && s != RPBD_NOT_CONVERGED) return s;
+    }
+    // 3 (right-hand side): slip c M^{1/2} W, force F^n
+    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, sp->dtype, B.fb, B.FT, st));
+    launch_scale_copy(3 * n, c, B.MhW, B.slip, st);
+    // 1b and 3: the RFD displacement problem (slip W^D, no force) and the
+    // predictor share M^n, so they are solved together (two-RHS matvecs)
+    RPBD_TRY(solve_pair(h, nb, nper, B.r, q, B.WD, nullptr, B.t2, B.dQ, B.slip, B.FT, B.lam, B.Un, sp, &S[0],
+                        &S[2], st));
     // 1c: Q+- = Q +- delta/2 dQ
     launch_advance(nb, q, theta, B.dQ, 0.5 * d, B.qp, B.tp, st);
     launch_advance(nb, q, theta, B.dQ, -0.5 * d, B.qm, B.tm, st);
@@ -162,15 +190,6 @@ int step_ts_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, doub
     RPBD_TRY(mobility_apply_impl(h, n, B.rm, B.WF, B.t2, 1, sp->dtype, true, st));
     diff_scale_kernel<<<g1(3 * n), 256, 0, st>>>(3 * n, B.t1, B.t2, 1.0 / d, B.DS); count_launch();
     RPBD_LAUNCH_CHECK(h);
-    // 2: M^{1/2} W (preconditioner of step 1b, built at Q^n)
-    {
-        int s = lanczos_impl(h, n, B.r, B.W, B.MhW, sp->tol_lanczos, sp->max_iter_lanczos, sp->dtype, 1, &S[1], st);
-        if (s != RPBD_OK && s != RPBD_NOT_CONVERGED) return s;
-    }
-    // 3: predictor solve, slip c M^{1/2} W, force F^n
-    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, sp->dtype, B.fb, B.FT, st));
-    launch_scale_copy(3 * n, c, B.MhW, B.slip, st);
-    RPBD_TRY(solve(h, nb, nper, B.r, q, B.slip, B.FT, B.lam, B.Un, sp, 0, &S[2], st));
     // 4: Q~ = Q^n + dt U^n
     launch_advance(nb, q, theta, B.Un, sp->dt, B.qt, B.tt, st);
     launch_blobs(nb, nper, shape, B.qt, B.tt, B.rt, st);
@@ -318,29 +337,33 @@ int step_tt_impl(rpbd_handle* h, int64_t nb, int nper, const double* shape, doub
     emt_random_kernel<<<(unsigned)((nb + 127) / 128), 128, 0, st>>>(nb, B.Wb, kT, L, B.b6a, B.dQ);
     count_launch();
     RPBD_LAUNCH_CHECK(h);
-    RPBD_TRY(solve(h, nb, nper, B.r, q, nullptr, B.b6a, B.lam, B.Un, sp, 1, &S[0], st));
+    // the preconditioner at Q^n serves the RFD solve, Lanczos and the predictor
+    RPBD_TRY(precond_build_impl(h, nb, nper, B.r, q, st));
+    {
+        int s = lanczos_impl(h, n, B.r, B.W, B.MhW, sp->tol_lanczos, sp->max_iter_lanczos, sp->dtype, 1, &S[1], st);
+        if (s != RPBD_OK && s != RPBD_NOT_CONVERGED) return s;
+    }
+    // predictor right-hand side, as step 3 of Algorithm 2
+    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, sp->dtype, B.fb, B.FT, st));
+    launch_scale_copy(3 * n, c, B.MhW, B.slip, st);
+    // the traction RFD problem (force W^FT, no slip; lambda^RFD -> WD, U^RFD
+    // unused) and the predictor share M^n: solved together
+    RPBD_TRY(solve_pair(h, nb, nper, B.r, q, nullptr, B.b6a, B.WD, B.Ut, B.slip, B.FT, B.lam, B.Un, sp, &S[0],
+                        &S[2], st));
     launch_advance(nb, q, theta, B.dQ, 0.5 * d, B.qp, B.tp, st);
     launch_advance(nb, q, theta, B.dQ, -0.5 * d, B.qm, B.tm, st);
     launch_blobs(nb, nper, shape, B.qp, B.tp, B.rp, st);
     launch_blobs(nb, nper, shape, B.qm, B.tm, B.rm, st);
     // D^F and D^S without the U^RFD term (the trapezoidal corrector supplies it)
-    launch_KT(nb, nper, B.rp, B.qp, B.lam, B.b6a, st);
-    launch_KT(nb, nper, B.rm, B.qm, B.lam, B.b6b, st);
+    launch_KT(nb, nper, B.rp, B.qp, B.WD, B.b6a, st);
+    launch_KT(nb, nper, B.rm, B.qm, B.WD, B.b6b, st);
     diff_scale_kernel<<<g1(6 * nb), 256, 0, st>>>(6 * nb, B.b6a, B.b6b, 1.0 / d, B.DF);
     count_launch();
-    RPBD_TRY(mobility_apply_impl(h, n, B.rp, B.lam, B.t1, 1, sp->dtype, true, st));
-    RPBD_TRY(mobility_apply_impl(h, n, B.rm, B.lam, B.t2, 1, sp->dtype, true, st));
+    RPBD_TRY(mobility_apply_impl(h, n, B.rp, B.WD, B.t1, 1, sp->dtype, true, st));
+    RPBD_TRY(mobility_apply_impl(h, n, B.rm, B.WD, B.t2, 1, sp->dtype, true, st));
     diff_scale_kernel<<<g1(3 * n), 256, 0, st>>>(3 * n, B.t1, B.t2, 1.0 / d, B.DS);
     count_launch();
     RPBD_LAUNCH_CHECK(h);
-    {
-        int s = lanczos_impl(h, n, B.r, B.W, B.MhW, sp->tol_lanczos, sp->max_iter_lanczos, sp->dtype, 1, &S[1], st);
-        if (s != RPBD_OK && s != RPBD_NOT_CONVERGED) return s;
-    }
-    // predictor, as step 3 of Algorithm 2
-    RPBD_TRY(body_forces(h, nb, nper, B.r, q, *f, sp->dtype, B.fb, B.FT, st));
-    launch_scale_copy(3 * n, c, B.MhW, B.slip, st);
-    RPBD_TRY(solve(h, nb, nper, B.r, q, B.slip, B.FT, B.lam, B.Un, sp, 0, &S[2], st));
     launch_advance(nb, q, theta, B.Un, sp->dt, B.qt, B.tt, st);
     launch_blobs(nb, nper, shape, B.qt, B.tt, B.rt, st);
     // corrector at Q~ with 2 D^S and 2 D^F

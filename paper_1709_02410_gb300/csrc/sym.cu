@@ -307,21 +307,51 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
     }
 }
 
-// U_i = s_i/(8 pi eta) [sum_{H < tile(i)} visitor partial(H) + sum_c home partial(c)]
-template <class P, class Out>
-__global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_home_tiles, int chunk,
-                              const P* __restrict__ partial, const double* __restrict__ scale, double inv8pieta,
-                              Out* __restrict__ U)
+// Visitor partials are reduced in two passes so the triangular sum over the
+// home tiles before blob i's tile spreads over many threads (several loads in
+// flight each): pass 1 sums home tiles [s SEG, (s+1) SEG) for segment s =
+// blockIdx.y; pass 2 adds the segments and the home partials, then scales.
+// Both passes use a fixed order (deterministic).
+constexpr int SEG = 64;  // home tiles per segment
+
+template <int KT, class P>
+__global__ void reduce_visitors_kernel(int64_t n, int64_t n_pad, int k, const P* __restrict__ partial,
+                                       double* __restrict__ segsum)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int h = (int)(i / HT);
+    const int H0 = blockIdx.y * SEG;
+    const int H1 = (H0 + SEG) < h ? (H0 + SEG) : h;
+    if (H0 >= H1) return;
+    double acc[3 * KT];
+#pragma unroll
+    for (int q = 0; q < 3 * KT; ++q) acc[q] = 0.0;
+    for (int H = H0; H < H1; ++H)
+#pragma unroll
+        for (int q = 0; q < 3 * KT; ++q)
+            if (q < 3 * k) acc[q] += (double)partial[((int64_t)H * 3 * KT + q) * n_pad + i];
+#pragma unroll
+    for (int q = 0; q < 3 * KT; ++q)
+        if (q < 3 * k) segsum[((int64_t)blockIdx.y * 3 * KT + q) * n_pad + i] = acc[q];
+}
+
+// U_i = s_i/(8 pi eta) [sum_{segments before tile(i)} + sum_c home partial(c)]
+template <class P, class Out>
+__global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_home_tiles, int chunk,
+                              const P* __restrict__ partial, const double* __restrict__ segsum,
+                              const double* __restrict__ scale, double inv8pieta, Out* __restrict__ U)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int h = (int)(i / HT);
+    const int nseg = (h + SEG - 1) / SEG;
     const int64_t vis = n_pad - (int64_t)(h + 1) * HT;  // visitors of tile h
     const int home_slots = 1 + (int)((vis + chunk - 1) / chunk);
     const double sc = scale[i] * inv8pieta;
     for (int q = 0; q < 3 * k; ++q) {
         double sum = 0.0;
-        for (int H = 0; H < h; ++H) sum += (double)partial[((int64_t)H * 3 * kt + q) * n_pad + i];
+        for (int sg = 0; sg < nseg; ++sg) sum += segsum[((int64_t)sg * 3 * kt + q) * n_pad + i];
         for (int c = 0; c < home_slots; ++c)
             sum += (double)partial[((int64_t)(n_home_tiles + c) * 3 * kt + q) * n_pad + i];
         U[(int64_t)q * n + i] = (Out)(sc * sum);
@@ -382,7 +412,8 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     const PairConst<float> pc = PairConst<float>::make(h->p.a, h->p.Lx, h->p.Ly);
     if (h->profile) prof_begin(h, st);
     // variant -1: the measured default per K (k = 1: unroll 4; otherwise unroll 2)
-    const int var = h->sym_variant >= 0 ? h->sym_variant : (K == 1 ? 3 : 0);
+    const int sv = h->sym_variant[sym_class(K)];
+    const int var = sv >= 0 ? sv : (K == 1 ? 3 : 0);
     switch (var) {  // tuning variants: (visitor-loop unroll, min CTAs per SM), see SymVar
     case 1: sym_kernel<K, WALL, PER, SymVar<K, 1>::UNR, SymVar<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
     case 2: sym_kernel<K, WALL, PER, SymVar<K, 2>::UNR, SymVar<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
@@ -393,8 +424,14 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     if (h->profile) prof_end(h, st, (K <= 2 && !PER) ? 4 /* symmetric, factored */ : 3 /* symmetric */, K,
                              (double)n * (double)n);
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
+    const int nseg = (n_home + SEG - 1) / SEG;
+    double* segsum;
+    RPBD_TRY(ensure_t(h, BUF_SYM_SEG, (size_t)nseg * 3 * K * n_pad, &segsum));
+    reduce_visitors_kernel<K, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)nseg), 256, 0, st>>>(
+        n, n_pad, k, partial, segsum);
+    count_launch();
     reduce_kernel<float, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_home, CHUNK, partial,
-                                                                           scale, inv8pieta, U);
+                                                                           segsum, scale, inv8pieta, U);
     count_launch();
     RPBD_LAUNCH_CHECK(h);
     return RPBD_OK;
