@@ -33,11 +33,11 @@ UNIT = "pairs/s"
 NB, NPER = 4369, 15
 N = NB * NPER
 K_RHS = 16
-F_GEOM = 116                 # algorithmic flops of one pair block (FMA = 2), see the design doc
+F_GEOM = 76                  # algorithmic flops of one pair block (FMA = 2, rsqrt = 1)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/pair_kernel_f32_k*_boomerangs_65535.md); None when not captured
-NCU_TRAFFIC = {"f32_k16": 20269312 + 342761728, "f32symf_k1": 158856704}
+NCU_TRAFFIC = {"f32_k16": 22749696 + 343597568, "f32symf_k1": 2990592 + 154483200}
 
 
 F_ASSEMBLY = 12             # flops of forming the 9 entries from the block's 5 scalars
@@ -60,6 +60,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle accuracy / CPU legs")
     ap.add_argument("--no-rollers", action="store_true", help="skip the 196,608-blob roller T-S step")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="time the steps only: skip the per-row, batched, roller and single-matvec extras")
     return ap.parse_args()
 
 
@@ -152,9 +154,11 @@ def run_ours(args, rank, world, local):
     forces = Forces(1.57e-11 * 9.81e6, 0.096, 0.162, 0.1, (0.0, 0.0, 0.0))
     Lp = 14 * 1.05 * s.a          # arm length: 7 spacings of 2.1 a
 
-    # pick the fastest FP32 kernel variant for this suspension (k = 1: the Krylov matvecs)
+    # pick the fastest FP32 kernel variant for this suspension (k = 1: the Krylov matvecs;
+    # k = 2: the RFD and predictor solves run in lockstep)
     r0 = h.blobs_from_bodies(shape, q0, th0)
     tuned = h.autotune(r0, 1)
+    tuned2 = h.autotune(r0, 2)   # the lockstep RFD + predictor solves
 
     def sp(i):
         return StepParams(0.01, 1e-3, Lp, 1e-6, 1e-4, 300, 100, 80, P.F32, 2024 + rank, i)
@@ -252,7 +256,7 @@ def run_ours(args, rank, world, local):
     # ---- separate measurements (outside the timed steps): k = 16 FP32 batch and
     # the plain FP64 single-RHS kernel, each alone, and their accuracy
     r = h.blobs_from_bodies(shape, q0, th0)
-    extra = {}
+    extra = None
 
     def time_launch(fn, reps):
         fn()
@@ -268,29 +272,12 @@ def run_ours(args, rank, world, local):
             tot += a.elapsed_time(b)
         return tot / reps / 1e3
 
-    t16 = time_launch(lambda: h.mobility_apply(r, F16, out=U16), 3)
-    F1 = T(synth.gaussian(200, (3, N)))
-    U1 = torch.empty_like(F1)
-    t64 = time_launch(lambda: h.mobility_apply(r, F1, out=U1), 1)
-    F1f = F1.float()
-    U1f = torch.empty_like(F1f)
-    t32k1 = time_launch(lambda: h.mobility_apply(r, F1f, out=U1f), 3)
-    extra["f32_k16"] = dict(s_per_launch=t16, pairs_per_s=N * N / t16, matvecs_per_s=K_RHS / t16,
-                            tflops=N * N * f_pair(16) / t16 / 1e12)
-    extra["f32_k1_symmetric"] = dict(s_per_launch=t32k1, pairs_per_s=N * N / t32k1,
-                                     tflops=N * N * f_pair(1, True, True) / t32k1 / 1e12)
-    h.set_symmetric(False)
-    t32k1d = time_launch(lambda: h.mobility_apply(r, F1f, out=U1f), 3)
-    h.set_symmetric(True)
-    extra["f32_k1_one_direction"] = dict(s_per_launch=t32k1d, pairs_per_s=N * N / t32k1d,
-                                         tflops=N * N * f_pair(1) / t32k1d / 1e12)
-    extra["f64_k1"] = dict(s_per_launch=t64, pairs_per_s=N * N / t64)
-    extra["speedup_f32_k16_vs_f64_k1_per_rhs"] = (t64 * K_RHS) / t16
-    extra["speedup_f32_k1_vs_f64_k1"] = t64 / t32k1
-
-    row_times = measure_rows(h, r, shape, q0, th0, T, time_launch) if rank == 0 else None
-    batched = measure_batched(h.lib, dev, T) if rank == 0 else None
-    rollers = measure_rollers(dev, T) if (rank == 0 and not args.no_rollers) else None
+    extras = not args.no_extras
+    if extras:
+        extra, F1, U1 = measure_matvecs(h, r, F16, U16, T, time_launch)
+    row_times = measure_rows(h, r, shape, q0, th0, T, time_launch) if (rank == 0 and extras) else None
+    batched = measure_batched(h.lib, dev, T) if (rank == 0 and extras) else None
+    rollers = measure_rollers(dev, T) if (rank == 0 and extras and not args.no_rollers) else None
 
     out = None
     if rank == 0:
@@ -313,7 +300,7 @@ def run_ours(args, rank, world, local):
                     "share_of_step": d["ms"] / (t_local * 1e3)}
         # accuracy vs the FP64 oracle on sampled rows (outside the timed region)
         acc = {}
-        if not args.no_oracle:
+        if extras and not args.no_oracle:
             from oracle import mobility as om
             from oracle import rigid
             ro = rigid.blob_positions(s.q, s.theta, s.shape)
@@ -359,6 +346,7 @@ def run_ours(args, rank, world, local):
             "solver_iterations_per_step": iters,
             "autotune_k1": {"choice": tuned[0], "ms_per_launch": tuned[1],
                             "legend": "0: one-direction kernel; 1 + v: symmetric kernel variant v"},
+            "autotune_k2": {"choice": tuned2[0], "ms_per_launch": tuned2[1]},
             "matvec": extra,
             "rows": row_times,
             "batched_c4": batched,
@@ -371,6 +359,42 @@ def run_ours(args, rank, world, local):
 
 # ---------------------------------------------------------------------------
 # every step of the hot path timed alone on the bench suspension
+
+def measure_matvecs(h, r, F16, U16, T, time_launch):
+    """k = 16 FP32 batch, k = 1 FP32 (symmetric and one-direction) and the
+    plain FP64 single-RHS kernel, each timed alone."""
+    import torch
+    from paper_1709_02410_gb300 import synth
+    extra = {}
+    t16 = time_launch(lambda: h.mobility_apply(r, F16, out=U16), 3)
+    F1 = T(synth.gaussian(200, (3, N)))
+    U1 = torch.empty_like(F1)
+    t64 = time_launch(lambda: h.mobility_apply(r, F1, out=U1), 1)
+    F1f = F1.float()
+    U1f = torch.empty_like(F1f)
+    t32k1 = time_launch(lambda: h.mobility_apply(r, F1f, out=U1f), 3)
+    extra["f32_k16"] = dict(s_per_launch=t16, pairs_per_s=N * N / t16, matvecs_per_s=K_RHS / t16,
+                            tflops=N * N * f_pair(16) / t16 / 1e12)
+    extra["f32_k1_symmetric"] = dict(s_per_launch=t32k1, pairs_per_s=N * N / t32k1,
+                                     tflops=N * N * f_pair(1, True, True) / t32k1 / 1e12)
+    h.set_symmetric(False)
+    t32k1d = time_launch(lambda: h.mobility_apply(r, F1f, out=U1f), 3)
+    h.set_symmetric(True)
+    extra["f32_k1_one_direction"] = dict(s_per_launch=t32k1d, pairs_per_s=N * N / t32k1d,
+                                         tflops=N * N * f_pair(1) / t32k1d / 1e12)
+    for kk in (2, 4, 8):
+        Fk = T(synth.gaussian(210 + kk, (kk, 3, N)), torch.float32)
+        Uk = torch.empty_like(Fk)
+        tk = time_launch(lambda: h.mobility_apply(r, Fk, out=Uk), 3)
+        sym = kk <= 4
+        extra[f"f32_k{kk}"] = dict(s_per_launch=tk, pairs_per_s=N * N / tk, matvecs_per_s=kk / tk,
+                                   kernel="symmetric" if sym else "one-direction",
+                                   tflops=N * N * f_pair(kk, sym, sym and kk <= 2) / tk / 1e12)
+    extra["f64_k1"] = dict(s_per_launch=t64, pairs_per_s=N * N / t64)
+    extra["speedup_f32_k16_vs_f64_k1_per_rhs"] = (t64 * K_RHS) / t16
+    extra["speedup_f32_k1_vs_f64_k1"] = t64 / t32k1
+    return extra, F1, U1
+
 
 def measure_rows(h, r, shape, q, th, T, time_launch):
     import torch
