@@ -159,6 +159,8 @@ def run_ours(args, rank, world, local):
     r0 = h.blobs_from_bodies(shape, q0, th0)
     tuned = h.autotune(r0, 1)
     tuned2 = h.autotune(r0, 2)   # the lockstep RFD + predictor solves
+    fma32 = h.measure_fma_peak(P.F32)
+    fma64 = h.measure_fma_peak(P.F64)
 
     def sp(i):
         return StepParams(0.01, 1e-3, Lp, 1e-6, 1e-4, 300, 100, 80, P.F32, 2024 + rank, i)
@@ -212,6 +214,7 @@ def run_ours(args, rank, world, local):
             if nl.value:
                 prof[f"{name}_k{k}"] = dict(ms=ms.value, launches=nl.value, pairs=pr.value)
     pairs_local = sum(v["pairs"] for v in prof.values())
+    rhs_local = sum(v["launches"] * int(name.split("_k")[1]) for name, v in prof.items())
 
     # whole job: max time over ranks, pairs summed over ranks
     t_max, pairs_total = aggregate(t_local, pairs_local, world, dev)
@@ -297,7 +300,10 @@ def run_ours(args, rank, world, local):
                     "flops_per_pair": f_pair(k, sym, fac), "avg_launch_ms": avg * 1e3,
                     "one_direction_equivalent_tflops":
                         d["pairs"] / d["launches"] * f_pair(k) / avg / 1e12,
-                    "share_of_step": d["ms"] / (t_local * 1e3)}
+                    "share_of_step": d["ms"] / (t_local * 1e3),
+                    "measured_fma_peak": fma32, "frac_of_measured_fma_peak": ach / fma32,
+                    "peak_note": "peak = 152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (derived); "
+                                 "measured_fma_peak = the library's FMA-chain probe on this GPU"}
         # accuracy vs the FP64 oracle on sampled rows (outside the timed region)
         acc = {}
         if extras and not args.no_oracle:
@@ -322,6 +328,16 @@ def run_ours(args, rank, world, local):
             tc = time.perf_counter() - t0
             cpu = {"value": nrows * N / tc, "unit": UNIT, "cores": om.num_threads(), "kind": "oracle",
                    "sample": f"{nrows} target rows x {N} sources, k = 16, FP64 ({tc:.1f} s)"}
+            # the same oracle on one core (smaller row sample)
+            ncores = om.num_threads()
+            om.set_num_threads(1)
+            rows_1 = np.arange(256)
+            t0 = time.perf_counter()
+            om.apply(ro, Fo, prm, rows=rows_1)
+            t1c = time.perf_counter() - t0
+            om.set_num_threads(ncores)
+            cpu["one_core"] = {"value": len(rows_1) * N / t1c, "unit": UNIT, "cores": 1,
+                               "sample": f"{len(rows_1)} target rows x {N} sources, k = 16, FP64 ({t1c:.1f} s)"}
         else:
             cpu = None
         iters = [[x["iterations"] for x in st] for st in timed_stats]
@@ -337,6 +353,7 @@ def run_ours(args, rank, world, local):
                        "l2": "flushed (256 MB write) before every timed step",
                        "parallelism": f"replicas x{world}"},
             "steps_per_s": args.steps / t_max * world,
+            "matvecs_per_s": rhs_local * world / t_max,
             "e2e": {"value": e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
             "gpu_launches": int(launches),
             "roofline": roof,
@@ -347,6 +364,7 @@ def run_ours(args, rank, world, local):
             "autotune_k1": {"choice": tuned[0], "ms_per_launch": tuned[1],
                             "legend": "0: one-direction kernel; 1 + v: symmetric kernel variant v"},
             "autotune_k2": {"choice": tuned2[0], "ms_per_launch": tuned2[1]},
+            "measured_fma_peak_tflops": {"f32": fma32, "f64": fma64},
             "matvec": extra,
             "rows": row_times,
             "batched_c4": batched,

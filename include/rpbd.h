@@ -347,6 +347,12 @@ int rpbd_autotune(rpbd_handle* h, int64_t n, const double* r, int k, double* bes
 
 /* Number of kernels this library has launched since it was loaded. */
 long long rpbd_launch_count(void);
+/* Measures the FMA throughput of this GPU in dtype (RPBD_F32 or RPBD_F64):
+ * one launch of independent FMA chains filling every SM, timed with CUDA
+ * events on the stream; *tflops (host) receives FLOP/s / 1e12 (FMA = 2).
+ * The denominator for roofline fractions of ALU-bound kernels.  Synchronises
+ * the stream. */
+int rpbd_measure_fma_peak(rpbd_handle* h, int dtype, double* tflops, void* stream);
 /* on != 0: bracket every pair-kernel launch of h with CUDA events on its
  * stream (used to time the kernel inside a larger step). */
 int rpbd_profile_enable(rpbd_handle* h, int on);

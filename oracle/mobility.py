@@ -32,6 +32,7 @@ def lib():
         _lib.orc_pair_dblock.argtypes = [P, P, i, d, d, i, d, d, d, P, P]
         _lib.orc_blake_point.argtypes = [P, P, P]
         _lib.orc_num_threads.restype = i
+        _lib.orc_set_num_threads.argtypes = [i]
     return _lib
 
 
@@ -57,6 +58,11 @@ class Params:
 
 def num_threads() -> int:
     return lib().orc_num_threads()
+
+
+def set_num_threads(n: int):
+    """OpenMP threads of the oracle's loops (timing at a fixed core count)."""
+    lib().orc_set_num_threads(int(n))
 
 
 def apply(r, F, prm: Params, rows=None):

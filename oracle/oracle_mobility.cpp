@@ -414,4 +414,14 @@ int orc_num_threads(void)
 #endif
 }
 
+/* threads of the OpenMP loops from now on (for timing at a fixed core count) */
+void orc_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
 }  /* extern "C" */

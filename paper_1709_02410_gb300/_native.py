@@ -75,6 +75,7 @@ SIGNATURES = [
     ("rpbd_lanczos_sqrt_apply_batched", _I, [_P, _I, _P, _P, _P, _P, _P, _P, _D, _I, _I, _I, _P, _P]),
     ("rpbd_mobility_apply_f32_noalloc", _I, [C.POINTER(Params), _I64, _P, _P, _P, _I, _P]),
     ("rpbd_launch_count", C.c_longlong, []),
+    ("rpbd_measure_fma_peak", _I, [_P, _I, C.POINTER(C.c_double), _P]),
     ("rpbd_set_option", _I, [_P, _I, _I]),
     ("rpbd_autotune", _I, [_P, _I64, _P, _I, C.POINTER(C.c_double), _P]),
     ("rpbd_profile_enable", _I, [_P, _I]),

@@ -73,6 +73,12 @@ class Handle:
     def set_sym_variant(self, v: int):
         self._check(self.lib.rpbd_set_option(self.h, 2, int(v)), "set_option")
 
+    def measure_fma_peak(self, dtype=F32):
+        """FMA throughput of this GPU in TFLOP/s (FMA = 2), measured by the library."""
+        v = C.c_double()
+        self._check(self.lib.rpbd_measure_fma_peak(self.h, dtype, C.byref(v), _stream()), "measure_fma_peak")
+        return v.value
+
     def autotune(self, r, k=1):
         """Pick the fastest FP32 kernel for this n and k; returns (choice, ms per launch)."""
         ms = C.c_double()

@@ -155,6 +155,70 @@ int rpbd_reserve(rpbd_handle* h, int64_t n, int64_t nb, int nper, int k, int bas
 
 long long rpbd_launch_count(void) { return g_launches.load(); }
 
+}  // extern "C"
+
+namespace rpbd {
+// FMA-throughput probe: every thread runs 8 independent FMA chains of
+// 16 * iters links each; the result is stored only under a condition the
+// chains never meet, so the work cannot be dropped.
+template <typename T>
+__global__ void __launch_bounds__(256) fma_peak_kernel(int iters, T a, T b, T* __restrict__ sink)
+{
+    T x[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) x[c] = T(threadIdx.x + c) * T(1e-3);
+    for (int i = 0; i < iters; ++i)
+#pragma unroll
+        for (int u = 0; u < 16; ++u)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) x[c] = fma(x[c], a, b);
+    T s = T(0);
+#pragma unroll
+    for (int c = 0; c < 8; ++c) s += x[c];
+    if (s == T(-1)) sink[blockIdx.x * blockDim.x + threadIdx.x] = s;
+}
+
+template <typename T>
+static int measure_peak(rpbd_handle* h, int iters, double* tflops, cudaStream_t st)
+{
+    int dev = 0, sms = 0;
+    RPBD_CU(h, cudaGetDevice(&dev));
+    RPBD_CU(h, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const unsigned grid = (unsigned)sms * 8;
+    T* sink;
+    RPBD_TRY(ensure_t(h, BUF_AUX, (size_t)grid * 256, &sink));
+    cudaEvent_t e0, e1;
+    RPBD_CU(h, cudaEventCreate(&e0));
+    RPBD_CU(h, cudaEventCreate(&e1));
+    fma_peak_kernel<T><<<grid, 256, 0, st>>>(iters / 8 + 1, T(0.9999999), T(1e-7), sink);  // warm-up
+    count_launch();
+    RPBD_CU(h, cudaEventRecord(e0, st));
+    fma_peak_kernel<T><<<grid, 256, 0, st>>>(iters, T(0.9999999), T(1e-7), sink);
+    count_launch();
+    RPBD_CU(h, cudaEventRecord(e1, st));
+    RPBD_CU(h, cudaEventSynchronize(e1));
+    float ms = 0.0f;
+    RPBD_CU(h, cudaEventElapsedTime(&ms, e0, e1));
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    const double flops = 2.0 * 8 * 16 * (double)iters * grid * 256;
+    *tflops = ms > 0.0f ? flops / (ms * 1e-3) / 1e12 : 0.0;
+    return RPBD_OK;
+}
+}  // namespace rpbd
+
+extern "C" {
+
+int rpbd_measure_fma_peak(rpbd_handle* h, int dtype, double* tflops, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (!tflops) return set_error(h, RPBD_BAD_ARG, "measure_fma_peak: null output");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    if (dtype == RPBD_F32) return measure_peak<float>(h, 4096, tflops, st);
+    if (dtype == RPBD_F64) return measure_peak<double>(h, 64, tflops, st);
+    return set_error(h, RPBD_BAD_ARG, "measure_fma_peak: bad dtype");
+}
+
 int rpbd_set_option(rpbd_handle* h, int option, int value)
 {
     if (!h) return RPBD_BAD_ARG;

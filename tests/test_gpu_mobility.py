@@ -145,3 +145,28 @@ def test_autotune_picks_a_correct_kernel():
         h.set_sym_variant(v)
         U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
         assert rel2(U, om.apply(r, F.astype(np.float64), oracle_params(s))) <= 1e-5
+
+
+def test_autotune_classes_are_independent():
+    """Autotuning k = 2 keeps the k = 1 choice; both classes stay correct."""
+    s = synth.c0_boomerangs_1920()
+    r = positions(s)
+    h = handle_for(s)
+    c1, _ = h.autotune(to_dev(r), 1)
+    c2, _ = h.autotune(to_dev(r), 2)
+    assert 0 <= c1 <= 4 and 0 <= c2 <= 4
+    for k in (1, 2, 3):
+        F = synth.gaussian(61 + k, (k, 3, s.n), np.float32)
+        U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+        assert rel2(U, om.apply(r, F.astype(np.float64), oracle_params(s))) <= 1e-5
+
+
+def test_fma_peak_probe():
+    """The FMA-throughput probe returns a plausible figure: below the nominal
+    dense peaks (FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz) with margin, and
+    FP32 well above FP64."""
+    h = handle_for(synth.c0_boomerangs_1920())
+    f32 = h.measure_fma_peak(F32)
+    f64 = h.measure_fma_peak(F64)
+    assert 1.0 < f32 < 1.2 * 80.55
+    assert 0.0 < f64 < f32
