@@ -37,7 +37,8 @@ F_GEOM = 76                  # algorithmic flops of one pair block (FMA = 2, rsq
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/pair_kernel_f32_k*_boomerangs_65535.md); None when not captured
-NCU_TRAFFIC = {"f32_k16": 22749696 + 343597568, "f32symf_k1": 2990592 + 154483200}
+NCU_TRAFFIC = {"f32_k16": 22749696 + 343597568, "f32symf_k1": 2990592 + 154483200,
+               "f32symf_k2": 6880512 + 369568768}
 
 
 F_ASSEMBLY = 12             # flops of forming the 9 entries from the block's 5 scalars
@@ -60,6 +61,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-oracle", action="store_true", help="skip the oracle accuracy / CPU legs")
     ap.add_argument("--no-rollers", action="store_true", help="skip the 196,608-blob roller T-S step")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the library's default kernels (autotuning under a profiler times the profiler)")
     ap.add_argument("--no-extras", action="store_true",
                     help="time the steps only: skip the per-row, batched, roller and single-matvec extras")
     return ap.parse_args()
@@ -157,8 +160,8 @@ def run_ours(args, rank, world, local):
     # pick the fastest FP32 kernel variant for this suspension (k = 1: the Krylov matvecs;
     # k = 2: the RFD and predictor solves run in lockstep)
     r0 = h.blobs_from_bodies(shape, q0, th0)
-    tuned = h.autotune(r0, 1)
-    tuned2 = h.autotune(r0, 2)   # the lockstep RFD + predictor solves
+    tuned = h.autotune(r0, 1) if not args.no_autotune else (None, None)
+    tuned2 = h.autotune(r0, 2) if not args.no_autotune else (None, None)   # the lockstep RFD + predictor solves
     fma32 = h.measure_fma_peak(P.F32)
     fma64 = h.measure_fma_peak(P.F64)
 

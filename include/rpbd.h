@@ -333,6 +333,10 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
 /* -1 (default): per-k default; 0..3: loop-unroll / occupancy variant of the
  * symmetric kernel, for every right-hand-side class. */
 #define RPBD_OPT_SYM_VARIANT 2
+/* value != 0 (default): with the wall and no periodic images, symmetric
+ * matvecs with k <= 2 use the packed kernel (two home blobs per thread, both
+ * pair blocks formed by two-wide FP32 instructions); 0: the one-home kernel. */
+#define RPBD_OPT_PACKED 3
 int rpbd_set_option(rpbd_handle* h, int option, int value);
 
 /* Times the FP32 matvec kernels on n blobs at r (k right-hand sides, zero
@@ -347,7 +351,8 @@ int rpbd_autotune(rpbd_handle* h, int64_t n, const double* r, int k, double* bes
 
 /* Number of kernels this library has launched since it was loaded. */
 long long rpbd_launch_count(void);
-/* Measures the FMA throughput of this GPU in dtype (RPBD_F32 or RPBD_F64):
+/* Measures the FMA throughput of this GPU in dtype (RPBD_F32, RPBD_F64, or 2:
+ * FP32 with packed two-wide FMA instructions):
  * one launch of independent FMA chains filling every SM, timed with CUDA
  * events on the stream; *tflops (host) receives FLOP/s / 1e12 (FMA = 2).
  * The denominator for roofline fractions of ALU-bound kernels.  Synchronises

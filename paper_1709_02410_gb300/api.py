@@ -66,6 +66,10 @@ class Handle:
             raise RpbdError(f"{what}: {_native.STATUS.get(st, st)}: {msg}")
         return st
 
+    def set_packed(self, on: bool):
+        """k <= 2 symmetric matvecs (wall, open cell): packed two-homes-per-thread kernel (default) or not."""
+        self._check(self.lib.rpbd_set_option(self.h, 3, int(bool(on))), "set_option")
+
     def set_symmetric(self, on: bool):
         """FP32 matvecs with k <= 4: symmetric kernel (default) or one-direction."""
         self._check(self.lib.rpbd_set_option(self.h, 1, int(bool(on))), "set_option")

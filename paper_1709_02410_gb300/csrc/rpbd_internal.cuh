@@ -67,6 +67,7 @@ enum Buf {
     BUF_SYM_ITEMS,   // symmetric kernel: work items
     BUF_GMRES_MV,    // lockstep GMRES: gathered multi-RHS matvec operands
     BUF_SYM_SEG,     // symmetric kernel: segment sums of the visitor partials
+    BUF_SYM2_ITEMS,  // packed symmetric kernel: work items
     BUF_COUNT
 };
 
@@ -77,6 +78,12 @@ struct ProfRec {
     cudaEvent_t a, b;
     int dtype, k;
     double pairs;
+};
+
+// cached work list of a symmetric kernel (per n)
+struct SymPlan {
+    int64_t n = -1;
+    int n_items = 0, n_home = 0, max_slots = 0;
 };
 
 }  // namespace rpbd
@@ -114,8 +121,8 @@ struct rpbd_handle {
     // loop unroll / occupancy variants
     int use_sym[3] = {1, 1, 1};
     int sym_variant[3] = {-1, -1, -1};
-    int64_t sym_plan_n = -1;
-    int sym_n_items = 0, sym_n_home = 0, sym_max_slots = 0;
+    rpbd::SymPlan sym_plan[2];  // work lists of the symmetric kernels: 128- and 256-blob home tiles
+    int use_packed = 1;         // k <= 2, open cell: the packed two-homes-per-thread symmetric kernel
 };
 
 namespace rpbd {

@@ -29,6 +29,7 @@
 
 #include "rpbd_internal.cuh"
 #include "wall_rpy.cuh"
+#include "wall_rpy_x2.cuh"
 
 namespace rpbd {
 namespace sym {
@@ -314,13 +315,13 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
 // Both passes use a fixed order (deterministic).
 constexpr int SEG = 64;  // home tiles per segment
 
-template <int KT, class P>
+template <int HTT, int KT, class P>
 __global__ void reduce_visitors_kernel(int64_t n, int64_t n_pad, int k, const P* __restrict__ partial,
                                        double* __restrict__ segsum)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int h = (int)(i / HT);
+    const int h = (int)(i / HTT);
     const int H0 = blockIdx.y * SEG;
     const int H1 = (H0 + SEG) < h ? (H0 + SEG) : h;
     if (H0 >= H1) return;
@@ -337,16 +338,16 @@ __global__ void reduce_visitors_kernel(int64_t n, int64_t n_pad, int k, const P*
 }
 
 // U_i = s_i/(8 pi eta) [sum_{segments before tile(i)} + sum_c home partial(c)]
-template <class P, class Out>
+template <int HTT, class P, class Out>
 __global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_home_tiles, int chunk,
                               const P* __restrict__ partial, const double* __restrict__ segsum,
                               const double* __restrict__ scale, double inv8pieta, Out* __restrict__ U)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
-    const int h = (int)(i / HT);
+    const int h = (int)(i / HTT);
     const int nseg = (h + SEG - 1) / SEG;
-    const int64_t vis = n_pad - (int64_t)(h + 1) * HT;  // visitors of tile h
+    const int64_t vis = n_pad - (int64_t)(h + 1) * HTT;  // visitors of tile h
     const int home_slots = 1 + (int)((vis + chunk - 1) / chunk);
     const double sc = scale[i] * inv8pieta;
     for (int q = 0; q < 3 * k; ++q) {
@@ -358,17 +359,22 @@ __global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_hom
     }
 }
 
-static int get_items(rpbd_handle* h, int64_t n, int64_t n_pad, SymItem** d_items, int* n_items, int* n_home,
+// Work items of the symmetric kernels for home tiles of TILE blobs: per home
+// tile one diagonal item (slot 0) and one item per CHUNK visitors after it.
+// Cached per n in plan slot `ps` (0: 128-blob tiles, 1: 256-blob tiles).
+template <int TILE>
+static int get_items(rpbd_handle* h, int ps, int64_t n, int64_t n_pad, SymItem** d_items, int* n_items, int* n_home,
                      int* max_slots)
 {
-    if (h->sym_plan_n != n) {
+    SymPlan& pl = h->sym_plan[ps];
+    if (pl.n != n) {
         std::vector<SymItem> items;
-        const int T = (int)(n_pad / HT);
+        const int T = (int)(n_pad / TILE);
         int ms = 1;
         for (int H = 0; H < T; ++H) {
-            items.push_back(SymItem{H, H * HT, HT / VT, 0});
+            items.push_back(SymItem{H, H * TILE, TILE / VT, 0});
             int c = 1;
-            for (int64_t v0 = (int64_t)(H + 1) * HT; v0 < n_pad; v0 += CHUNK, ++c) {
+            for (int64_t v0 = (int64_t)(H + 1) * TILE; v0 < n_pad; v0 += CHUNK, ++c) {
                 const int64_t v1 = std::min<int64_t>(n_pad, v0 + CHUNK);
                 items.push_back(SymItem{H, (int)v0, (int)((v1 - v0) / VT), c});
             }
@@ -377,17 +383,18 @@ static int get_items(rpbd_handle* h, int64_t n, int64_t n_pad, SymItem** d_items
         // longest items first so the hardware scheduler fills the tail with short ones
         std::stable_sort(items.begin(), items.end(), [](const SymItem& a, const SymItem& b) { return a.ntile > b.ntile; });
         void* d = nullptr;
-        RPBD_TRY(ensure(h, BUF_SYM_ITEMS, items.size() * sizeof(SymItem), &d));
+        const Buf b = ps == 0 ? BUF_SYM_ITEMS : BUF_SYM2_ITEMS;
+        RPBD_TRY(ensure(h, b, items.size() * sizeof(SymItem), &d));
         RPBD_CU(h, cudaMemcpy(d, items.data(), items.size() * sizeof(SymItem), cudaMemcpyHostToDevice));
-        h->sym_plan_n = n;
-        h->sym_n_items = (int)items.size();
-        h->sym_n_home = T;
-        h->sym_max_slots = ms;
+        pl.n = n;
+        pl.n_items = (int)items.size();
+        pl.n_home = T;
+        pl.max_slots = ms;
     }
-    *d_items = reinterpret_cast<SymItem*>(h->buf[BUF_SYM_ITEMS]);
-    *n_items = h->sym_n_items;
-    *n_home = h->sym_n_home;
-    *max_slots = h->sym_max_slots;
+    *d_items = reinterpret_cast<SymItem*>(h->buf[ps == 0 ? BUF_SYM_ITEMS : BUF_SYM2_ITEMS]);
+    *n_items = pl.n_items;
+    *n_home = pl.n_home;
+    *max_slots = pl.max_slots;
     return RPBD_OK;
 }
 
@@ -398,7 +405,7 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     const int64_t n_pad = (n + HT - 1) / HT * HT;
     SymItem* items;
     int n_items, n_home, max_slots;
-    RPBD_TRY(get_items(h, n, n_pad, &items, &n_items, &n_home, &max_slots));
+    RPBD_TRY(get_items<HT>(h, 0, n, n_pad, &items, &n_items, &n_home, &max_slots));
     float* rec;
     double* scale;
     float* partial;
@@ -411,9 +418,9 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 2 * 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
     const PairConst<float> pc = PairConst<float>::make(h->p.a, h->p.Lx, h->p.Ly);
     if (h->profile) prof_begin(h, st);
-    // variant -1: the measured default per K (k = 1: unroll 4; otherwise unroll 2)
+    // variant -1: the measured default per K (k <= 2: unroll 4; otherwise unroll 2)
     const int sv = h->sym_variant[sym_class(K)];
-    const int var = sv >= 0 ? sv : (K == 1 ? 3 : 0);
+    const int var = sv >= 0 ? sv : (K <= 2 ? 3 : 0);
     switch (var) {  // tuning variants: (visitor-loop unroll, min CTAs per SM), see SymVar
     case 1: sym_kernel<K, WALL, PER, SymVar<K, 1>::UNR, SymVar<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
     case 2: sym_kernel<K, WALL, PER, SymVar<K, 2>::UNR, SymVar<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
@@ -427,11 +434,314 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     const int nseg = (n_home + SEG - 1) / SEG;
     double* segsum;
     RPBD_TRY(ensure_t(h, BUF_SYM_SEG, (size_t)nseg * 3 * K * n_pad, &segsum));
-    reduce_visitors_kernel<K, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)nseg), 256, 0, st>>>(
+    reduce_visitors_kernel<HT, K, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)nseg), 256, 0, st>>>(
         n, n_pad, k, partial, segsum);
     count_launch();
-    reduce_kernel<float, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_home, CHUNK, partial,
-                                                                           segsum, scale, inv8pieta, U);
+    reduce_kernel<HT, float, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_home, CHUNK,
+                                                                               partial, segsum, scale, inv8pieta, U);
+    count_launch();
+    RPBD_LAUNCH_CHECK(h);
+    return RPBD_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Packed variant for k <= 2 in an open cell with the wall (the Krylov
+// matvecs of a time step).  Each thread holds two home blobs (256 per CTA)
+// and meets every visitor with both at once: the two pair blocks are formed
+// in the .x / .y lanes of float2 values with packed two-wide FP32
+// instructions (wall_rpy_x2.cuh), so one instruction stream serves two pairs.
+// The visitor's running sums carry both homes' contributions (.x, .y) and are
+// added only when the tile's sums go to shared memory.  Source records are
+// stored with every field duplicated ([xh xh yh yh][xl xl yl yl][z z fx fx]
+// ...) so a 16-byte shared load yields two packed operands, and transposed
+// within each 32-record tile (field chunk c of record j at (c * 32 + j) * 4
+// floats) so the 32 lanes' loads of different records hit distinct banks.
+
+constexpr int HT2 = 256;  // home blobs per CTA, two per thread
+
+template <int K>
+struct Rec2 {
+    static constexpr int NCH = K == 1 ? 4 : 6;  // 16-byte chunks per record
+    static constexpr int LEN = 4 * NCH;         // floats per record
+};
+
+__host__ __device__ __forceinline__ int64_t rec2_off(int64_t i, int c, int len)
+{
+    return (i / VT) * VT * len + ((int64_t)c * VT + (i % VT)) * 4;
+}
+
+template <int K, class In>
+__global__ void pack2_kernel(int64_t n, int64_t n_pad, int k, const double* __restrict__ r, const In* __restrict__ F,
+                             double a, int wall, double s_min, float* __restrict__ rec, double* __restrict__ scale)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (i >= n_pad) return;
+    constexpr int NCH = Rec2<K>::NCH, LEN = Rec2<K>::LEN;
+    double x = 1.0e7, y = 1.0e7, zt = a, s = 0.0;
+    if (i < n) {
+        x = r[i];
+        y = r[n + i];
+        const double z = r[2 * n + i];
+        if (wall) {
+            zt = z > a ? z : a;
+            const double t = z / a;
+            s = t >= 1.0 ? 1.0 : (t <= s_min ? s_min : t);
+        } else {
+            zt = z;
+            s = 1.0;
+        }
+        scale[i] = s;
+    }
+    float v[2 * NCH];
+#pragma unroll
+    for (int q = 0; q < 2 * NCH; ++q) v[q] = 0.0f;
+    const float xh = (float)x, yh = (float)y;
+    v[0] = xh;
+    v[1] = yh;
+    v[2] = (float)(x - (double)xh);
+    v[3] = (float)(y - (double)yh);
+    v[4] = (float)zt;
+    if (i < n)
+        for (int m = 0; m < k; ++m)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[5 + 3 * m + c] = (float)(s * (double)F[((int64_t)m * 3 + c) * n + i]);
+#pragma unroll
+    for (int c = 0; c < NCH; ++c)
+        *reinterpret_cast<float4*>(rec + rec2_off(i, c, LEN)) = make_float4(v[2 * c], v[2 * c], v[2 * c + 1], v[2 * c + 1]);
+}
+
+// record j of a staged tile -> packed operands (both lanes equal)
+template <int K>
+__device__ __forceinline__ void load_rec2(const float* st, int j, float2& xh, float2& yh, float2& xl, float2& yl,
+                                          float2& z, float2* f)
+{
+    const float4* p = reinterpret_cast<const float4*>(st) + j;
+    const float4 c0 = p[0], c1 = p[VT], c2 = p[2 * VT], c3 = p[3 * VT];
+    xh = make_float2(c0.x, c0.y);
+    yh = make_float2(c0.z, c0.w);
+    xl = make_float2(c1.x, c1.y);
+    yl = make_float2(c1.z, c1.w);
+    z = make_float2(c2.x, c2.y);
+    f[0] = make_float2(c2.z, c2.w);
+    f[1] = make_float2(c3.x, c3.y);
+    f[2] = make_float2(c3.z, c3.w);
+    if constexpr (K == 2) {
+        const float4 c4 = p[4 * VT], c5 = p[5 * VT];
+        f[3] = make_float2(c4.x, c4.y);
+        f[4] = make_float2(c4.z, c4.w);
+        f[5] = make_float2(c5.x, c5.y);
+    }
+}
+
+template <int K, int V>
+struct Sym2Var {
+    static constexpr int UNR = V == 0 ? 2 : (V == 1 ? 1 : (V == 2 ? 2 : 4));
+    static constexpr int MINB = V == 2 ? 3 : 4;
+};
+
+template <int K, int UNR, int MINB>
+__global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict__ rec, int64_t n, int64_t n_pad,
+                                                  const SymItem* __restrict__ items, int n_home_tiles,
+                                                  PairConst<float> pc1, float* __restrict__ partial,
+                                                  int* __restrict__ err_flag)
+{
+    constexpr int LEN = Rec2<K>::LEN;
+    constexpr uint32_t TILE_BYTES = VT * LEN * sizeof(float);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* stage = reinterpret_cast<float*>(smem_raw);
+    float* red = reinterpret_cast<float*>(smem_raw + NST * TILE_BYTES);  // [2 buffers][4 warps][VT][3K]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + NST * TILE_BYTES + 2 * 4 * VT * 3 * K * sizeof(float));
+    const SymItem it = items[blockIdx.x];
+    const bool diag = it.slot == 0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t i0 = (int64_t)it.home * HT2 + warp * 64 + lane, i1 = i0 + 32;  // home blobs (< n_pad)
+    const PairConstX2 pc = PairConstX2::make(pc1);
+    const float2 m1 = pc.m1;
+
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < NST; ++s) mbar_init(&bar[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int s = 0; s < NST && s < it.ntile; ++s) {
+            mbar_expect_tx(&bar[s], TILE_BYTES);
+            tma_load_1d(stage + (size_t)s * VT * LEN, rec + ((size_t)it.v0 + (size_t)s * VT) * LEN, TILE_BYTES, &bar[s]);
+        }
+    float2 hxh, hyh, hxl, hyl, hz, hf[3 * K];
+    {
+        float4 a[Rec2<K>::NCH], b[Rec2<K>::NCH];
+#pragma unroll
+        for (int c = 0; c < Rec2<K>::NCH; ++c) {
+            a[c] = *reinterpret_cast<const float4*>(rec + rec2_off(i0, c, LEN));
+            b[c] = *reinterpret_cast<const float4*>(rec + rec2_off(i1, c, LEN));
+        }
+        hxh = make_float2(a[0].x, b[0].x);
+        hyh = make_float2(a[0].z, b[0].z);
+        hxl = make_float2(a[1].x, b[1].x);
+        hyl = make_float2(a[1].z, b[1].z);
+        hz = make_float2(a[2].x, b[2].x);
+        hf[0] = make_float2(a[2].z, b[2].z);
+        hf[1] = make_float2(a[3].x, b[3].x);
+        hf[2] = make_float2(a[3].z, b[3].z);
+        if constexpr (K == 2) {
+            hf[3] = make_float2(a[4].x, b[4].x);
+            hf[4] = make_float2(a[4].z, b[4].z);
+            hf[5] = make_float2(a[5].x, b[5].x);
+        }
+    }
+    float2 acc[3 * K];
+#pragma unroll
+    for (int q = 0; q < 3 * K; ++q) acc[q] = make_float2(0.0f, 0.0f);
+
+    int t = 0;
+    bool bad = false;
+    for (; t < it.ntile; ++t) {
+        const int s = t % NST;
+        const bool ok = mbar_wait_bounded(&bar[s], (t / NST) & 1);
+        const float* st = stage + (size_t)s * VT * LEN;
+        if (ok && diag) {
+            // one direction, every lane on the same source (broadcast reads)
+#pragma unroll 2
+            for (int jj = 0; jj < VT; ++jj) {
+                float2 xh, yh, xl, yl, zj, f[3 * K];
+                load_rec2<K>(st, jj, xh, yh, xl, yl, zj, f);
+                const float2 dx = add2(fma2(m1, xh, hxh), fma2(m1, xl, hxl));
+                const float2 dy = add2(fma2(m1, yh, hyh), fma2(m1, yl, hyl));
+                const float2 dz = fma2(m1, zj, hz);
+                float2 al, be, gx, gz, mzz;
+                pair_factors_x2(dx, dy, dz, hz, zj, pc, al, be, gx, gz, mzz);
+#pragma unroll
+                for (int m = 0; m < K; ++m) {
+                    const float2 fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
+                    const float2 P = fma2(dy, fy, mul2(dx, fx));
+                    const float2 Q = fma2(be, P, mul2(gx, fz));
+                    acc[3 * m + 0] = fma2(dx, Q, fma2(al, fx, acc[3 * m + 0]));
+                    acc[3 * m + 1] = fma2(dy, Q, fma2(al, fy, acc[3 * m + 1]));
+                    acc[3 * m + 2] = fma2(mzz, fz, fma2(gz, P, acc[3 * m + 2]));
+                }
+            }
+        } else if (ok) {
+            // both directions; lane l takes visitor (step + l) mod 32
+            float2 vacc[3 * K];
+#pragma unroll
+            for (int q = 0; q < 3 * K; ++q) vacc[q] = make_float2(0.0f, 0.0f);
+#pragma unroll UNR
+            for (int step = 0; step < VT; ++step) {
+                const int v = (step + lane) & (VT - 1);
+                float2 xh, yh, xl, yl, zj, f[3 * K];
+                load_rec2<K>(st, v, xh, yh, xl, yl, zj, f);
+                const float2 dx = add2(fma2(m1, xh, hxh), fma2(m1, xl, hxl));
+                const float2 dy = add2(fma2(m1, yh, hyh), fma2(m1, yl, hyl));
+                const float2 dz = fma2(m1, zj, hz);
+                float2 al, be, gx, gz, mzz;
+                pair_factors_x2(dx, dy, dz, hz, zj, pc, al, be, gx, gz, mzz);
+#pragma unroll
+                for (int m = 0; m < K; ++m) {
+                    const float2 fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
+                    const float2 P = fma2(dy, fy, mul2(dx, fx));
+                    const float2 Q = fma2(be, P, mul2(gx, fz));
+                    acc[3 * m + 0] = fma2(dx, Q, fma2(al, fx, acc[3 * m + 0]));
+                    acc[3 * m + 1] = fma2(dy, Q, fma2(al, fy, acc[3 * m + 1]));
+                    acc[3 * m + 2] = fma2(mzz, fz, fma2(gz, P, acc[3 * m + 2]));
+                    // M^T applied to the home forces
+                    const float2 hx = hf[3 * m], hy = hf[3 * m + 1], hzf = hf[3 * m + 2];
+                    const float2 Pt = fma2(dy, hy, mul2(dx, hx));
+                    const float2 Qt = fma2(be, Pt, mul2(gz, hzf));
+                    vacc[3 * m + 0] = fma2(dx, Qt, fma2(al, hx, vacc[3 * m + 0]));
+                    vacc[3 * m + 1] = fma2(dy, Qt, fma2(al, hy, vacc[3 * m + 1]));
+                    vacc[3 * m + 2] = fma2(mzz, hzf, fma2(gx, Pt, vacc[3 * m + 2]));
+                }
+                // hand the visitor sums to the lane that takes that visitor next
+#pragma unroll
+                for (int q = 0; q < 3 * K; ++q) {
+                    vacc[q].x = __shfl_sync(0xffffffffu, vacc[q].x, (lane + 1) & 31);
+                    vacc[q].y = __shfl_sync(0xffffffffu, vacc[q].y, (lane + 1) & 31);
+                }
+            }
+            // lane l now holds visitor l's sums over this warp's 64 homes
+            float* rb = red + (t & 1) * (4 * VT * 3 * K);  // double-buffered: one barrier per tile
+#pragma unroll
+            for (int q = 0; q < 3 * K; ++q) rb[(warp * VT + lane) * 3 * K + q] = vacc[q].x + vacc[q].y;
+        }
+        if (__syncthreads_or(!ok)) {
+            bad = true;
+            break;
+        }
+        if (!diag) {
+            const float* rb = red + (t & 1) * (4 * VT * 3 * K);
+            const int64_t vbase = (int64_t)it.v0 + (int64_t)t * VT;
+            for (int e = tid; e < VT * 3 * K; e += HT) {
+                const int vl = e / (3 * K), q = e % (3 * K);
+                const int64_t vg = vbase + vl;
+                if (vg < n) {
+                    const float sum = rb[(0 * VT + vl) * 3 * K + q] + rb[(1 * VT + vl) * 3 * K + q] +
+                                      rb[(2 * VT + vl) * 3 * K + q] + rb[(3 * VT + vl) * 3 * K + q];
+                    partial[((int64_t)it.home * 3 * K + q) * n_pad + vg] = sum;
+                }
+            }
+        }
+        if (tid == 0 && t + NST < it.ntile) {
+            fence_proxy_async();
+            mbar_expect_tx(&bar[s], TILE_BYTES);
+            tma_load_1d(stage + (size_t)s * VT * LEN, rec + ((size_t)it.v0 + (size_t)(t + NST) * VT) * LEN, TILE_BYTES,
+                        &bar[s]);
+        }
+    }
+    if (bad) {
+        if (tid == 0) {
+            atomicExch(err_flag, 1);
+            for (int u = t + 1; u < it.ntile && u < t + NST; ++u) mbar_wait_bounded(&bar[u % NST], (u / NST) & 1);
+        }
+        return;
+    }
+    const int slot = n_home_tiles + it.slot;
+#pragma unroll
+    for (int q = 0; q < 3 * K; ++q) {
+        if (i0 < n) partial[((int64_t)slot * 3 * K + q) * n_pad + i0] = acc[q].x;
+        if (i1 < n) partial[((int64_t)slot * 3 * K + q) * n_pad + i1] = acc[q].y;
+    }
+}
+
+template <int K, class In, class Out>
+static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
+{
+    constexpr int LEN = Rec2<K>::LEN;
+    const int64_t n_pad = (n + HT2 - 1) / HT2 * HT2;
+    SymItem* items;
+    int n_items, n_home, max_slots;
+    RPBD_TRY(get_items<HT2>(h, 1, n, n_pad, &items, &n_items, &n_home, &max_slots));
+    float* rec;
+    double* scale;
+    float* partial;
+    RPBD_TRY(ensure_t(h, BUF_PACK, (size_t)n_pad * LEN, &rec));
+    RPBD_TRY(ensure_t(h, BUF_SCALE, (size_t)n_pad, &scale));
+    RPBD_TRY(ensure_t(h, BUF_PARTIAL, (size_t)(n_home + max_slots) * 3 * K * n_pad, &partial));
+    pack2_kernel<K, In><<<(unsigned)((n_pad + 255) / 256), 256, 0, st>>>(n, n_pad, k, r, F, h->p.a, h->p.wall,
+                                                                         h->p.s_min, rec, scale);
+    count_launch();
+    const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 2 * 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
+    const PairConst<float> pc = PairConst<float>::make(h->p.a, h->p.Lx, h->p.Ly);
+    if (h->profile) prof_begin(h, st);
+    const int sv = h->sym_variant[sym_class(K)];
+    switch (sv >= 0 ? sv : 0) {  // tuning variants: (visitor-loop unroll, min CTAs per SM), see Sym2Var
+    case 1: sym2_kernel<K, Sym2Var<K, 1>::UNR, Sym2Var<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    case 2: sym2_kernel<K, Sym2Var<K, 2>::UNR, Sym2Var<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    case 3: sym2_kernel<K, Sym2Var<K, 3>::UNR, Sym2Var<K, 3>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    default: sym2_kernel<K, Sym2Var<K, 0>::UNR, Sym2Var<K, 0>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    }
+    count_launch();
+    if (h->profile) prof_end(h, st, 4 /* symmetric, factored */, K, (double)n * (double)n);
+    const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
+    const int nseg = (n_home + SEG - 1) / SEG;
+    double* segsum;
+    RPBD_TRY(ensure_t(h, BUF_SYM_SEG, (size_t)nseg * 3 * K * n_pad, &segsum));
+    reduce_visitors_kernel<HT2, K, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)nseg), 256, 0, st>>>(
+        n, n_pad, k, partial, segsum);
+    count_launch();
+    reduce_kernel<HT2, float, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_home, CHUNK,
+                                                                                partial, segsum, scale, inv8pieta, U);
     count_launch();
     RPBD_LAUNCH_CHECK(h);
     return RPBD_OK;
@@ -442,6 +752,8 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
 template <int K, class In, class Out>
 static int sym_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
 {
+    if constexpr (K <= 2)
+        if (h->use_packed && h->p.wall && !(h->p.Lx > 0.0)) return sym::run2<K>(h, n, r, F, U, k, st);
     if (h->p.Lx > 0.0) return sym::run<K, true, true>(h, n, r, F, U, k, st);
     return h->p.wall ? sym::run<K, true, false>(h, n, r, F, U, k, st) : sym::run<K, false, false>(h, n, r, F, U, k, st);
 }

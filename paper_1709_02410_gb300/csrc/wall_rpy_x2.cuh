@@ -1,0 +1,104 @@
+// Two wall-RPY pair blocks at once in packed two-wide FP32 arithmetic.
+//
+// The same five block scalars as pair_factors in wall_rpy.cuh (free-space
+// c1, c2 and the wall part in the reduced variables s^2, e_z^2,
+// zi zj/|R|^2), for two pairs held in the .x and .y lanes of float2 values,
+// so every add / multiply / FMA is one packed instruction for both pairs.
+// Used by the symmetric kernel, which gives each thread two home blobs
+// against the same visitor.  Only the open cell with the wall is covered
+// (the default path); overlapping pairs (r < 2a) and self pairs take a
+// scalar branch per lane, as in the one-pair form.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "wall_rpy.cuh"
+
+namespace rpbd {
+
+__device__ __forceinline__ float2 bc2(float a) { return make_float2(a, a); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+
+// Constants of the packed form, each duplicated into both lanes.
+struct PairConstX2 {
+    float2 a2, a23, m2a2, one, third, m1;
+    float four_a2, k_self, k_ovl, inv8a2;
+    __device__ static PairConstX2 make(const PairConst<float>& c)
+    {
+        PairConstX2 p;
+        p.a2 = bc2(c.a2);
+        p.a23 = bc2(c.a23);
+        p.m2a2 = bc2(-c.two_a2);
+        p.one = bc2(1.0f);
+        p.third = bc2(1.0f / 3.0f);
+        p.m1 = bc2(-1.0f);
+        p.four_a2 = c.four_a2;
+        p.k_self = c.k_self;
+        p.k_ovl = c.k_ovl;
+        p.inv8a2 = c.inv8a2;
+        return p;
+    }
+};
+
+// free-space coefficients of one lane in the rare overlapping / self case
+__device__ __forceinline__ void overlap_fix(float r2, float rinv, const PairConstX2& c, float& c1, float& c2)
+{
+    if (r2 < c.four_a2) {
+        if (r2 > 0.0f) {
+            c1 = c.k_self - c.k_ovl * (r2 * rinv);
+            c2 = rinv * c.inv8a2;
+        } else {
+            c1 = c.k_self;
+            c2 = 0.0f;
+        }
+    }
+}
+
+// alpha, beta, gx, gz, Mzz of two pairs (see pair_factors for the formulas)
+__device__ __forceinline__ void pair_factors_x2(float2 dx, float2 dy, float2 dz, float2 zi, float2 zj,
+                                                const PairConstX2& c, float2& alpha, float2& beta, float2& gx,
+                                                float2& gz, float2& Mzz)
+{
+    const float2 rho2 = fma2(dy, dy, mul2(dx, dx));
+    const float2 r2 = fma2(dz, dz, rho2);
+    const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
+    const float2 rinv2 = mul2(rinv, rinv);
+    const float2 rinv3 = mul2(rinv, rinv2);
+    float2 c1 = fma2(c.a23, rinv3, rinv);
+    float2 c2 = mul2(rinv3, fma2(c.m2a2, rinv2, c.one));
+    if (r2.x < c.four_a2 || r2.y < c.four_a2) {
+        overlap_fix(r2.x, rinv.x, c, c1.x, c2.x);
+        overlap_fix(r2.y, rinv.y, c, c1.y, c2.y);
+    }
+    // wall part
+    const float2 Rz = add2(zi, zj);
+    const float2 q = mul2(Rz, Rz);
+    const float2 R2 = add2(rho2, q);
+    const float2 Rinv = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
+    const float2 w = mul2(Rinv, Rinv);
+    const float2 v = mul2(Rinv, w);
+    const float2 sg = mul2(c.a2, w);   // s^2
+    const float2 sg2 = mul2(sg, sg);   // s^4
+    const float2 y = mul2(q, w);       // e_z^2
+    const float2 x1 = fma2(c.third, sg, mul2(mul2(zi, zj), w));
+    const float2 x2 = mul2(sg, fma2(c.third, sg, y));
+    const float2 x3 = mul2(sg2, y);
+    // A + 1 = 2 (x2 - x1) - 10/3 x3 ;  B + 1 = 6 x1 - 10 x2 + 70/3 x3
+    const float2 Ap = fma2(bc2(2.0f), add2(x2, mul2(c.m1, x1)), mul2(bc2(-10.0f / 3.0f), x3));
+    const float2 Bp = fma2(bc2(6.0f), x1, fma2(bc2(-10.0f), x2, mul2(bc2(70.0f / 3.0f), x3)));
+    const float2 P = fma2(c.m1, Bp, mul2(bc2(20.0f / 3.0f), sg2));
+    // Z = 20 x3 - 4 x2 - 4/3 s^4 - e_z^2 (B + 1)
+    const float2 Zd = fma2(c.m1, mul2(y, Bp), fma2(bc2(20.0f), x3, fma2(bc2(-4.0f), x2, mul2(bc2(-4.0f / 3.0f), sg2))));
+    alpha = fma2(Rinv, add2(Ap, c.m1), c1);
+    const float2 c2v = fma2(c.m1, v, c2);
+    beta = fma2(v, Bp, c2v);
+    const float2 base = mul2(dz, c2v);
+    const float2 vRP = mul2(mul2(v, Rz), P);
+    gx = add2(base, vRP);
+    gz = fma2(c.m1, vRP, base);
+    Mzz = fma2(Rinv, Zd, fma2(dz, base, alpha));
+}
+
+}  // namespace rpbd

@@ -88,13 +88,14 @@ def test_empty_is_noop():
     assert U.numel() == 0
 
 
-def test_f32_k16_full_size_row_sampled():
-    """65,535 blobs, 16 right-hand sides, in the bench's launch configuration;
-    128 sampled target rows against the oracle."""
+@pytest.mark.parametrize("k", [1, 2, 16])
+def test_f32_full_size_row_sampled(k):
+    """65,535 blobs in the bench's launch configurations (k = 1, 2: packed
+    symmetric kernel; k = 16: one-direction kernel); 128 sampled target rows
+    (the first and last blob included) against the oracle."""
     s = synth.c1_boomerangs_65535()
     r = positions(s)
-    k = 16
-    F = synth.gaussian(40, (k, 3, s.n), np.float32)
+    F = synth.gaussian(40 + k, (k, 3, s.n), np.float32)
     h = handle_for(s)
     U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
     rows = np.random.default_rng(41).choice(s.n, 128, replace=False)
@@ -170,3 +171,35 @@ def test_fma_peak_probe():
     f64 = h.measure_fma_peak(F64)
     assert 1.0 < f32 < 1.2 * 80.55
     assert 0.0 < f64 < f32
+
+
+@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("n", [1, 31, 255, 256, 257, 700, 2049, 4500])
+def test_f32_packed_symmetric_kernel(k, n):
+    """The packed symmetric kernel (two homes per thread, 256-blob home tiles,
+    two-wide FP32 arithmetic) against the oracle and against the one-home
+    symmetric kernel: sizes below, at and across the 256-blob tile and the
+    2048-visitor chunk, blobs overlapping each other and the wall."""
+    rng = np.random.default_rng(11 * n + k)
+    box = max(2.0, np.sqrt(n))
+    r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
+    F = rng.standard_normal((k, 3, n)).astype(np.float32)
+    s = synth.c0_boomerangs_1920()
+    h = handle_for(s)
+    Up = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    h.set_packed(False)
+    Us = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
+    assert rel2(Up, Uo) <= 1e-5 and rel2(Us, Uo) <= 1e-5
+    assert rel2(Up, Us) <= 1e-5
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_f32_packed_variants(variant):
+    s = synth.c0_boomerangs_1920()
+    r = positions(s)
+    F = synth.gaussian(70 + variant, (2, 3, s.n), np.float32)
+    h = handle_for(s)
+    h.set_sym_variant(variant)
+    U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    assert rel2(U, om.apply(r, F.astype(np.float64), oracle_params(s))) <= 1e-5
