@@ -29,10 +29,14 @@ namespace rpbd {
 
 template <class R, int K>
 struct Rec;
-// FP32: [x_hi, y_hi, x_lo, y_lo][z~, F(0,x), F(0,y), F(0,z), F(1,x) ...] padded to 4 floats
+// FP32, k = 1: [x_hi, y_hi, x_lo, y_lo][z~, F(0,x), F(0,y), F(0,z)].
+// FP32, k >= 2 (even): the right-hand sides interleaved in pairs, so one
+// 8-byte lane pair holds the same component of two of them:
+//   [x_hi, y_hi, x_lo, y_lo][z~, 0, F(0,x), F(1,x), F(0,y), F(1,y), F(0,z), F(1,z), F(2,x), F(3,x) ...]
+// padded to 4 floats.
 template <int K>
 struct Rec<float, K> {
-    static constexpr int TAIL = ((1 + 3 * K) + 3) / 4 * 4;
+    static constexpr int TAIL = K == 1 ? 4 : ((2 + 3 * K) + 3) / 4 * 4;
     static constexpr int LEN = 4 + TAIL;  // floats
 };
 // FP64: [x, y, z~, F(0,x), F(0,y), F(0,z), ...] padded to 2 doubles
@@ -143,8 +147,11 @@ __global__ void pack_kernel(int64_t n, int64_t n_pad, int k, const double* __res
         if (i < n)
             for (int m = 0; m < k; ++m)
 #pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    o[5 + 3 * m + c] = (float)(s * (double)F[((int64_t)m * 3 + c) * n + i]);
+                for (int c = 0; c < 3; ++c) {
+                    const float v = (float)(s * (double)F[((int64_t)m * 3 + c) * n + i]);
+                    if constexpr (K == 1) o[5 + c] = v;
+                    else o[6 + 6 * (m / 2) + 2 * c + (m & 1)] = v;
+                }
     } else {
         o[0] = x;
         o[1] = y;
@@ -203,9 +210,17 @@ __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, 
         xh = me[0]; yh = me[1]; zi = me[2];
     }
 
-    R acc[3 * K];
+    // FP32 with k >= 2: accumulators of right-hand-side pairs (2p, 2p+1) in
+    // the .x / .y lanes, updated by two-wide FMAs against the broadcast block
+    constexpr bool PK = sizeof(R) == 4 && K >= 2;
+    constexpr int NA = PK ? 3 * K : 1;  // scalar accumulators, or float2 pairs below
+    R acc[PK ? 1 : 3 * K];
+    float2 acc2[PK ? 3 * K / 2 : 1];
 #pragma unroll
-    for (int q = 0; q < 3 * K; ++q) acc[q] = R(0);
+    for (int q = 0; q < (PK ? 1 : 3 * K); ++q) acc[q] = R(0);
+#pragma unroll
+    for (int q = 0; q < (PK ? 3 * K / 2 : 1); ++q) acc2[q] = make_float2(0.0f, 0.0f);
+    (void)NA;
 
     int t = 0;
     bool bad = false;
@@ -234,7 +249,7 @@ __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, 
                     }
                     zj = tail[0];
 #pragma unroll
-                    for (int q = 0; q < 3 * K; ++q) f[q] = tail[1 + q];
+                    for (int q = 0; q < 3 * K; ++q) f[q] = tail[(K == 1 ? 1 : 2) + q];
                 } else {
                     dx = xh - rj[0];
                     dy = yh - rj[1];
@@ -245,13 +260,29 @@ __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, 
                 const R dz = zi - zj;
                 R Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz;
                 pair_block_images<R, R, WALL, PER>(dx, dy, dz, zi, zj, pc, Mxx, Mxy, Mxz, Myy, Myz, Mzx, Mzy, Mzz);
+                if constexpr (PK) {
+                    // two right-hand sides per instruction: f[6p + 2c + e] = F(2p + e, c)
+                    const float2 bxx = make_float2(Mxx, Mxx), bxy = make_float2(Mxy, Mxy), bxz = make_float2(Mxz, Mxz);
+                    const float2 byy = make_float2(Myy, Myy), byz = make_float2(Myz, Myz), bzx = make_float2(Mzx, Mzx);
+                    const float2 bzy = make_float2(Mzy, Mzy), bzz = make_float2(Mzz, Mzz);
 #pragma unroll
-                for (int m = 0; m < K; ++m) {
-                    // three FMA chains: 9 FMA per right-hand side
-                    const R fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
-                    acc[3 * m + 0] = fma(Mxz, fz, fma(Mxy, fy, fma(Mxx, fx, acc[3 * m + 0])));
-                    acc[3 * m + 1] = fma(Myz, fz, fma(Myy, fy, fma(Mxy, fx, acc[3 * m + 1])));
-                    acc[3 * m + 2] = fma(Mzz, fz, fma(Mzy, fy, fma(Mzx, fx, acc[3 * m + 2])));
+                    for (int pp = 0; pp < K / 2; ++pp) {
+                        const float2 fx = make_float2(f[6 * pp], f[6 * pp + 1]);
+                        const float2 fy = make_float2(f[6 * pp + 2], f[6 * pp + 3]);
+                        const float2 fz = make_float2(f[6 * pp + 4], f[6 * pp + 5]);
+                        acc2[3 * pp + 0] = __ffma2_rn(bxz, fz, __ffma2_rn(bxy, fy, __ffma2_rn(bxx, fx, acc2[3 * pp + 0])));
+                        acc2[3 * pp + 1] = __ffma2_rn(byz, fz, __ffma2_rn(byy, fy, __ffma2_rn(bxy, fx, acc2[3 * pp + 1])));
+                        acc2[3 * pp + 2] = __ffma2_rn(bzz, fz, __ffma2_rn(bzy, fy, __ffma2_rn(bzx, fx, acc2[3 * pp + 2])));
+                    }
+                } else {
+#pragma unroll
+                    for (int m = 0; m < K; ++m) {
+                        // three FMA chains: 9 FMA per right-hand side
+                        const R fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
+                        acc[3 * m + 0] = fma(Mxz, fz, fma(Mxy, fy, fma(Mxx, fx, acc[3 * m + 0])));
+                        acc[3 * m + 1] = fma(Myz, fz, fma(Myy, fy, fma(Mxy, fx, acc[3 * m + 1])));
+                        acc[3 * m + 2] = fma(Mzz, fz, fma(Mzy, fy, fma(Mzx, fx, acc[3 * m + 2])));
+                    }
                 }
             }
         }
@@ -276,8 +307,18 @@ __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, 
         return;
     }
     if (i < n) {
+        if constexpr (PK) {
 #pragma unroll
-        for (int q = 0; q < 3 * K; ++q) partial[((int64_t)chunk * 3 * K + q) * n_pad + i] = acc[q];
+            for (int pp = 0; pp < K / 2; ++pp)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    partial[((int64_t)chunk * 3 * K + 3 * (2 * pp) + c) * n_pad + i] = acc2[3 * pp + c].x;
+                    partial[((int64_t)chunk * 3 * K + 3 * (2 * pp + 1) + c) * n_pad + i] = acc2[3 * pp + c].y;
+                }
+        } else {
+#pragma unroll
+            for (int q = 0; q < 3 * K; ++q) partial[((int64_t)chunk * 3 * K + q) * n_pad + i] = acc[q];
+        }
     }
 }
 

@@ -495,6 +495,11 @@ __global__ void pack2_kernel(int64_t n, int64_t n_pad, int k, const double* __re
     float v[2 * NCH];
 #pragma unroll
     for (int q = 0; q < 2 * NCH; ++q) v[q] = 0.0f;
+    // lengths in units of a (the packed pair form takes a = 1)
+    const double ia = 1.0 / a;
+    x *= ia;
+    y *= ia;
+    zt *= ia;
     const float xh = (float)x, yh = (float)y;
     v[0] = xh;
     v[1] = yh;
@@ -533,17 +538,17 @@ __device__ __forceinline__ void load_rec2(const float* st, int j, float2& xh, fl
     }
 }
 
+// tuning variants (visitor-loop unroll, min CTAs per SM); chosen per K so no variant spills
 template <int K, int V>
 struct Sym2Var {
     static constexpr int UNR = V == 0 ? 2 : (V == 1 ? 1 : (V == 2 ? 2 : 4));
-    static constexpr int MINB = V == 2 ? 3 : 4;
+    static constexpr int MINB = K == 1 ? (V == 1 || V == 2 ? 5 : 4) : (V == 2 ? 3 : 4);
 };
 
 template <int K, int UNR, int MINB>
 __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict__ rec, int64_t n, int64_t n_pad,
                                                   const SymItem* __restrict__ items, int n_home_tiles,
-                                                  PairConst<float> pc1, float* __restrict__ partial,
-                                                  int* __restrict__ err_flag)
+                                                  float* __restrict__ partial, int* __restrict__ err_flag)
 {
     constexpr int LEN = Rec2<K>::LEN;
     constexpr uint32_t TILE_BYTES = VT * LEN * sizeof(float);
@@ -555,7 +560,7 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
     const bool diag = it.slot == 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t i0 = (int64_t)it.home * HT2 + warp * 64 + lane, i1 = i0 + 32;  // home blobs (< n_pad)
-    const PairConstX2 pc = PairConstX2::make(pc1);
+    const PairConstX2 pc = PairConstX2::make_unit();
     const float2 m1 = pc.m1;
 
     if (tid == 0) {
@@ -722,18 +727,18 @@ static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U,
                                                                          h->p.s_min, rec, scale);
     count_launch();
     const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 2 * 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
-    const PairConst<float> pc = PairConst<float>::make(h->p.a, h->p.Lx, h->p.Ly);
     if (h->profile) prof_begin(h, st);
     const int sv = h->sym_variant[sym_class(K)];
     switch (sv >= 0 ? sv : 0) {  // tuning variants: (visitor-loop unroll, min CTAs per SM), see Sym2Var
-    case 1: sym2_kernel<K, Sym2Var<K, 1>::UNR, Sym2Var<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
-    case 2: sym2_kernel<K, Sym2Var<K, 2>::UNR, Sym2Var<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
-    case 3: sym2_kernel<K, Sym2Var<K, 3>::UNR, Sym2Var<K, 3>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
-    default: sym2_kernel<K, Sym2Var<K, 0>::UNR, Sym2Var<K, 0>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    case 1: sym2_kernel<K, Sym2Var<K, 1>::UNR, Sym2Var<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, partial, h->dev_flag); break;
+    case 2: sym2_kernel<K, Sym2Var<K, 2>::UNR, Sym2Var<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, partial, h->dev_flag); break;
+    case 3: sym2_kernel<K, Sym2Var<K, 3>::UNR, Sym2Var<K, 3>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, partial, h->dev_flag); break;
+    default: sym2_kernel<K, Sym2Var<K, 0>::UNR, Sym2Var<K, 0>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, partial, h->dev_flag); break;
     }
     count_launch();
     if (h->profile) prof_end(h, st, 4 /* symmetric, factored */, K, (double)n * (double)n);
-    const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
+    // blocks were formed in units of a: M = M(a = 1) / a
+    const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta * h->p.a);
     const int nseg = (n_home + SEG - 1) / SEG;
     double* segsum;
     RPBD_TRY(ensure_t(h, BUF_SYM_SEG, (size_t)nseg * 3 * K * n_pad, &segsum));

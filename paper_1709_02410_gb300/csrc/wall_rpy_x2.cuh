@@ -5,9 +5,9 @@
 // zi zj/|R|^2), for two pairs held in the .x and .y lanes of float2 values,
 // so every add / multiply / FMA is one packed instruction for both pairs.
 // Used by the symmetric kernel, which gives each thread two home blobs
-// against the same visitor.  Only the open cell with the wall is covered
-// (the default path); overlapping pairs (r < 2a) and self pairs take a
-// scalar branch per lane, as in the one-pair form.
+// against the same visitor; lengths in units of a.  Only the open cell with
+// the wall is covered (the default path); overlapping pairs (r < 2a) and
+// self pairs take a scalar branch per lane, as in the one-pair form.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -21,23 +21,24 @@ __device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a
 __device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
 __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
 
-// Constants of the packed form, each duplicated into both lanes.
+// Constants of the packed form, each duplicated into both lanes.  Lengths
+// are in units of the blob radius (a = 1): the block is homogeneous of degree
+// -1 in length, so the caller scales positions by 1/a and the result by 1/a.
 struct PairConstX2 {
-    float2 a2, a23, m2a2, one, third, m1;
+    float2 a23, m2a2, one, third, m1;
     float four_a2, k_self, k_ovl, inv8a2;
-    __device__ static PairConstX2 make(const PairConst<float>& c)
+    __device__ static PairConstX2 make_unit()
     {
         PairConstX2 p;
-        p.a2 = bc2(c.a2);
-        p.a23 = bc2(c.a23);
-        p.m2a2 = bc2(-c.two_a2);
+        p.a23 = bc2(2.0f / 3.0f);
+        p.m2a2 = bc2(-2.0f);
         p.one = bc2(1.0f);
         p.third = bc2(1.0f / 3.0f);
         p.m1 = bc2(-1.0f);
-        p.four_a2 = c.four_a2;
-        p.k_self = c.k_self;
-        p.k_ovl = c.k_ovl;
-        p.inv8a2 = c.inv8a2;
+        p.four_a2 = 4.0f;
+        p.k_self = 4.0f / 3.0f;
+        p.k_ovl = 3.0f / 8.0f;
+        p.inv8a2 = 1.0f / 8.0f;
         return p;
     }
 };
@@ -79,7 +80,7 @@ __device__ __forceinline__ void pair_factors_x2(float2 dx, float2 dy, float2 dz,
     const float2 Rinv = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
     const float2 w = mul2(Rinv, Rinv);
     const float2 v = mul2(Rinv, w);
-    const float2 sg = mul2(c.a2, w);   // s^2
+    const float2 sg = w;               // s^2 = a^2 / |R|^2 with a = 1
     const float2 sg2 = mul2(sg, sg);   // s^4
     const float2 y = mul2(q, w);       // e_z^2
     const float2 x1 = fma2(c.third, sg, mul2(mul2(zi, zj), w));
