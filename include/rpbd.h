@@ -337,6 +337,10 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
  * matvecs with k <= 2 use the packed kernel (two home blobs per thread, both
  * pair blocks formed by two-wide FP32 instructions); 0: the one-home kernel. */
 #define RPBD_OPT_PACKED 3
+/* tile variant of the batched kernel (what rpbd_autotune_batched picks):
+ * -1 / 0: 128 targets x 64-source tiles, 1: 64 x 64, 2: 256 x 32, 3 (wall
+ * only): 256 targets, two per thread in packed two-wide FP32 x 64-source tiles. */
+#define RPBD_OPT_BATCH_VARIANT 4
 int rpbd_set_option(rpbd_handle* h, int option, int value);
 
 /* Times the FP32 matvec kernels on n blobs at r (k right-hand sides, zero

@@ -66,6 +66,10 @@ class Handle:
             raise RpbdError(f"{what}: {_native.STATUS.get(st, st)}: {msg}")
         return st
 
+    def set_batch_variant(self, v: int):
+        """tile variant of the batched kernel (-1 default, 0..3; 3: packed two targets per thread)"""
+        self._check(self.lib.rpbd_set_option(self.h, 4, int(v)), "set_option")
+
     def set_packed(self, on: bool):
         """k <= 2 symmetric matvecs (wall, open cell): packed two-homes-per-thread kernel (default) or not."""
         self._check(self.lib.rpbd_set_option(self.h, 3, int(bool(on))), "set_option")

@@ -248,6 +248,11 @@ int rpbd_set_option(rpbd_handle* h, int option, int value)
         for (int c = 0; c < 3; ++c) h->use_sym[c] = value != 0;
         return RPBD_OK;
     case RPBD_OPT_PACKED: h->use_packed = value != 0; return RPBD_OK;
+    case RPBD_OPT_BATCH_VARIANT:
+        if (value < -1 || value > 3) return set_error(h, RPBD_BAD_ARG, "batched variant must be -1..3");
+        if (value == 3 && !h->p.wall) return set_error(h, RPBD_BAD_ARG, "the packed batched variant needs the wall");
+        h->batch_variant = value;
+        return RPBD_OK;
     case RPBD_OPT_SYM_VARIANT:
         if (value < -1 || value > 3) return set_error(h, RPBD_BAD_ARG, "symmetric variant must be -1..3");
         for (int c = 0; c < 3; ++c) h->sym_variant[c] = value;

@@ -24,6 +24,7 @@
 
 #include "rpbd_internal.cuh"
 #include "wall_rpy.cuh"
+#include "wall_rpy_x2.cuh"
 
 namespace rpbd {
 
@@ -248,6 +249,175 @@ __global__ void __launch_bounds__(BT) bpair_kernel(const float* __restrict__ rec
     }
 }
 
+// Packed variant (wall only): each thread owns two targets (t and t + BT of
+// the item) and meets every source with both at once in packed two-wide FP32
+// instructions (wall_rpy_x2.cuh, lengths in units of a).  Source records
+// duplicate every field so a 16-byte load gives two packed operands:
+// [x_hi x_hi y_hi y_hi][x_lo x_lo y_lo y_lo][z z F0x F0x][F0y F0y F0z F0z]...
+template <int K>
+struct BRec2 {
+    static constexpr int LEN = (2 * (5 + 3 * K) + 3) / 4 * 4;
+};
+
+template <int K, class In>
+__global__ void bpack2_kernel(int n_sys, int64_t n_tot, int64_t rec_tot, int k, SysTab tab,
+                              const double* __restrict__ r, const In* __restrict__ F, double a, double s_min,
+                              float* __restrict__ rec, double* __restrict__ scale)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= rec_tot) return;
+    const int s = find_sys(tab.rec_off, n_sys, g);
+    const int64_t local = g - tab.rec_off[s];
+    const int64_t i = tab.off[s] + local;
+    const bool real = i < tab.off[s + 1];
+    constexpr int LEN = BRec2<K>::LEN;
+    float* o = rec + g * LEN;
+    double x = 1.0e7, y = 1.0e7, zt = a, sc = 0.0;
+    if (real) {
+        x = r[i];
+        y = r[n_tot + i];
+        const double z = r[2 * n_tot + i];
+        zt = z > a ? z : a;
+        const double t = z / a;
+        sc = t >= 1.0 ? 1.0 : (t <= s_min ? s_min : t);
+        scale[i] = sc;
+    }
+    const double ia = 1.0 / a;  // lengths in units of a
+    x *= ia;
+    y *= ia;
+    zt *= ia;
+    float v[LEN / 2];
+#pragma unroll
+    for (int q = 0; q < LEN / 2; ++q) v[q] = 0.0f;
+    const float xh = (float)x, yh = (float)y;
+    v[0] = xh;
+    v[1] = yh;
+    v[2] = (float)(x - (double)xh);
+    v[3] = (float)(y - (double)yh);
+    v[4] = (float)zt;
+    if (real)
+        for (int m = 0; m < k; ++m)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) v[5 + 3 * m + c] = (float)(sc * (double)F[((int64_t)m * 3 + c) * n_tot + i]);
+#pragma unroll
+    for (int q = 0; q < LEN / 2; ++q) {
+        o[2 * q] = v[q];
+        o[2 * q + 1] = v[q];
+    }
+}
+
+template <int K, int BT, int TS, int NST>
+__global__ void __launch_bounds__(BT) bpair2_kernel(const float* __restrict__ rec, SysTab tab,
+                                                    const Item* __restrict__ items, int n_items,
+                                                    int* __restrict__ queue, const int* __restrict__ active,
+                                                    float* __restrict__ partial, int64_t n_tot,
+                                                    int* __restrict__ err_flag)
+{
+    constexpr int LEN = BRec2<K>::LEN;
+    constexpr uint32_t TILE_BYTES = TS * LEN * sizeof(float);
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    float* stage = reinterpret_cast<float*>(smem_raw);
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + NST * TILE_BYTES);
+    __shared__ int s_item;
+    const int tid = threadIdx.x;
+    const PairConstX2 pc = PairConstX2::make_unit();
+    const float2 m1 = pc.m1;
+    if (tid == 0) {
+#pragma unroll
+        for (int s = 0; s < NST; ++s) bt::mbar_init(&bar[s], 1);
+        bt::fence_mbar_init();
+    }
+    __syncthreads();
+    uint32_t g = 0;  // tiles consumed by this CTA: ring stage g % NST, parity (g / NST) & 1
+    for (;;) {
+        if (tid == 0) s_item = atomicAdd(queue, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();
+        if (it >= n_items) break;
+        const Item w = items[it];
+        if (active && !active[w.sys]) continue;  // system already converged
+        const int64_t off = tab.off[w.sys];
+        const int64_t n_s = tab.off[w.sys + 1] - off;
+        const float* srec = rec + tab.rec_off[w.sys] * LEN;
+        const int64_t l0 = (int64_t)w.tgt0 + tid, l1 = l0 + BT;  // system-local targets
+        const int64_t c0 = l0 < n_s ? l0 : n_s - 1, c1 = l1 < n_s ? l1 : n_s - 1;
+        if (tid == 0) {
+            for (int s = 0; s < NST && s < w.ntile; ++s) {
+                const uint32_t st = (g + s) % NST;
+                bt::mbar_expect_tx(&bar[st], TILE_BYTES);
+                bt::tma_load_1d(stage + (size_t)st * TS * LEN, srec + (size_t)(w.tile0 + s) * TS * LEN, TILE_BYTES,
+                                &bar[st]);
+            }
+        }
+        const float* r0 = srec + c0 * LEN;
+        const float* r1 = srec + c1 * LEN;
+        const float2 xh = make_float2(r0[0], r1[0]), yh = make_float2(r0[2], r1[2]);
+        const float2 xl = make_float2(r0[4], r1[4]), yl = make_float2(r0[6], r1[6]);
+        const float2 zi = make_float2(r0[8], r1[8]);
+        float2 acc[3 * K];
+#pragma unroll
+        for (int q = 0; q < 3 * K; ++q) acc[q] = make_float2(0.0f, 0.0f);
+        bool bad = false;
+        int t = 0;
+        for (; t < w.ntile; ++t) {
+            const uint32_t st = (g + t) % NST;
+            const uint32_t par = ((g + t) / NST) & 1;
+            const bool ok = bt::mbar_wait_bounded(&bar[st], par);
+            if (ok) {
+                const float* sp = stage + (size_t)st * TS * LEN;
+#pragma unroll(K <= 4 ? 2 : 1)
+                for (int jj = 0; jj < TS; ++jj) {
+                    const float4* rj = reinterpret_cast<const float4*>(sp + jj * LEN);
+                    const float4 p0 = rj[0], p1 = rj[1], p2 = rj[2];
+                    const float2 dx = add2(fma2(m1, make_float2(p0.x, p0.y), xh), fma2(m1, make_float2(p1.x, p1.y), xl));
+                    const float2 dy = add2(fma2(m1, make_float2(p0.z, p0.w), yh), fma2(m1, make_float2(p1.z, p1.w), yl));
+                    const float2 zj = make_float2(p2.x, p2.y);
+                    const float2 dz = fma2(m1, zj, zi);
+                    float2 al, be, gx, gz, mzz;
+                    pair_factors_x2(dx, dy, dz, zi, zj, pc, al, be, gx, gz, mzz);
+                    // forces F(m, c) at float index 10 + 2 (3m + c) of the record
+#pragma unroll
+                    for (int m = 0; m < K; ++m) {
+                        const float* fp = sp + jj * LEN + 10 + 6 * m;
+                        const float2 fx = make_float2(fp[0], fp[1]), fy = make_float2(fp[2], fp[3]);
+                        const float2 fz = make_float2(fp[4], fp[5]);
+                        const float2 P = fma2(dy, fy, mul2(dx, fx));
+                        const float2 Q = fma2(be, P, mul2(gx, fz));
+                        acc[3 * m + 0] = fma2(dx, Q, fma2(al, fx, acc[3 * m + 0]));
+                        acc[3 * m + 1] = fma2(dy, Q, fma2(al, fy, acc[3 * m + 1]));
+                        acc[3 * m + 2] = fma2(mzz, fz, fma2(gz, P, acc[3 * m + 2]));
+                    }
+                }
+            }
+            if (__syncthreads_or(!ok)) {
+                bad = true;
+                break;
+            }
+            if (tid == 0 && t + NST < w.ntile) {
+                bt::fence_proxy_async();
+                bt::mbar_expect_tx(&bar[st], TILE_BYTES);
+                bt::tma_load_1d(stage + (size_t)st * TS * LEN, srec + (size_t)(w.tile0 + t + NST) * TS * LEN,
+                                TILE_BYTES, &bar[st]);
+            }
+        }
+        if (bad) {
+            if (tid == 0) {
+                atomicExch(err_flag, 1);
+                for (int u = t + 1; u < w.ntile && u < t + NST; ++u)
+                    bt::mbar_wait_bounded(&bar[(g + u) % NST], ((g + u) / NST) & 1);
+            }
+            return;
+        }
+        g += w.ntile;
+#pragma unroll
+        for (int q = 0; q < 3 * K; ++q) {
+            if (l0 < n_s) partial[((int64_t)w.slot * 3 * K + q) * n_tot + off + l0] = acc[q].x;
+            if (l1 < n_s) partial[((int64_t)w.slot * 3 * K + q) * n_tot + off + l1] = acc[q].y;
+        }
+    }
+}
+
 template <class Out>
 __global__ void breduce_kernel(int n_sys, int64_t n_tot, int k, int kt, SysTab tab, const float* __restrict__ partial,
                                const double* __restrict__ scale, const int* __restrict__ active, double inv8pieta,
@@ -271,9 +441,11 @@ __global__ void breduce_kernel(int n_sys, int64_t n_tot, int k, int kt, SysTab t
 
 struct Variant {
     int BT, TS;
+    bool packed;  // two targets per thread (wall only)
+    int targets() const { return packed ? 2 * BT : BT; }
 };
-static const Variant VARIANTS[] = {{128, 64}, {64, 64}, {256, 32}};
-constexpr int N_VARIANTS = 3;
+static const Variant VARIANTS[] = {{128, 64, false}, {64, 64, false}, {256, 32, false}, {128, 64, true}};
+constexpr int N_VARIANTS = 4;
 constexpr int B_NST = 3;
 constexpr int B_MAX_CHUNK = 2048;
 
@@ -302,6 +474,17 @@ static void free_plan(BatchPlan* p)
     cudaFree(p->d_items);
     cudaFree(p->d_queue);
     delete p;
+}
+
+template <int K, int BT, int TS>
+static int occupancy2(int* blocks)
+{
+    constexpr int LEN = BRec2<K>::LEN;
+    const size_t smem = (size_t)B_NST * TS * LEN * sizeof(float) + B_NST * sizeof(uint64_t);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks, bpair2_kernel<K, BT, TS, B_NST>, BT, smem) ==
+                   cudaSuccess
+               ? RPBD_OK
+               : RPBD_CUDA;
 }
 
 template <int K, int BT, int TS, bool WALL>
@@ -334,7 +517,7 @@ static int build_plan(rpbd_handle* h, const int64_t* off_host, int n_sys, int k,
         const int nch = (int)((ntiles + tpc - 1) / tpc);
         nslots[s] = nch;
         p->max_slots = std::max(p->max_slots, nch);
-        for (int64_t t0 = 0; t0 < n_s; t0 += V.BT)
+        for (int64_t t0 = 0; t0 < n_s; t0 += V.targets())
             for (int c = 0; c < nch; ++c) {
                 Item it;
                 it.sys = s;
@@ -414,6 +597,51 @@ static int run_variant(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r,
     return RPBD_OK;
 }
 
+template <int K, int BT, int TS, class In, class Out>
+static int run_variant2(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r, const In* F, Out* U, int k,
+                        const int* active, cudaStream_t st)
+{
+    constexpr int LEN = BRec2<K>::LEN;
+    const int64_t n_tot = p->off[n_sys];
+    float* rec;
+    double* scale;
+    float* partial;
+    RPBD_TRY(ensure_t(h, BUF_BPACK, (size_t)p->rec_tot * LEN, &rec));
+    RPBD_TRY(ensure_t(h, BUF_BSCALE, (size_t)n_tot, &scale));
+    RPBD_TRY(ensure_t(h, BUF_BPARTIAL, (size_t)p->max_slots * 3 * K * n_tot, &partial));
+    SysTab tab{p->d_off, p->d_rec_off, p->d_nslots};
+    bpack2_kernel<K, In><<<(unsigned)((p->rec_tot + 255) / 256), 256, 0, st>>>(n_sys, n_tot, p->rec_tot, k, tab, r, F,
+                                                                               h->p.a, h->p.s_min, rec, scale);
+    count_launch();
+    const size_t smem = (size_t)B_NST * TS * LEN * sizeof(float) + B_NST * sizeof(uint64_t);
+    auto kern = bpair2_kernel<K, BT, TS, B_NST>;
+    if (smem > 48 * 1024) RPBD_CU(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    if (p->grid == 0) {
+        int blocks = 0;
+        RPBD_TRY((occupancy2<K, BT, TS>(&blocks)));
+        p->grid = std::max(1, blocks) * h->sm_count;
+    }
+    RPBD_CU(h, cudaMemsetAsync(p->d_queue, 0, sizeof(int), st));
+    if (h->profile) prof_begin(h, st);
+    kern<<<p->grid, BT, smem, st>>>(rec, tab, p->d_items, p->n_items, p->d_queue, active, partial, n_tot, h->dev_flag);
+    count_launch();
+    if (h->profile) {
+        double pairs = 0.0;
+        for (int s = 0; s < n_sys; ++s) {
+            const double ns = (double)(p->off[s + 1] - p->off[s]);
+            pairs += ns * ns;
+        }
+        prof_end(h, st, 2 /* batched FP32 */, K, pairs);
+    }
+    // blocks were formed in units of a: M = M(a = 1) / a
+    const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta * h->p.a);
+    breduce_kernel<Out><<<(unsigned)((n_tot + 255) / 256), 256, 0, st>>>(n_sys, n_tot, k, K, tab, partial, scale,
+                                                                         active, inv8pieta, U);
+    count_launch();
+    RPBD_LAUNCH_CHECK(h);
+    return RPBD_OK;
+}
+
 template <int K, bool WALL, class In, class Out>
 static int run_k(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r, const In* F, Out* U, int k,
                  const int* active, cudaStream_t st)
@@ -421,6 +649,9 @@ static int run_k(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r, const
     switch (p->variant) {
     case 1: return run_variant<K, 64, 64, WALL>(h, p, n_sys, r, F, U, k, active, st);
     case 2: return run_variant<K, 256, 32, WALL>(h, p, n_sys, r, F, U, k, active, st);
+    case 3:
+        if constexpr (WALL) return run_variant2<K, 128, 64>(h, p, n_sys, r, F, U, k, active, st);
+        else return set_error(h, RPBD_BAD_ARG, "batched: the packed variant needs the wall");
     default: return run_variant<K, 128, 64, WALL>(h, p, n_sys, r, F, U, k, active, st);
     }
 }
@@ -509,6 +740,7 @@ int rpbd_autotune_batched(rpbd_handle* h, int n_sys, const int64_t* offsets, con
     double best = 1e300;
     int best_v = 0;
     for (int v = 0; v < N_VARIANTS; ++v) {
+        if (VARIANTS[v].packed && !h->p.wall) continue;
         h->batch_variant = v;
         RPBD_TRY(batched_apply_impl(h, n_sys, offsets, r, F, U, k, false, nullptr, st));  // warm-up, plan
         RPBD_CU(h, cudaEventRecord(e0, st));

@@ -729,7 +729,8 @@ static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U,
     const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 2 * 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
     if (h->profile) prof_begin(h, st);
     const int sv = h->sym_variant[sym_class(K)];
-    switch (sv >= 0 ? sv : 0) {  // tuning variants: (visitor-loop unroll, min CTAs per SM), see Sym2Var
+    switch (sv >= 0 ? sv : (K == 1 ? 2 : 3)) {  // tuning variants (unroll, min CTAs per SM), see Sym2Var;
+                                                 // -1: the measured default per K
     case 1: sym2_kernel<K, Sym2Var<K, 1>::UNR, Sym2Var<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, partial, h->dev_flag); break;
     case 2: sym2_kernel<K, Sym2Var<K, 2>::UNR, Sym2Var<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, partial, h->dev_flag); break;
     case 3: sym2_kernel<K, Sym2Var<K, 3>::UNR, Sym2Var<K, 3>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, partial, h->dev_flag); break;
