@@ -542,7 +542,7 @@ __device__ __forceinline__ void load_rec2(const float* st, int j, float2& xh, fl
 template <int K, int V>
 struct Sym2Var {
     static constexpr int UNR = V == 0 ? 2 : (V == 1 ? 1 : (V == 2 ? 2 : 4));
-    static constexpr int MINB = K == 1 ? (V == 1 || V == 2 ? 5 : 4) : (V == 2 ? 3 : 4);
+    static constexpr int MINB = K == 1 ? (V == 1 ? 6 : (V == 2 ? 5 : 4)) : (V == 2 ? 3 : 4);
 };
 
 template <int K, int UNR, int MINB>
