@@ -284,6 +284,7 @@ def run_ours(args, rank, world, local):
     row_times = measure_rows(h, r, shape, q0, th0, T, time_launch) if (rank == 0 and extras) else None
     batched = measure_batched(h.lib, dev, T) if (rank == 0 and extras) else None
     rollers = measure_rollers(dev, T) if (rank == 0 and extras and not args.no_rollers) else None
+    next_rows = measure_next_rows(dev, T, s, shape, q0, th0, forces, Lp) if (rank == 0 and extras) else None
 
     out = None
     if rank == 0:
@@ -372,6 +373,7 @@ def run_ours(args, rank, world, local):
             "rows": row_times,
             "batched_c4": batched,
             "ts_step_rollers_c3": rollers,
+            "next_rows": next_rows,
             "accuracy": acc,
             "wall_s_timed": wall,
         }
@@ -447,6 +449,63 @@ def measure_rows(h, r, shape, q, th, T, time_launch):
     fst = P.Forces(1.57e-11 * 9.81e6, 0.096, 0.162, 0.1, (0.0, 0.0, 0.0), 0.096, 0.162, 0.1, 0.0)
     fb = torch.empty_like(r)
     out["f4_steric_forces_f32_s"] = time_launch(lambda: h.blob_forces(r, fst, nper=NPER, dtype=P.F32, out=fb), 3)
+    return out
+
+
+# ---------------------------------------------------------------------------
+# the other integrators (f2) on the bench suspension, and the pseudo-periodic
+# cell (f1): the bench suspension in a periodic box, and the paper's 256
+# boomerangs in a 45.3 um cell
+
+def measure_next_rows(dev, T, s, shape, q0, th0, forces, Lp):
+    import torch
+    import paper_1709_02410_gb300 as P
+    from paper_1709_02410_gb300 import synth
+    from paper_1709_02410_gb300._native import StepParams
+    out = {}
+    sp = lambda i: StepParams(0.01, 1e-3, Lp, 1e-6, 1e-4, 300, 100, 80, P.F32, 99, i)
+    h = P.Handle(synth.ETA, s.a, synth.KT)
+    for kind in ("emt", "emrfd", "tt"):
+        q, th = q0.clone(), th0.clone()
+        fn = getattr(h, "step_" + kind)
+        fn(shape, q, th, forces, sp(0))          # warm-up: workspace, plans
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        st, status = fn(shape, q, th, forces, sp(1))
+        e1.record()
+        torch.cuda.synchronize()
+        out[f"f2_step_{kind}_s"] = e0.elapsed_time(e1) / 1e3
+        out[f"f2_step_{kind}_iterations"] = [x["iterations"] for x in st]
+    # f1: periodic images, k = 1 FP32 matvec (9 images per pair) on the bench suspension
+    L = 40.0 * np.sqrt(NB / 128)
+    hp = P.Handle(synth.ETA, s.a, synth.KT, Lx=L, Ly=L)
+    r = hp.blobs_from_bodies(shape, q0, th0)
+    F = T(synth.gaussian(500, (1, 3, r.shape[1])), torch.float32)
+    U = torch.empty_like(F)
+    hp.mobility_apply(r, F, out=U)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(2):
+        hp.mobility_apply(r, F, out=U)
+    e1.record()
+    torch.cuda.synchronize()
+    tp = e0.elapsed_time(e1) / 2e3
+    out["f1_periodic_f32_k1_s"] = tp
+    out["f1_periodic_pair_images_per_s"] = 9.0 * r.shape[1] ** 2 / tp
+    # f1: T-S step of the paper's periodic boomerang suspension (256 bodies, 45.3 um cell, Sec. 4.2)
+    sc = synth.boomerang_suspension(256, 45.3, 7)
+    hc = P.Handle(synth.ETA, sc.a, synth.KT, Lx=45.3, Ly=45.3)
+    shc, qc, thc = T(sc.shape), T(sc.q), T(sc.theta)
+    hc.step_ts(shc, qc, thc, forces, sp(0))
+    torch.cuda.synchronize()
+    e0.record()
+    st, status = hc.step_ts(shc, qc, thc, forces, sp(1))
+    e1.record()
+    torch.cuda.synchronize()
+    out["f1_ts_step_256_boomerangs_periodic_s"] = e0.elapsed_time(e1) / 1e3
+    out["f1_ts_step_256_boomerangs_iterations"] = [x["iterations"] for x in st]
     return out
 
 

@@ -80,19 +80,19 @@ __device__ __forceinline__ void pair_factors_x2(float2 dx, float2 dy, float2 dz,
     const float2 Rinv = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
     const float2 w = mul2(Rinv, Rinv);
     const float2 v = mul2(Rinv, w);
-    const float2 sg = w;               // s^2 = a^2 / |R|^2 with a = 1
-    const float2 sg2 = mul2(sg, sg);   // s^4
+    // with a = 1: s^2 = w, so x1 = w (zi zj + 1/3), x2 = w (e_z^2 + w/3)
+    const float2 sg2 = mul2(w, w);     // s^4
     const float2 y = mul2(q, w);       // e_z^2
-    const float2 x1 = fma2(c.third, sg, mul2(mul2(zi, zj), w));
-    const float2 x2 = mul2(sg, fma2(c.third, sg, y));
+    const float2 x1 = mul2(w, fma2(zi, zj, c.third));
+    const float2 x2 = mul2(w, fma2(c.third, w, y));
     const float2 x3 = mul2(sg2, y);
-    // A + 1 = 2 (x2 - x1) - 10/3 x3 ;  B + 1 = 6 x1 - 10 x2 + 70/3 x3
-    const float2 Ap = fma2(bc2(2.0f), add2(x2, mul2(c.m1, x1)), mul2(bc2(-10.0f / 3.0f), x3));
+    // A = 2 (x2 - x1) - 10/3 x3 - 1 ;  B + 1 = 6 x1 - 10 x2 + 70/3 x3
+    const float2 A = fma2(bc2(2.0f), fma2(c.m1, x1, x2), fma2(bc2(-10.0f / 3.0f), x3, c.m1));
     const float2 Bp = fma2(bc2(6.0f), x1, fma2(bc2(-10.0f), x2, mul2(bc2(70.0f / 3.0f), x3)));
     const float2 P = fma2(c.m1, Bp, mul2(bc2(20.0f / 3.0f), sg2));
     // Z = 20 x3 - 4 x2 - 4/3 s^4 - e_z^2 (B + 1)
     const float2 Zd = fma2(c.m1, mul2(y, Bp), fma2(bc2(20.0f), x3, fma2(bc2(-4.0f), x2, mul2(bc2(-4.0f / 3.0f), sg2))));
-    alpha = fma2(Rinv, add2(Ap, c.m1), c1);
+    alpha = fma2(Rinv, A, c1);
     const float2 c2v = fma2(c.m1, v, c2);
     beta = fma2(v, Bp, c2v);
     const float2 base = mul2(dz, c2v);

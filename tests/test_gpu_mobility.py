@@ -194,11 +194,12 @@ def test_f32_packed_symmetric_kernel(k, n):
     assert rel2(Up, Us) <= 1e-5
 
 
+@pytest.mark.parametrize("k", [1, 2])
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
-def test_f32_packed_variants(variant):
+def test_f32_packed_variants(variant, k):
     s = synth.c0_boomerangs_1920()
     r = positions(s)
-    F = synth.gaussian(70 + variant, (2, 3, s.n), np.float32)
+    F = synth.gaussian(70 + variant, (k, 3, s.n), np.float32)
     h = handle_for(s)
     h.set_sym_variant(variant)
     U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
