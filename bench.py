@@ -37,8 +37,8 @@ F_GEOM = 76                  # algorithmic flops of one pair block (FMA = 2, rsq
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/pair_kernel_f32_k*_boomerangs_65535.md); None when not captured
-NCU_TRAFFIC = {"f32_k16": 22067968 + 343998464, "f32symf_k1": 4489216 + 54942208,
-               "f32symf_k2": 9583616 + 168398848}
+NCU_TRAFFIC = {"f32_k16": 22067968 + 343998464, "f32symf_k1": 4379392 + 55015936,
+               "f32symf_k2": 8208640 + 168576256}
 
 
 F_ASSEMBLY = 12             # flops of forming the 9 entries from the block's 5 scalars
