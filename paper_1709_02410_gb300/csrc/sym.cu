@@ -445,8 +445,8 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
 }
 
 // ---------------------------------------------------------------------------
-// Packed variant for k <= 2 in an open cell with the wall (the Krylov
-// matvecs of a time step).  Each thread holds two home blobs (256 per CTA)
+// Packed variant for k <= 4 with the wall, open or pseudo-periodic cell (k =
+// 1, 2: the Krylov matvecs of a time step).  Each thread holds two home blobs (256 per CTA)
 // and meets every visitor with both at once: the two pair blocks are formed
 // in the .x / .y lanes of float2 values with packed two-wide FP32
 // instructions (wall_rpy_x2.cuh), so one instruction stream serves two pairs.
@@ -461,7 +461,8 @@ constexpr int HT2 = 256;  // home blobs per CTA, two per thread
 
 template <int K>
 struct Rec2 {
-    static constexpr int NCH = K == 1 ? 4 : 6;  // 16-byte chunks per record
+    static constexpr int NV = 5 + 3 * K;        // values: x_hi, y_hi, x_lo, y_lo, z, forces
+    static constexpr int NCH = (NV + 1) / 2;    // 16-byte chunks per record (two values each)
     static constexpr int LEN = 4 * NCH;         // floats per record
 };
 
@@ -515,40 +516,93 @@ __global__ void pack2_kernel(int64_t n, int64_t n_pad, int k, const double* __re
         *reinterpret_cast<float4*>(rec + rec2_off(i, c, LEN)) = make_float4(v[2 * c], v[2 * c], v[2 * c + 1], v[2 * c + 1]);
 }
 
-// record j of a staged tile -> packed operands (both lanes equal)
+// record j of a staged tile -> packed operands (both lanes equal); value m
+// sits in chunk m / 2, lanes (0, 1) for even m and (2, 3) for odd m
 template <int K>
 __device__ __forceinline__ void load_rec2(const float* st, int j, float2& xh, float2& yh, float2& xl, float2& yl,
                                           float2& z, float2* f)
 {
     const float4* p = reinterpret_cast<const float4*>(st) + j;
-    const float4 c0 = p[0], c1 = p[VT], c2 = p[2 * VT], c3 = p[3 * VT];
-    xh = make_float2(c0.x, c0.y);
-    yh = make_float2(c0.z, c0.w);
-    xl = make_float2(c1.x, c1.y);
-    yl = make_float2(c1.z, c1.w);
-    z = make_float2(c2.x, c2.y);
-    f[0] = make_float2(c2.z, c2.w);
-    f[1] = make_float2(c3.x, c3.y);
-    f[2] = make_float2(c3.z, c3.w);
-    if constexpr (K == 2) {
-        const float4 c4 = p[4 * VT], c5 = p[5 * VT];
-        f[3] = make_float2(c4.x, c4.y);
-        f[4] = make_float2(c4.z, c4.w);
-        f[5] = make_float2(c5.x, c5.y);
+    float2 v[2 * Rec2<K>::NCH];
+#pragma unroll
+    for (int c = 0; c < Rec2<K>::NCH; ++c) {
+        const float4 q = p[c * VT];
+        v[2 * c] = make_float2(q.x, q.y);
+        v[2 * c + 1] = make_float2(q.z, q.w);
+    }
+    xh = v[0];
+    yh = v[1];
+    xl = v[2];
+    yl = v[3];
+    z = v[4];
+#pragma unroll
+    for (int q = 0; q < 3 * K; ++q) f[q] = v[5 + q];
+}
+
+// Both directions (BOTH) or the home direction only, for one pair separation
+// in packed form: acc += M f (visitor forces f), vacc += M^T hf (home forces).
+template <int K, bool BOTH>
+__device__ __forceinline__ void pair_apply2(float2 dx, float2 dy, float2 dz, float2 hz, float2 zj,
+                                            const PairConstX2& pc, const float2* f, const float2* hf, float2* acc,
+                                            float2* vacc)
+{
+    float2 al, be, gx, gz, mzz;
+    pair_factors_x2(dx, dy, dz, hz, zj, pc, al, be, gx, gz, mzz);
+#pragma unroll
+    for (int m = 0; m < K; ++m) {
+        const float2 fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
+        const float2 P = fma2(dy, fy, mul2(dx, fx));
+        const float2 Q = fma2(be, P, mul2(gx, fz));
+        acc[3 * m + 0] = fma2(dx, Q, fma2(al, fx, acc[3 * m + 0]));
+        acc[3 * m + 1] = fma2(dy, Q, fma2(al, fy, acc[3 * m + 1]));
+        acc[3 * m + 2] = fma2(mzz, fz, fma2(gz, P, acc[3 * m + 2]));
+        if constexpr (BOTH) {
+            const float2 hx = hf[3 * m], hy = hf[3 * m + 1], hzf = hf[3 * m + 2];
+            const float2 Pt = fma2(dy, hy, mul2(dx, hx));
+            const float2 Qt = fma2(be, Pt, mul2(gz, hzf));
+            vacc[3 * m + 0] = fma2(dx, Qt, fma2(al, hx, vacc[3 * m + 0]));
+            vacc[3 * m + 1] = fma2(dy, Qt, fma2(al, hy, vacc[3 * m + 1]));
+            vacc[3 * m + 2] = fma2(mzz, hzf, fma2(gx, Pt, vacc[3 * m + 2]));
+        }
+    }
+}
+
+// pair_apply2 summed over the minimum image and its 8 nearest periodic images
+// in x, y (Sec. 4.2); Lx, Ly in units of a
+template <int K, bool BOTH, bool PER>
+__device__ __forceinline__ void pair_apply2_images(float2 dx, float2 dy, float2 dz, float2 hz, float2 zj,
+                                                   const PairConstX2& pc, float Lx, float Ly, const float2* f,
+                                                   const float2* hf, float2* acc, float2* vacc)
+{
+    if constexpr (!PER) {
+        pair_apply2<K, BOTH>(dx, dy, dz, hz, zj, pc, f, hf, acc, vacc);
+    } else {
+        const float iLx = 1.0f / Lx, iLy = 1.0f / Ly;
+        dx = make_float2(dx.x - Lx * rintf(dx.x * iLx), dx.y - Lx * rintf(dx.y * iLx));
+        dy = make_float2(dy.x - Ly * rintf(dy.x * iLy), dy.y - Ly * rintf(dy.y * iLy));
+#pragma unroll
+        for (int ia = -1; ia <= 1; ++ia)
+#pragma unroll
+            for (int ib = -1; ib <= 1; ++ib)
+                pair_apply2<K, BOTH>(add2(dx, bc2((float)ia * Lx)), add2(dy, bc2((float)ib * Ly)), dz, hz, zj, pc,
+                                     f, hf, acc, vacc);
     }
 }
 
 // tuning variants (visitor-loop unroll, min CTAs per SM); chosen per K so no variant spills
-template <int K, int V>
+template <int K, int V, bool PER = false>
 struct Sym2Var {
     static constexpr int UNR = V == 0 ? 2 : (V == 1 ? 1 : (V == 2 ? 2 : 4));
-    static constexpr int MINB = K == 1 ? (V == 1 ? 6 : (V == 2 ? 5 : 4)) : (V == 2 ? 3 : 4);
+    static constexpr int MINB0 = K == 1 ? (V == 1 ? 6 : (V == 2 ? 5 : 4))
+                                        : (K == 2 ? (V == 2 ? 3 : 4) : (V == 1 ? 3 : 2));
+    // the image loop of the periodic cell needs more registers
+    static constexpr int MINB = PER ? (MINB0 > (K == 1 ? 4 : 2) ? (K == 1 ? 4 : 2) : MINB0) : MINB0;
 };
 
-template <int K, int UNR, int MINB>
+template <int K, bool PER, int UNR, int MINB>
 __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict__ rec, int64_t n, int64_t n_pad,
-                                                  const SymItem* __restrict__ items, int n_home_tiles,
-                                                  float* __restrict__ partial, int* __restrict__ err_flag)
+                                                  const SymItem* __restrict__ items, int n_home_tiles, float Lx,
+                                                  float Ly, float* __restrict__ partial, int* __restrict__ err_flag)
 {
     constexpr int LEN = Rec2<K>::LEN;
     constexpr uint32_t TILE_BYTES = VT * LEN * sizeof(float);
@@ -576,25 +630,22 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
         }
     float2 hxh, hyh, hxl, hyl, hz, hf[3 * K];
     {
-        float4 a[Rec2<K>::NCH], b[Rec2<K>::NCH];
+        // value m of home blob i0 in .x, of i1 in .y
+        float2 hv[2 * Rec2<K>::NCH];
 #pragma unroll
         for (int c = 0; c < Rec2<K>::NCH; ++c) {
-            a[c] = *reinterpret_cast<const float4*>(rec + rec2_off(i0, c, LEN));
-            b[c] = *reinterpret_cast<const float4*>(rec + rec2_off(i1, c, LEN));
+            const float4 a = *reinterpret_cast<const float4*>(rec + rec2_off(i0, c, LEN));
+            const float4 b = *reinterpret_cast<const float4*>(rec + rec2_off(i1, c, LEN));
+            hv[2 * c] = make_float2(a.x, b.x);
+            hv[2 * c + 1] = make_float2(a.z, b.z);
         }
-        hxh = make_float2(a[0].x, b[0].x);
-        hyh = make_float2(a[0].z, b[0].z);
-        hxl = make_float2(a[1].x, b[1].x);
-        hyl = make_float2(a[1].z, b[1].z);
-        hz = make_float2(a[2].x, b[2].x);
-        hf[0] = make_float2(a[2].z, b[2].z);
-        hf[1] = make_float2(a[3].x, b[3].x);
-        hf[2] = make_float2(a[3].z, b[3].z);
-        if constexpr (K == 2) {
-            hf[3] = make_float2(a[4].x, b[4].x);
-            hf[4] = make_float2(a[4].z, b[4].z);
-            hf[5] = make_float2(a[5].x, b[5].x);
-        }
+        hxh = hv[0];
+        hyh = hv[1];
+        hxl = hv[2];
+        hyl = hv[3];
+        hz = hv[4];
+#pragma unroll
+        for (int q = 0; q < 3 * K; ++q) hf[q] = hv[5 + q];
     }
     float2 acc[3 * K];
 #pragma unroll
@@ -615,17 +666,7 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
                 const float2 dx = add2(fma2(m1, xh, hxh), fma2(m1, xl, hxl));
                 const float2 dy = add2(fma2(m1, yh, hyh), fma2(m1, yl, hyl));
                 const float2 dz = fma2(m1, zj, hz);
-                float2 al, be, gx, gz, mzz;
-                pair_factors_x2(dx, dy, dz, hz, zj, pc, al, be, gx, gz, mzz);
-#pragma unroll
-                for (int m = 0; m < K; ++m) {
-                    const float2 fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
-                    const float2 P = fma2(dy, fy, mul2(dx, fx));
-                    const float2 Q = fma2(be, P, mul2(gx, fz));
-                    acc[3 * m + 0] = fma2(dx, Q, fma2(al, fx, acc[3 * m + 0]));
-                    acc[3 * m + 1] = fma2(dy, Q, fma2(al, fy, acc[3 * m + 1]));
-                    acc[3 * m + 2] = fma2(mzz, fz, fma2(gz, P, acc[3 * m + 2]));
-                }
+                pair_apply2_images<K, false, PER>(dx, dy, dz, hz, zj, pc, Lx, Ly, f, hf, acc, nullptr);
             }
         } else if (ok) {
             // both directions; lane l takes visitor (step + l) mod 32
@@ -640,24 +681,7 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
                 const float2 dx = add2(fma2(m1, xh, hxh), fma2(m1, xl, hxl));
                 const float2 dy = add2(fma2(m1, yh, hyh), fma2(m1, yl, hyl));
                 const float2 dz = fma2(m1, zj, hz);
-                float2 al, be, gx, gz, mzz;
-                pair_factors_x2(dx, dy, dz, hz, zj, pc, al, be, gx, gz, mzz);
-#pragma unroll
-                for (int m = 0; m < K; ++m) {
-                    const float2 fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
-                    const float2 P = fma2(dy, fy, mul2(dx, fx));
-                    const float2 Q = fma2(be, P, mul2(gx, fz));
-                    acc[3 * m + 0] = fma2(dx, Q, fma2(al, fx, acc[3 * m + 0]));
-                    acc[3 * m + 1] = fma2(dy, Q, fma2(al, fy, acc[3 * m + 1]));
-                    acc[3 * m + 2] = fma2(mzz, fz, fma2(gz, P, acc[3 * m + 2]));
-                    // M^T applied to the home forces
-                    const float2 hx = hf[3 * m], hy = hf[3 * m + 1], hzf = hf[3 * m + 2];
-                    const float2 Pt = fma2(dy, hy, mul2(dx, hx));
-                    const float2 Qt = fma2(be, Pt, mul2(gz, hzf));
-                    vacc[3 * m + 0] = fma2(dx, Qt, fma2(al, hx, vacc[3 * m + 0]));
-                    vacc[3 * m + 1] = fma2(dy, Qt, fma2(al, hy, vacc[3 * m + 1]));
-                    vacc[3 * m + 2] = fma2(mzz, hzf, fma2(gx, Pt, vacc[3 * m + 2]));
-                }
+                pair_apply2_images<K, true, PER>(dx, dy, dz, hz, zj, pc, Lx, Ly, f, hf, acc, vacc);
                 // hand the visitor sums to the lane that takes that visitor next
 #pragma unroll
                 for (int q = 0; q < 3 * K; ++q) {
@@ -709,7 +733,7 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
     }
 }
 
-template <int K, class In, class Out>
+template <int K, bool PER, class In, class Out>
 static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
 {
     constexpr int LEN = Rec2<K>::LEN;
@@ -727,17 +751,19 @@ static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U,
                                                                          h->p.s_min, rec, scale);
     count_launch();
     const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 2 * 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
+    const float Lxa = (float)(h->p.Lx / h->p.a), Lya = (float)(h->p.Ly / h->p.a);  // periodic cell in units of a
     if (h->profile) prof_begin(h, st);
     const int sv = h->sym_variant[sym_class(K)];
     switch (sv >= 0 ? sv : (K == 1 ? 2 : 3)) {  // tuning variants (unroll, min CTAs per SM), see Sym2Var;
                                                  // -1: the measured default per K
-    case 1: sym2_kernel<K, Sym2Var<K, 1>::UNR, Sym2Var<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, partial, h->dev_flag); break;
-    case 2: sym2_kernel<K, Sym2Var<K, 2>::UNR, Sym2Var<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, partial, h->dev_flag); break;
-    case 3: sym2_kernel<K, Sym2Var<K, 3>::UNR, Sym2Var<K, 3>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, partial, h->dev_flag); break;
-    default: sym2_kernel<K, Sym2Var<K, 0>::UNR, Sym2Var<K, 0>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, partial, h->dev_flag); break;
+    case 1: sym2_kernel<K, PER, Sym2Var<K, 1, PER>::UNR, Sym2Var<K, 1, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, Lxa, Lya, partial, h->dev_flag); break;
+    case 2: sym2_kernel<K, PER, Sym2Var<K, 2, PER>::UNR, Sym2Var<K, 2, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, Lxa, Lya, partial, h->dev_flag); break;
+    case 3: sym2_kernel<K, PER, Sym2Var<K, 3, PER>::UNR, Sym2Var<K, 3, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, Lxa, Lya, partial, h->dev_flag); break;
+    default: sym2_kernel<K, PER, Sym2Var<K, 0, PER>::UNR, Sym2Var<K, 0, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, Lxa, Lya, partial, h->dev_flag); break;
     }
     count_launch();
-    if (h->profile) prof_end(h, st, 4 /* symmetric, factored */, K, (double)n * (double)n);
+    if (h->profile) prof_end(h, st, PER ? 3 : 4 /* symmetric (images) or symmetric factored */, K,
+                             (double)n * (double)n);
     // blocks were formed in units of a: M = M(a = 1) / a
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta * h->p.a);
     const int nseg = (n_home + SEG - 1) / SEG;
@@ -758,8 +784,8 @@ static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U,
 template <int K, class In, class Out>
 static int sym_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
 {
-    if constexpr (K <= 2)
-        if (h->use_packed && h->p.wall && !(h->p.Lx > 0.0)) return sym::run2<K>(h, n, r, F, U, k, st);
+    if (h->use_packed && h->p.wall)
+        return h->p.Lx > 0.0 ? sym::run2<K, true>(h, n, r, F, U, k, st) : sym::run2<K, false>(h, n, r, F, U, k, st);
     if (h->p.Lx > 0.0) return sym::run<K, true, true>(h, n, r, F, U, k, st);
     return h->p.wall ? sym::run<K, true, false>(h, n, r, F, U, k, st) : sym::run<K, false, false>(h, n, r, F, U, k, st);
 }

@@ -173,7 +173,7 @@ def test_fma_peak_probe():
     assert 0.0 < f64 < f32
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
 @pytest.mark.parametrize("n", [1, 31, 255, 256, 257, 700, 2049, 4500])
 def test_f32_packed_symmetric_kernel(k, n):
     """The packed symmetric kernel (two homes per thread, 256-blob home tiles,
@@ -194,7 +194,7 @@ def test_f32_packed_symmetric_kernel(k, n):
     assert rel2(Up, Us) <= 1e-5
 
 
-@pytest.mark.parametrize("k", [1, 2])
+@pytest.mark.parametrize("k", [1, 2, 4])
 @pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_f32_packed_variants(variant, k):
     s = synth.c0_boomerangs_1920()

@@ -32,12 +32,15 @@ def test_periodic_f64(nb):
 
 
 @pytest.mark.parametrize("k", [1, 2, 4, 16])
-@pytest.mark.parametrize("sym", [True, False])
-def test_periodic_f32(k, sym):
+@pytest.mark.parametrize("sym,packed", [(True, True), (True, False), (False, False)])
+def test_periodic_f32(k, sym, packed):
+    """FP32 in the periodic cell: packed symmetric kernel (default for k <= 4),
+    one-home symmetric kernel, one-direction kernel"""
     s, r, prm = cell(40, 52)
     F = synth.gaussian(53 + k, (k, 3, s.n), np.float32)
     h = handle(s)
     h.set_symmetric(sym)
+    h.set_packed(packed)
     U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
     assert rel2(U, om.apply(r, F.astype(np.float64), prm)) <= 1e-5
 
