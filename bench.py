@@ -350,12 +350,7 @@ def run_ours(args, rank, world, local):
             "warmup": args.warmup, "ms_per_step": t_max * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded boomerang suspension, forces N(0,1))",
-            "config": {"workload": "boomerangs_65535: 4369 L-bodies x 15 blobs, T-S step + k=16 FP32 batch",
-                       "n_blobs": N, "n_bodies": NB, "k_rhs": K_RHS, "gmres_tol": 1e-6, "gmres_restart": 100,
-                       "lanczos_tol": 1e-4,
-                       "rfd_delta": 1e-3, "gmres_x0": "corrector starts from the predictor's solution",
-                       "l2": "flushed (256 MB write) before every timed step",
-                       "parallelism": f"replicas x{world}"},
+            "config": bench_config(world),
             "steps_per_s": args.steps / t_max * world,
             "matvecs_per_s": rhs_local * world / t_max,
             "e2e": {"value": e2e_pairs / e2e_t, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
@@ -609,6 +604,14 @@ def measure_batched(lib, dev, T, tol=1e-4, max_iter=60):
 # ---------------------------------------------------------------------------
 # reference arm: the CPU oracle, bounded sample of the same workload
 
+def bench_config(world):
+    """the workload both arms report"""
+    return {"workload": "boomerangs_65535: 4369 L-bodies x 15 blobs, T-S step + k=16 FP32 batch",
+            "n_blobs": N, "n_bodies": NB, "k_rhs": K_RHS, "gmres_tol": 1e-6, "gmres_restart": 100,
+            "lanczos_tol": 1e-4, "rfd_delta": 1e-3, "gmres_x0": "corrector starts from the predictor's solution",
+            "l2": "flushed (256 MB write) before every timed step", "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return None
@@ -636,9 +639,10 @@ def run_reference(args, rank, world):
             "warmup": args.warmup, "ms_per_step": t * 1e3 / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "impl": "reference",
-            "config": {"workload": "boomerangs_65535 (oracle: k=16 FP64 matvec rows)", "n_blobs": N},
+            "config": bench_config(world),
             "cpu_baseline": {"value": v, "unit": UNIT, "cores": om.num_threads(), "kind": "oracle",
-                             "sample": f"{nrows} target rows x {N} sources x k=16 per step"},
+                             "sample": f"each step: {nrows} target rows x {N} sources of the same suspension, "
+                                       f"k = 16, FP64 (the oracle's pair interactions per second)"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
 
 

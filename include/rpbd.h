@@ -250,8 +250,9 @@ int rpbd_rfd_drift(rpbd_handle* h, int64_t n, const double* r, const double* W, 
  * at 0.  FP32 pair arithmetic, FP32 F and U, 1 <= k <= 16 (k in {1, 4, 16}
  * hit specialised kernels, other k run as the next larger one).  One
  * persistent launch over a work list of (system, target tile, source chunk)
- * items with the tile shape chosen by rpbd_autotune_batched (default:
- * 128 targets x 64 sources).  The work list is cached per offsets. */
+ * items with the tile shape chosen by rpbd_autotune_batched (default: the
+ * packed 256-target tile with the wall, else 128 targets x 64 sources).  The
+ * work list is cached per offsets. */
 int rpbd_mobility_apply_batched(rpbd_handle* h, int n_sys, const int64_t* offsets, const double* r,
                                 const float* F, float* U, int k, void* stream);
 
@@ -333,13 +334,14 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
 /* -1 (default): per-k default; 0..3: loop-unroll / occupancy variant of the
  * symmetric kernel, for every right-hand-side class. */
 #define RPBD_OPT_SYM_VARIANT 2
-/* value != 0 (default): with the wall and no periodic images, symmetric
- * matvecs with k <= 2 use the packed kernel (two home blobs per thread, both
+/* value != 0 (default): with the wall (open or periodic cell), symmetric
+ * matvecs (k <= 4) use the packed kernel (two home blobs per thread, both
  * pair blocks formed by two-wide FP32 instructions); 0: the one-home kernel. */
 #define RPBD_OPT_PACKED 3
 /* tile variant of the batched kernel (what rpbd_autotune_batched picks):
- * -1 / 0: 128 targets x 64-source tiles, 1: 64 x 64, 2: 256 x 32, 3 (wall
- * only): 256 targets, two per thread in packed two-wide FP32 x 64-source tiles. */
+ * -1: the default (3 with the wall, else 0); 0: 128 targets x 64-source
+ * tiles, 1: 64 x 64, 2: 256 x 32, 3 (wall only): 256 targets, two per thread
+ * in packed two-wide FP32 x 64-source tiles. */
 #define RPBD_OPT_BATCH_VARIANT 4
 int rpbd_set_option(rpbd_handle* h, int option, int value);
 

@@ -71,7 +71,7 @@ class Handle:
         self._check(self.lib.rpbd_set_option(self.h, 4, int(v)), "set_option")
 
     def set_packed(self, on: bool):
-        """k <= 2 symmetric matvecs (wall, open cell): packed two-homes-per-thread kernel (default) or not."""
+        """k <= 4 symmetric matvecs with the wall: packed two-homes-per-thread kernel (default) or not."""
         self._check(self.lib.rpbd_set_option(self.h, 3, int(bool(on))), "set_option")
 
     def set_symmetric(self, on: bool):

@@ -694,7 +694,9 @@ int batched_apply_impl(rpbd_handle* h, int n_sys, const int64_t* off, const doub
     if (off[0] != 0) return set_error(h, RPBD_BAD_ARG, "batched: offsets must start at 0");
     if (off[n_sys] == 0) return RPBD_OK;
     BatchPlan* p = nullptr;
-    RPBD_TRY(get_plan(h, n_sys, off, k, h->batch_variant < 0 ? 0 : h->batch_variant, &p));
+    // default: the packed tile with the wall (fastest on the uneven boomerang batch), else 128 x 64
+    const int variant = h->batch_variant >= 0 ? h->batch_variant : (h->p.wall ? 3 : 0);
+    RPBD_TRY(get_plan(h, n_sys, off, k, variant, &p));
     const bool wall = h->p.wall != 0;
     if (io_double)
         return wall ? run_dispatch<true>(h, p, n_sys, r, (const double*)F, (double*)U, k, active, st)

@@ -83,7 +83,7 @@ struct ProfRec {
 // cached work list of a symmetric kernel (per n)
 struct SymPlan {
     int64_t n = -1;
-    int n_items = 0, n_home = 0, max_slots = 0;
+    int n_items = 0, n_home = 0, max_slots = 0, chunk = 0;
 };
 
 }  // namespace rpbd

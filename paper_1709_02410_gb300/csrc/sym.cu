@@ -37,7 +37,7 @@ namespace sym {
 constexpr int HT = 128;    // home tile (threads per CTA)
 constexpr int VT = 32;     // visitor tile (records per stage)
 constexpr int NST = 4;     // TMA ring depth
-constexpr int CHUNK = 2048;  // visitors per off-diagonal item
+constexpr int CHUNK = 2048;  // visitors per off-diagonal item (at most; see get_items)
 
 template <int K>
 struct Rec {
@@ -360,22 +360,31 @@ __global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_hom
 }
 
 // Work items of the symmetric kernels for home tiles of TILE blobs: per home
-// tile one diagonal item (slot 0) and one item per CHUNK visitors after it.
+// tile one diagonal item (slot 0) and one item per `chunk` visitors after it.
+// The chunk is CHUNK, halved (down to one visitor tile) while the items would
+// not fill 4 CTAs per SM, so small suspensions still spread over the GPU.
 // Cached per n in plan slot `ps` (0: 128-blob tiles, 1: 256-blob tiles).
 template <int TILE>
 static int get_items(rpbd_handle* h, int ps, int64_t n, int64_t n_pad, SymItem** d_items, int* n_items, int* n_home,
-                     int* max_slots)
+                     int* max_slots, int* chunk_out)
 {
     SymPlan& pl = h->sym_plan[ps];
     if (pl.n != n) {
         std::vector<SymItem> items;
         const int T = (int)(n_pad / TILE);
+        int chunk = CHUNK;
+        auto count = [&](int c) {
+            int64_t m = T;
+            for (int H = 0; H < T; ++H) m += (n_pad - (int64_t)(H + 1) * TILE + c - 1) / c;
+            return m;
+        };
+        while (chunk > VT && count(chunk) < 4 * (int64_t)h->sm_count) chunk /= 2;
         int ms = 1;
         for (int H = 0; H < T; ++H) {
             items.push_back(SymItem{H, H * TILE, TILE / VT, 0});
             int c = 1;
-            for (int64_t v0 = (int64_t)(H + 1) * TILE; v0 < n_pad; v0 += CHUNK, ++c) {
-                const int64_t v1 = std::min<int64_t>(n_pad, v0 + CHUNK);
+            for (int64_t v0 = (int64_t)(H + 1) * TILE; v0 < n_pad; v0 += chunk, ++c) {
+                const int64_t v1 = std::min<int64_t>(n_pad, v0 + chunk);
                 items.push_back(SymItem{H, (int)v0, (int)((v1 - v0) / VT), c});
             }
             ms = std::max(ms, c);
@@ -390,11 +399,13 @@ static int get_items(rpbd_handle* h, int ps, int64_t n, int64_t n_pad, SymItem**
         pl.n_items = (int)items.size();
         pl.n_home = T;
         pl.max_slots = ms;
+        pl.chunk = chunk;
     }
     *d_items = reinterpret_cast<SymItem*>(h->buf[ps == 0 ? BUF_SYM_ITEMS : BUF_SYM2_ITEMS]);
     *n_items = pl.n_items;
     *n_home = pl.n_home;
     *max_slots = pl.max_slots;
+    *chunk_out = pl.chunk;
     return RPBD_OK;
 }
 
@@ -405,7 +416,8 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     const int64_t n_pad = (n + HT - 1) / HT * HT;
     SymItem* items;
     int n_items, n_home, max_slots;
-    RPBD_TRY(get_items<HT>(h, 0, n, n_pad, &items, &n_items, &n_home, &max_slots));
+    int chunk;
+    RPBD_TRY(get_items<HT>(h, 0, n, n_pad, &items, &n_items, &n_home, &max_slots, &chunk));
     float* rec;
     double* scale;
     float* partial;
@@ -437,7 +449,7 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     reduce_visitors_kernel<HT, K, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)nseg), 256, 0, st>>>(
         n, n_pad, k, partial, segsum);
     count_launch();
-    reduce_kernel<HT, float, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_home, CHUNK,
+    reduce_kernel<HT, float, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_home, chunk,
                                                                                partial, segsum, scale, inv8pieta, U);
     count_launch();
     RPBD_LAUNCH_CHECK(h);
@@ -740,7 +752,8 @@ static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U,
     const int64_t n_pad = (n + HT2 - 1) / HT2 * HT2;
     SymItem* items;
     int n_items, n_home, max_slots;
-    RPBD_TRY(get_items<HT2>(h, 1, n, n_pad, &items, &n_items, &n_home, &max_slots));
+    int chunk;
+    RPBD_TRY(get_items<HT2>(h, 1, n, n_pad, &items, &n_items, &n_home, &max_slots, &chunk));
     float* rec;
     double* scale;
     float* partial;
@@ -772,7 +785,7 @@ static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U,
     reduce_visitors_kernel<HT2, K, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)nseg), 256, 0, st>>>(
         n, n_pad, k, partial, segsum);
     count_launch();
-    reduce_kernel<HT2, float, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_home, CHUNK,
+    reduce_kernel<HT2, float, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_home, chunk,
                                                                                 partial, segsum, scale, inv8pieta, U);
     count_launch();
     RPBD_LAUNCH_CHECK(h);

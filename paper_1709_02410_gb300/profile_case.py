@@ -1,6 +1,8 @@
 """Time one wall-RPY matvec variant on synthetic boomerangs (CUDA events).
 
     python -m paper_1709_02410_gb300.profile_case --n 65535 --k 16 --dtype f32 --reps 5
+    python -m paper_1709_02410_gb300.profile_case --batched --k 1 --reps 5     # 64 uneven suspensions
+    python -m paper_1709_02410_gb300.profile_case --adjoint --n 65535 --reps 3 # FP32 adjoint
 
 Prints one JSON line: seconds per launch (pack + pair kernel + reduce),
 pairs/s and matvecs/s.  Useful on its own and as the target of profilers.
@@ -20,9 +22,16 @@ def main():
     ap.add_argument("--wall", type=int, default=1)
     ap.add_argument("--sym", type=int, default=1, help="FP32 k <= 4: symmetric kernel (1) or one-direction (0)")
     ap.add_argument("--variant", type=int, default=-1, help="symmetric kernel variant 0..3 (-1: default)")
+    ap.add_argument("--batched", action="store_true",
+                    help="the uneven batch of 64 boomerang suspensions (one batched launch; --variant: tile variant)")
+    ap.add_argument("--adjoint", action="store_true", help="the FP32 adjoint instead of the matvec")
     a = ap.parse_args()
     import torch
     from . import F32, F64, Handle, synth
+    if a.batched:
+        return batched(a)
+    if a.adjoint:
+        return adjoint(a)
     nb = max(1, a.n // 15)
     s = synth.boomerang_suspension(nb, 40.0 * np.sqrt(nb / 128), 1)
     dev = "cuda:0"
@@ -46,6 +55,57 @@ def main():
     print(json.dumps({"n": s.n, "k": a.k, "dtype": a.dtype, "sym": a.sym, "variant": a.variant,
                       "s_per_launch": t, "pairs_per_s": s.n * s.n / t,
                       "matvecs_per_s": a.k / t}))
+
+
+def batched(a):
+    import torch
+    from . import Handle, synth
+    systems = synth.c4_uneven_batch()
+    h = Handle(synth.ETA, systems[0].a, synth.KT)
+    if a.variant >= 0:
+        h.set_batch_variant(a.variant)
+    dev = "cuda:0"
+    T = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
+    shape = T(systems[0].shape)
+    q = T(np.concatenate([s.q for s in systems]))
+    th = T(np.concatenate([s.theta for s in systems]))
+    r = h.blobs_from_bodies(shape, q, th)
+    off = np.concatenate([[0], np.cumsum([s.n for s in systems])]).astype(np.int64)
+    F = T(synth.gaussian(7, (a.k, 3, int(off[-1]))), torch.float32)
+    U = h.mobility_apply_batched(off, r, F)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        U = h.mobility_apply_batched(off, r, F)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / a.reps
+    pairs = float(sum(float(s.n) ** 2 for s in systems))
+    print(json.dumps({"batched": len(systems), "blobs": int(off[-1]), "k": a.k, "variant": a.variant,
+                      "s_per_launch": t, "pairs_per_s": pairs / t}))
+
+
+def adjoint(a):
+    import torch
+    from . import F32, Handle, synth
+    nb = max(1, a.n // 15)
+    s = synth.boomerang_suspension(nb, 40.0 * np.sqrt(nb / 128), 1)
+    h = Handle(synth.ETA, s.a, synth.KT)
+    dev = "cuda:0"
+    T = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
+    r = h.blobs_from_bodies(T(s.shape), T(s.q), T(s.theta))
+    u, F = T(synth.gaussian(8, (3, s.n))), T(synth.gaussian(9, (3, s.n)))
+    g = h.mobility_adjoint(r, u, F, dtype=F32)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(a.reps):
+        g = h.mobility_adjoint(r, u, F, dtype=F32)
+    e1.record()
+    torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) / 1e3 / a.reps
+    print(json.dumps({"adjoint_f32": True, "n": s.n, "s_per_launch": t, "pairs_per_s": s.n * s.n / t}))
 
 
 if __name__ == "__main__":
