@@ -262,7 +262,6 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
                 for (int q = 0; q < 3 * K; ++q) vacc[q] = __shfl_sync(0xffffffffu, vacc[q], (lane + 1) & 31);
             }
             // lane l now holds visitor l's sum over this warp's homes
-#pragma unroll
             float* rb = red + (t & 1) * (4 * VT * 3 * K);  // double-buffered: one barrier per tile
 #pragma unroll
             for (int q = 0; q < 3 * K; ++q) rb[(warp * VT + lane) * 3 * K + q] = vacc[q];

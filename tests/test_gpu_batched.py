@@ -39,15 +39,22 @@ def test_batched_matvec_matches_oracle_per_system(k, variant):
 
 
 def test_autotune_and_variants_agree():
+    """the default tile and the autotuned one both match the oracle; they
+    differ only by FP32 rounding (the packed tile works in units of a)"""
     systems, rs, off, r = batch([30, 7, 64, 100, 12], seed=1)
     h = handle_for(systems[0])
     rd = to_dev(r)
-    F = to_dev(synth.gaussian(9, (1, 3, r.shape[1]), np.float32), torch.float32)
+    Fh = synth.gaussian(9, (1, 3, r.shape[1]), np.float32)
+    F = to_dev(Fh, torch.float32)
     U0 = h.mobility_apply_batched(off, rd, F).cpu().numpy()
     v, ms = h.autotune_batched(off, rd, 1)
     assert 0 <= v < 4 and ms > 0
     U1 = h.mobility_apply_batched(off, rd, F).cpu().numpy()
-    assert rel2(U1, U0) <= 1e-6
+    assert rel2(U1, U0) <= 5e-6
+    for s, (sy, rr) in enumerate(zip(systems, rs)):
+        sl = slice(off[s], off[s + 1])
+        ref = om.apply(rr, Fh[:, :, sl].astype(np.float64), oracle_params(sy))
+        assert rel2(U0[:, :, sl], ref) <= 1e-5 and rel2(U1[:, :, sl], ref) <= 1e-5
 
 
 @pytest.mark.parametrize("use_graph", [False, True])
