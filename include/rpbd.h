@@ -369,9 +369,11 @@ int rpbd_measure_fma_peak(rpbd_handle* h, int dtype, double* tflops, void* strea
 int rpbd_profile_enable(rpbd_handle* h, int on);
 /* Sum of the recorded pair-kernel durations for (kind, k-variant), their
  * launch count and pairs (n^2 per launch); kind: RPBD_F64, RPBD_F32 (one-direction
- * kernel), 2 (batched FP32), 3 (symmetric FP32), 4 (symmetric FP32 applying the
- * block in factored form: k <= 2, open cell).  Synchronises the device.  reset
- * != 0 drops every record afterwards. */
+ * kernel), 2 (batched FP32), 3 (symmetric FP32 with the assembled block, or
+ * the packed kernel in a periodic cell), 4 (symmetric FP32 applying the block
+ * in factored form: the packed kernel in an open cell, or the one-home kernel
+ * with k <= 2).  Synchronises the device.  reset != 0 drops every record
+ * afterwards. */
 int rpbd_profile_read(rpbd_handle* h, int dtype, int k, double* ms, long long* launches, double* pairs,
                       int reset);
 

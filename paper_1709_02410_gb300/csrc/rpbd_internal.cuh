@@ -122,7 +122,7 @@ struct rpbd_handle {
     int use_sym[3] = {1, 1, 1};
     int sym_variant[3] = {-1, -1, -1};
     rpbd::SymPlan sym_plan[2];  // work lists of the symmetric kernels: 128- and 256-blob home tiles
-    int use_packed = 1;         // k <= 2, open cell: the packed two-homes-per-thread symmetric kernel
+    int use_packed = 1;         // k <= 4 with the wall: the packed two-homes-per-thread symmetric kernel
 };
 
 namespace rpbd {
