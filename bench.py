@@ -39,6 +39,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # kernels (profiles/pair_kernel_f32_k*_boomerangs_65535.md); None when not captured
 NCU_TRAFFIC = {"f32_k16": 22067968 + 343998464, "f32symf_k1": 4379392 + 55015936,
                "f32symf_k2": 8208640 + 168576256}
+# FMA-pipe activity (sm__pipe_fma_cycles_active) from the same captures
+NCU_FMA_PIPE = {"f32_k16": 0.781, "f32symf_k1": 0.778, "f32symf_k2": 0.749}
 
 
 F_ASSEMBLY = 12             # flops of forming the 9 entries from the block's 5 scalars
@@ -306,6 +308,7 @@ def run_ours(args, rank, world, local):
                         d["pairs"] / d["launches"] * f_pair(k) / avg / 1e12,
                     "share_of_step": d["ms"] / (t_local * 1e3),
                     "measured_fma_peak": fma32, "frac_of_measured_fma_peak": ach / fma32,
+                    "ncu_fma_pipe_active": NCU_FMA_PIPE.get(name),
                     "peak_note": "peak = 152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (derived); "
                                  "measured_fma_peak = the library's FMA-chain probe on this GPU"}
         # accuracy vs the FP64 oracle on sampled rows (outside the timed region)
