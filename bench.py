@@ -287,6 +287,7 @@ def run_ours(args, rank, world, local):
     batched = measure_batched(h.lib, dev, T) if (rank == 0 and extras) else None
     rollers = measure_rollers(dev, T) if (rank == 0 and extras and not args.no_rollers) else None
     next_rows = measure_next_rows(dev, T, s, shape, q0, th0, forces, Lp) if (rank == 0 and extras) else None
+    c2_div = measure_c2_divergence(T) if (rank == 0 and extras) else None
 
     out = None
     if rank == 0:
@@ -372,6 +373,7 @@ def run_ours(args, rank, world, local):
             "batched_c4": batched,
             "ts_step_rollers_c3": rollers,
             "next_rows": next_rows,
+            "c2_rfd_vs_divergence": c2_div,
             "accuracy": acc,
             "wall_s_timed": wall,
         }
@@ -505,6 +507,48 @@ def measure_next_rows(dev, T, s, shape, q0, th0, forces, Lp):
     out["f1_ts_step_256_boomerangs_periodic_s"] = e0.elapsed_time(e1) / 1e3
     out["f1_ts_step_256_boomerangs_iterations"] = [x["iterations"] for x in st]
     return out
+
+
+# ---------------------------------------------------------------------------
+# config 2: the exact divergence of M (FP64 dual-number kernel) against the
+# mean of the blob RFD drift over 10^4 random W (Sec. 3), 16,380 blobs
+
+def measure_c2_divergence(T, samples=10000, chunk=250):
+    import torch
+    import paper_1709_02410_gb300 as P
+    from paper_1709_02410_gb300 import synth
+    s = synth.c2_blobs_16384()
+    h = P.Handle(synth.ETA, s.a, synth.KT)
+    r = h.blobs_from_bodies(T(s.shape), T(s.q), T(s.theta))
+    n = r.shape[1]
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    div = h.mobility_divergence(r)
+    e1.record()
+    torch.cuda.synchronize()
+    t_div = e0.elapsed_time(e1) / 1e3
+    gen = torch.Generator(device=r.device).manual_seed(2024)
+    acc = torch.zeros((3, n), dtype=torch.float64, device=r.device)
+    acc2 = torch.zeros_like(acc)
+    d = torch.empty((3, n), dtype=torch.float64, device=r.device)
+    e0.record()
+    for c0 in range(0, samples, chunk):
+        Ws = torch.randn((chunk, 3, n), dtype=torch.float64, device=r.device, generator=gen)
+        for i in range(chunk):
+            h.rfd_drift(r, Ws[i], 1e-3, dtype=P.F32, out=d)
+            acc += d
+            acc2 += d * d
+    e1.record()
+    torch.cuda.synchronize()
+    t_rfd = e0.elapsed_time(e1) / 1e3
+    mean = acc / samples
+    se = torch.sqrt(torch.clamp(acc2 / samples - mean * mean, min=0.0) / samples)
+    z = (mean - div).abs() / (se + 1e-300)
+    return {"n_blobs": n, "samples": samples, "rfd_delta": 1e-3, "rfd_dtype": "f32 pairs",
+            "frac_within_3se": float((z < 3).double().mean()), "max_z": float(z.max()),
+            "rel_err_mean_vs_div": float(torch.linalg.norm(mean - div) / torch.linalg.norm(div)),
+            "rel_se": float(torch.linalg.norm(se) / torch.linalg.norm(div)),
+            "divergence_s": t_div, "rfd_s_per_sample": t_rfd / samples}
 
 
 # ---------------------------------------------------------------------------
