@@ -436,6 +436,13 @@ def measure_rows(h, r, shape, q, th, T, time_launch):
         st["l"] = h.lanczos_sqrt_apply(r, W, 1e-4, 80, dtype=P.F32)[1]
     out["a4_lanczos_tol1e-4_s"] = time_launch(lz, 2)
     out["a4_lanczos_iterations"] = st["l"]["iterations"]
+    # four Brownian increments in lockstep (shared k = 4 matvecs) vs four separate runs
+    W4 = [T(synth.gaussian(410 + i, (3, n))) for i in range(4)]
+
+    def lz4():
+        st["l4"] = h.lanczos_sqrt_apply_multi(r, W4, tol=1e-4, max_iter=80, dtype=P.F32)
+    out["a4_lanczos_x4_lockstep_s"] = time_launch(lz4, 2)
+    out["a4_lanczos_x4_iterations"] = [x[1]["iterations"] for x in st["l4"]]
 
     def gm():
         st["g"] = h.gmres_rigid_solve(NPER, r, q, W, FT, tol=1e-6, max_iter=300, restart=100, dtype=P.F32,

@@ -206,6 +206,19 @@ int rpbd_lanczos_sqrt_apply(rpbd_handle* h, int64_t n, const double* r, const do
                             double* out, double tol, int max_iter, int dtype, int use_precond,
                             rpbd_stats* stats, void* stream);
 
+/* nsys (1..4) Lanczos square roots M^{1/2} W_s at the same r (same M and
+ * preconditioner), each as in rpbd_lanczos_sqrt_apply.  The processes are
+ * advanced in lockstep, so each iteration's matvecs go out as one multi-RHS
+ * launch and their scalars come back with one synchronisation; every process
+ * keeps its own basis, tridiagonal matrix and stopping test (the answers are
+ * those of nsys separate calls; this is not a block-Krylov method).  W and out
+ * are HOST arrays of nsys DEVICE pointers ([3][n] each); stats (host, may be
+ * NULL) receives nsys records.  Returns RPBD_NOT_CONVERGED when any process
+ * stopped at max_iter. */
+int rpbd_lanczos_sqrt_apply_multi(rpbd_handle* h, int64_t n, const double* r, int nsys,
+                                  const double* const* W, double* const* out, double tol, int max_iter,
+                                  int dtype, int use_precond, rpbd_stats* stats, void* stream);
+
 /* ---- a5: GMRES saddle-point mobility solve (eq. saddle, Sec. 2.1) ------ */
 
 /* Solve [M -K; -K^T 0][lambda; U] = [-slip; -FT] by right-preconditioned

@@ -55,6 +55,7 @@ SIGNATURES = [
     ("rpbd_precond_build", _I, [_P, _I64, _I, _P, _P, _P]),
     ("rpbd_precond_apply", _I, [_P, _I, _P, _P, _P]),
     ("rpbd_lanczos_sqrt_apply", _I, [_P, _I64, _P, _P, _P, _D, _I, _I, _I, C.POINTER(Stats), _P]),
+    ("rpbd_lanczos_sqrt_apply_multi", _I, [_P, _I64, _P, _I, _P, _P, _D, _I, _I, _I, C.POINTER(Stats), _P]),
     ("rpbd_gmres_rigid_solve_multi", _I, [_P, _I64, _I, _P, _P, _I, _P, _P, _P, _P, _D, _I, _I, _I, _I,
                                           C.POINTER(Stats), _P]),
     ("rpbd_gmres_rigid_solve", _I, [_P, _I64, _I, _P, _P, _P, _P, _P, _P, _D, _I, _I, _I, _I, _I,

@@ -196,6 +196,21 @@ class Handle:
             self._check(s, "gmres_rigid_solve")
         return lam, U, st.as_dict()
 
+    def lanczos_sqrt_apply_multi(self, r, Ws, tol=1e-4, max_iter=60, dtype=F64, use_precond=True):
+        """1..4 Lanczos square roots M^{1/2} W at the same positions, in lockstep
+        (shared multi-RHS matvecs).  Returns a list of (out, stats)."""
+        n = r.shape[1]
+        ns = len(Ws)
+        outs = [torch.empty((3, n), dtype=torch.float64, device=r.device) for _ in range(ns)]
+        arr = C.c_void_p * ns
+        st = (Stats * ns)()
+        s = self.lib.rpbd_lanczos_sqrt_apply_multi(self.h, n, _ptr(r), ns, arr(*[_ptr(w) for w in Ws]),
+                                                   arr(*[_ptr(o) for o in outs]), tol, max_iter, dtype,
+                                                   int(bool(use_precond)), st, _stream())
+        if s not in (0, -4):
+            self._check(s, "lanczos_sqrt_apply_multi")
+        return [(o, st[i].as_dict()) for i, o in enumerate(outs)]
+
     def gmres_rigid_solve_multi(self, nper, r, q, problems, tol=1e-6, max_iter=200, restart=50, dtype=F64,
                                 build_precond=True):
         """problems: list of 1..4 (slip, FT) pairs (either None) at the same

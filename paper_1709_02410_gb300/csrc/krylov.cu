@@ -280,28 +280,38 @@ struct Small {
 // ---------------------------------------------------------------------------
 // Lanczos
 
-int lanczos_impl(rpbd_handle* h, int64_t n, const double* r, const double* W, double* out, double tol, int max_iter,
-                 int dtype, int use_precond, rpbd_stats* stats, cudaStream_t st)
+// Several Lanczos processes (different W, same M and preconditioner) advance
+// in lockstep: each iteration gathers the active processes' vectors into one
+// multi-RHS matvec and reads every process's scalars with one
+// synchronisation.  Each process keeps its own basis, tridiagonal matrix and
+// stopping test, so the answers are those of separate runs.
+struct LanczosProc {
+    const double* W;
+    double* out;
+    double *V, *z, *y, *w, *alpha, *beta, *cvec, *cprev, *sc;  // sc: [0] |W|^2, [1] |w|^2, [2] change
+    Small S{nullptr, 0};
+    double W2 = 0.0, change = INFINITY;
+    int m = 0, matvecs = 0, status = RPBD_NOT_CONVERGED;
+    bool active = false;
+};
+
+int lanczos_multi_impl(rpbd_handle* h, int64_t n, const double* r, int nsys, const double* const* W,
+                       double* const* out, double tol, int max_iter, int dtype, int use_precond, rpbd_stats* stats,
+                       cudaStream_t st)
 {
     if (n <= 0) return set_error(h, RPBD_BAD_ARG, "lanczos: n <= 0");
+    if (nsys < 1 || nsys > 4) return set_error(h, RPBD_BAD_ARG, "lanczos: 1..4 vectors");
     if (max_iter < 1 || max_iter > LANCZOS_MAX) return set_error(h, RPBD_BAD_ARG, "lanczos: max_iter must be in 1..80");
     if (use_precond && (!h->prec_valid || h->prec_nb * h->prec_nper != n))
         return set_error(h, RPBD_BAD_ARG, "lanczos: preconditioner not built for these blobs");
     const int64_t len = 3 * n;
-    double *V, *vec, *sm;
-    RPBD_TRY(ensure_t(h, BUF_KRYLOV, (size_t)(max_iter + 1) * len, &V));
-    RPBD_TRY(ensure_t(h, BUF_VEC, (size_t)3 * len, &vec));
     const int mdim = LANCZOS_MAX + 1;
-    RPBD_TRY(ensure_t(h, BUF_SMALL, Small::count(mdim) + 4 * (size_t)mdim, &sm));
-    Small S{sm, mdim};
-    double* alpha = S.partial() + (size_t)DOT_BLOCKS * (mdim + 2);
-    double* beta = alpha + mdim;
-    double* cvec = beta + mdim;
-    double* cprev = cvec + mdim;
-    double* z = vec;
-    double* y = vec + len;
-    double* w = vec + 2 * len;
-    double* sc = S.scal();  // [0] |W|^2, [1] |w|^2, [2] change
+    const size_t small_count = Small::count(mdim) + 4 * (size_t)mdim;
+    double *Vall, *vall, *small, *mv = nullptr;
+    RPBD_TRY(ensure_t(h, BUF_KRYLOV, (size_t)nsys * (max_iter + 1) * len, &Vall));
+    RPBD_TRY(ensure_t(h, BUF_VEC, (size_t)nsys * 3 * len, &vall));
+    RPBD_TRY(ensure_t(h, BUF_SMALL, (size_t)nsys * small_count, &small));
+    if (nsys > 1) RPBD_TRY(ensure_t(h, BUF_GMRES_MV, (size_t)2 * nsys * len, &mv));
     static bool attr = false;
     if (!attr) {
         RPBD_CU(h, cudaFuncSetAttribute(lanczos_sqrt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -309,65 +319,122 @@ int lanczos_impl(rpbd_handle* h, int64_t n, const double* r, const double* W, do
         attr = true;
     }
     RPBD_CU(h, cudaMemsetAsync(h->dev_flag, 0, sizeof(int), st));
-    RPBD_CU(h, cudaMemsetAsync(cprev, 0, sizeof(double) * mdim, st));
     const unsigned g = vgrid(len);
-    RPBD_TRY(multidot(h, len, W, 0, 1, W, &sc[0], 0, S.partial(), st));
-    normalize_kernel<<<g, 256, 0, st>>>(len, W, &sc[0], V); count_launch();
-    RPBD_LAUNCH_CHECK(h);
-    double W2;
-    RPBD_TRY(read_scalar(h, &sc[0], &W2, st));
-    if (!(W2 > 0.0)) {
-        RPBD_CU(h, cudaMemsetAsync(out, 0, sizeof(double) * len, st));
-        if (stats) *stats = rpbd_stats{0, 0, 0.0, RPBD_OK};
-        return RPBD_OK;
+    LanczosProc P[4];
+    for (int s = 0; s < nsys; ++s) {
+        LanczosProc& p = P[s];
+        if (!W[s] || !out[s]) return set_error(h, RPBD_BAD_ARG, "lanczos: null pointer");
+        p.W = W[s];
+        p.out = out[s];
+        p.V = Vall + (int64_t)s * (max_iter + 1) * len;
+        p.z = vall + (int64_t)s * 3 * len;
+        p.y = p.z + len;
+        p.w = p.z + 2 * len;
+        p.S = Small{small + (int64_t)s * small_count, mdim};
+        p.alpha = p.S.partial() + (size_t)DOT_BLOCKS * (mdim + 2);
+        p.beta = p.alpha + mdim;
+        p.cvec = p.beta + mdim;
+        p.cprev = p.cvec + mdim;
+        p.sc = p.S.scal();
+        RPBD_CU(h, cudaMemsetAsync(p.cprev, 0, sizeof(double) * mdim, st));
+        RPBD_TRY(multidot(h, len, p.W, 0, 1, p.W, &p.sc[0], 0, p.S.partial(), st));
+        normalize_kernel<<<g, 256, 0, st>>>(len, p.W, &p.sc[0], p.V); count_launch();
+        RPBD_CU(h, cudaMemcpyAsync(h->host_small + s, &p.sc[0], sizeof(double), cudaMemcpyDeviceToHost, st));
     }
-    int m = 0, matvecs = 0, status = RPBD_NOT_CONVERGED;
-    double change = INFINITY;
-    for (;; ++m) {
-        const double* vm = V + (int64_t)m * len;
-        // w = G v_m
-        if (use_precond) {
-            RPBD_TRY(precond_apply_impl(h, 2, vm, z, st));
-            RPBD_TRY(mobility_apply_impl(h, n, r, z, y, 1, dtype, true, st));
-            RPBD_TRY(precond_apply_impl(h, 1, y, w, st));
+    RPBD_LAUNCH_CHECK(h);
+    RPBD_CU(h, cudaStreamSynchronize(st));
+    for (int s = 0; s < nsys; ++s) {
+        P[s].W2 = h->host_small[s];
+        if (P[s].W2 > 0.0) {
+            P[s].active = true;
         } else {
-            RPBD_TRY(mobility_apply_impl(h, n, r, vm, w, 1, dtype, true, st));
+            RPBD_CU(h, cudaMemsetAsync(P[s].out, 0, sizeof(double) * len, st));
+            P[s].status = RPBD_OK;
         }
-        ++matvecs;
-        // full reorthogonalisation, classical Gram-Schmidt twice
-        RPBD_TRY(multidot(h, len, V, len, m + 1, w, S.hcol(), 0, S.partial(), st));
-        multiaxpy_kernel<<<g, 256, 0, st>>>(len, V, len, m + 1, S.hcol(), w); count_launch();
-        RPBD_TRY(multidot(h, len, V, len, m + 1, w, S.y(), 0, S.partial(), st));
-        multiaxpy_kernel<<<g, 256, 0, st>>>(len, V, len, m + 1, S.y(), w); count_launch();
-        add_kernel<<<1, 128, 0, st>>>(m + 1, S.y(), S.hcol()); count_launch();
-        RPBD_TRY(multidot(h, len, w, 0, 1, w, &sc[1], 0, S.partial(), st));
-        lanczos_coef_kernel<<<1, 1, 0, st>>>(m, S.hcol(), &sc[1], alpha, beta); count_launch();
-        const int m1 = m + 1;
-        lanczos_sqrt_kernel<<<1, 32, tridiag_sqrt_smem_doubles(m1) * sizeof(double), st>>>(m1, alpha, beta, cvec, cprev,
-                                                                                           &sc[2]);
-        count_launch();
-        normalize_kernel<<<g, 256, 0, st>>>(len, w, &sc[1], V + (int64_t)(m + 1) * len); count_launch();
+    }
+    for (;;) {
+        int act[4], k = 0;
+        for (int s = 0; s < nsys; ++s)
+            if (P[s].active) act[k++] = s;
+        if (k == 0) break;
+        // w = G v_m for every active process, one k-RHS matvec
+        for (int a = 0; a < k; ++a) {
+            LanczosProc& p = P[act[a]];
+            const double* vm = p.V + (int64_t)p.m * len;
+            double* dst = k == 1 ? p.z : mv + (int64_t)a * len;
+            if (use_precond) RPBD_TRY(precond_apply_impl(h, 2, vm, dst, st));
+            else RPBD_CU(h, cudaMemcpyAsync(dst, vm, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+        }
+        if (k == 1) {
+            LanczosProc& p = P[act[0]];
+            RPBD_TRY(mobility_apply_impl(h, n, r, p.z, p.y, 1, dtype, true, st));
+        } else {
+            RPBD_TRY(mobility_apply_impl(h, n, r, mv, mv + (int64_t)k * len, k, dtype, true, st));
+        }
+        for (int a = 0; a < k; ++a) {
+            LanczosProc& p = P[act[a]];
+            const double* my = k == 1 ? p.y : mv + (int64_t)(k + a) * len;
+            if (use_precond) RPBD_TRY(precond_apply_impl(h, 1, my, p.w, st));
+            else RPBD_CU(h, cudaMemcpyAsync(p.w, my, sizeof(double) * len, cudaMemcpyDeviceToDevice, st));
+            ++p.matvecs;
+            // full reorthogonalisation, classical Gram-Schmidt twice
+            const int m = p.m;
+            RPBD_TRY(multidot(h, len, p.V, len, m + 1, p.w, p.S.hcol(), 0, p.S.partial(), st));
+            multiaxpy_kernel<<<g, 256, 0, st>>>(len, p.V, len, m + 1, p.S.hcol(), p.w); count_launch();
+            RPBD_TRY(multidot(h, len, p.V, len, m + 1, p.w, p.S.y(), 0, p.S.partial(), st));
+            multiaxpy_kernel<<<g, 256, 0, st>>>(len, p.V, len, m + 1, p.S.y(), p.w); count_launch();
+            add_kernel<<<1, 128, 0, st>>>(m + 1, p.S.y(), p.S.hcol()); count_launch();
+            RPBD_TRY(multidot(h, len, p.w, 0, 1, p.w, &p.sc[1], 0, p.S.partial(), st));
+            lanczos_coef_kernel<<<1, 1, 0, st>>>(m, p.S.hcol(), &p.sc[1], p.alpha, p.beta); count_launch();
+            const int m1 = m + 1;
+            lanczos_sqrt_kernel<<<1, 32, tridiag_sqrt_smem_doubles(m1) * sizeof(double), st>>>(
+                m1, p.alpha, p.beta, p.cvec, p.cprev, &p.sc[2]);
+            count_launch();
+            normalize_kernel<<<g, 256, 0, st>>>(len, p.w, &p.sc[1], p.V + (int64_t)(m + 1) * len); count_launch();
+            RPBD_CU(h, cudaMemcpyAsync(h->host_small + 2 * a, &p.sc[1], 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
         RPBD_LAUNCH_CHECK(h);
-        double cur[3];
-        RPBD_CU(h, cudaMemcpyAsync(h->host_small, sc, 3 * sizeof(double), cudaMemcpyDeviceToHost, st));
         RPBD_CU(h, cudaStreamSynchronize(st));
-        cur[1] = h->host_small[1];
-        cur[2] = h->host_small[2];
-        if (m >= 1) {
-            change = cur[2];
-            if (change < tol) { status = RPBD_OK; break; }
+        for (int a = 0; a < k; ++a) {
+            LanczosProc& p = P[act[a]];
+            const double w2 = h->host_small[2 * a], ch = h->host_small[2 * a + 1];
+            bool stop = false;
+            if (p.m >= 1) {
+                p.change = ch;
+                if (ch < tol) { p.status = RPBD_OK; stop = true; }
+            }
+            if (!stop && !(w2 > 1e-300 * p.W2)) { p.status = RPBD_OK; stop = true; }  // invariant subspace: exact
+            if (!stop && p.m + 1 >= max_iter) stop = true;
+            if (stop) {
+                p.active = false;
+                // y = |W| V c, out = L y
+                const int nv = p.m + 1;
+                lincomb_kernel<<<g, 256, 0, st>>>(len, p.V, len, nv, p.cvec, std::sqrt(p.W2), nullptr,
+                                                  use_precond ? p.y : p.out);
+                count_launch();
+                if (use_precond) RPBD_TRY(precond_apply_impl(h, 0, p.y, p.out, st));
+            } else {
+                ++p.m;
+            }
         }
-        if (!(cur[1] > 1e-300 * W2) ) { status = RPBD_OK; break; }  // invariant subspace: exact
-        if (m + 1 >= max_iter) break;
+        RPBD_LAUNCH_CHECK(h);
     }
     RPBD_TRY(check_flag(h, st));
-    const int nv = m + 1;
-    // y = |W| V c
-    lincomb_kernel<<<g, 256, 0, st>>>(len, V, len, nv, cvec, std::sqrt(W2), nullptr, use_precond ? y : out); count_launch();
-    if (use_precond) RPBD_TRY(precond_apply_impl(h, 0, y, out, st));
-    RPBD_LAUNCH_CHECK(h);
-    if (stats) *stats = rpbd_stats{nv, matvecs, m >= 1 ? change : 0.0, status};
-    return status == RPBD_OK ? RPBD_OK : RPBD_NOT_CONVERGED;
+    bool all_ok = true;
+    for (int s = 0; s < nsys; ++s) {
+        const LanczosProc& p = P[s];
+        if (stats)
+            stats[s] = p.W2 > 0.0 ? rpbd_stats{p.m + 1, p.matvecs, p.m >= 1 ? p.change : 0.0, p.status}
+                                  : rpbd_stats{0, 0, 0.0, RPBD_OK};
+        all_ok = all_ok && p.status == RPBD_OK;
+    }
+    return all_ok ? RPBD_OK : RPBD_NOT_CONVERGED;
+}
+
+int lanczos_impl(rpbd_handle* h, int64_t n, const double* r, const double* W, double* out, double tol, int max_iter,
+                 int dtype, int use_precond, rpbd_stats* stats, cudaStream_t st)
+{
+    return lanczos_multi_impl(h, n, r, 1, &W, &out, tol, max_iter, dtype, use_precond, stats, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -609,6 +676,18 @@ int rpbd_lanczos_sqrt_apply(rpbd_handle* h, int64_t n, const double* r, const do
     if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "lanczos: bad dtype");
     return lanczos_impl(h, n, r, W, out, tol, max_iter, dtype, use_precond, stats,
                         reinterpret_cast<cudaStream_t>(stream));
+}
+
+int rpbd_lanczos_sqrt_apply_multi(rpbd_handle* h, int64_t n, const double* r, int nsys, const double* const* W,
+                                  double* const* out, double tol, int max_iter, int dtype, int use_precond,
+                                  rpbd_stats* stats, void* stream)
+{
+    if (!h) return RPBD_BAD_ARG;
+    if (!r || !W || !out) return set_error(h, RPBD_BAD_ARG, "lanczos_multi: null pointer");
+    if (!(tol > 0)) return set_error(h, RPBD_BAD_ARG, "lanczos_multi: tol must be > 0");
+    if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "lanczos_multi: bad dtype");
+    return lanczos_multi_impl(h, n, r, nsys, W, out, tol, max_iter, dtype, use_precond, stats,
+                              reinterpret_cast<cudaStream_t>(stream));
 }
 
 int rpbd_gmres_rigid_solve_multi(rpbd_handle* h, int64_t nb, int nper, const double* r, const double* q, int nsys,

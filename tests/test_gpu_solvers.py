@@ -66,6 +66,30 @@ def test_lanczos_matches_oracle_iterates():
     assert rel2(out.cpu().numpy(), ref) <= 1e-4
 
 
+@pytest.mark.parametrize("dtype,tol,bound", [(F64, 1e-10, 1e-9), (F32, 1e-5, 1e-4)])
+@pytest.mark.parametrize("nw", [2, 3, 4])
+def test_lanczos_multi_matches_single(dtype, tol, bound, nw):
+    """Lockstep Lanczos (shared multi-RHS matvecs): each W gets the answer
+    and iteration count of its own run; one W = 0 gives zero."""
+    s = small(8, 41)
+    r = positions(s)
+    h = handle_for(s)
+    rd = to_dev(r)
+    h.precond_build(s.nper, rd, to_dev(s.q))
+    rng = np.random.default_rng(42)
+    Ws = [rng.standard_normal((3, s.n)) for _ in range(nw)]
+    Ws[-1] = np.zeros((3, s.n)) if nw == 3 else Ws[-1]
+    out = h.lanczos_sqrt_apply_multi(rd, [to_dev(w) for w in Ws], tol=tol, max_iter=60, dtype=dtype)
+    for w, (y, st) in zip(Ws, out):
+        y1, st1 = h.lanczos_sqrt_apply(rd, to_dev(w), tol=tol, max_iter=60, dtype=dtype)
+        if not np.any(w):
+            assert float(y.abs().max()) == 0.0 and st["iterations"] == 0
+            continue
+        assert st["status"] == 0
+        assert abs(st["iterations"] - st1["iterations"]) <= (0 if dtype == F64 else 1)
+        assert rel2(y.cpu().numpy(), y1.cpu().numpy()) <= bound
+
+
 def test_lanczos_unpreconditioned():
     s = small(4, 9)
     r = positions(s)
