@@ -462,7 +462,13 @@ int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* 
     if (k < 1 || k > 16) return set_error(h, RPBD_BAD_ARG, "k must be in 1..16");
     if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "bad dtype");
     if (!r || !F || !U) return set_error(h, RPBD_BAD_ARG, "null pointer");
-    if (dtype == RPBD_F32 && k <= 4 && h->use_sym[sym_class(k)]) return sym_apply_impl(h, n, r, F, U, k, io_double, st);
+    // the symmetric kernels keep one visitor partial per (home tile, blob): about
+    // n^2 / 256 * 3k floats; beyond 16 GiB (n of order a million) the
+    // one-direction kernel, whose partials grow as n^2 / 2048, takes over
+    const double np_ = (double)(n + 255);
+    const double sym_bytes = (np_ / 256.0 + np_ / 2048.0 + 2.0) * 3.0 * (k <= 2 ? k : 4) * np_ * 4.0;
+    if (dtype == RPBD_F32 && k <= 4 && h->use_sym[sym_class(k)] && sym_bytes <= 16.0 * (1ull << 30))
+        return sym_apply_impl(h, n, r, F, U, k, io_double, st);
     if (io_double || dtype == RPBD_F64)
         return apply_typed<double, double>(h, n, r, (const double*)F, (double*)U, k, dtype, st);
     return apply_typed<float, float>(h, n, r, (const float*)F, (float*)U, k, dtype, st);
