@@ -553,7 +553,7 @@ static int build_plan(rpbd_handle* h, const int64_t* off_host, int n_sys, int k,
 
 template <int K, int BT, int TS, bool WALL, class In, class Out>
 static int run_variant(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r, const In* F, Out* U, int k,
-                       const int* active, cudaStream_t st)
+                       const int* active, int prof_kind, cudaStream_t st)
 {
     constexpr int LEN = BRec<K>::LEN;
     const int64_t n_tot = p->off[n_sys];
@@ -587,7 +587,7 @@ static int run_variant(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r,
             const double ns = (double)(p->off[s + 1] - p->off[s]);
             pairs += ns * ns;
         }
-        prof_end(h, st, 2 /* batched FP32 */, K, pairs);
+        prof_end(h, st, prof_kind, K, pairs);
     }
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
     breduce_kernel<Out><<<(unsigned)((n_tot + 255) / 256), 256, 0, st>>>(n_sys, n_tot, k, K, tab, partial, scale,
@@ -599,7 +599,7 @@ static int run_variant(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r,
 
 template <int K, int BT, int TS, class In, class Out>
 static int run_variant2(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r, const In* F, Out* U, int k,
-                        const int* active, cudaStream_t st)
+                        const int* active, int prof_kind, cudaStream_t st)
 {
     constexpr int LEN = BRec2<K>::LEN;
     const int64_t n_tot = p->off[n_sys];
@@ -631,7 +631,7 @@ static int run_variant2(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r
             const double ns = (double)(p->off[s + 1] - p->off[s]);
             pairs += ns * ns;
         }
-        prof_end(h, st, 2 /* batched FP32 */, K, pairs);
+        prof_end(h, st, prof_kind, K, pairs);
     }
     // blocks were formed in units of a: M = M(a = 1) / a
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta * h->p.a);
@@ -644,25 +644,25 @@ static int run_variant2(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r
 
 template <int K, bool WALL, class In, class Out>
 static int run_k(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r, const In* F, Out* U, int k,
-                 const int* active, cudaStream_t st)
+                 const int* active, int pk, cudaStream_t st)
 {
     switch (p->variant) {
-    case 1: return run_variant<K, 64, 64, WALL>(h, p, n_sys, r, F, U, k, active, st);
-    case 2: return run_variant<K, 256, 32, WALL>(h, p, n_sys, r, F, U, k, active, st);
+    case 1: return run_variant<K, 64, 64, WALL>(h, p, n_sys, r, F, U, k, active, pk, st);
+    case 2: return run_variant<K, 256, 32, WALL>(h, p, n_sys, r, F, U, k, active, pk, st);
     case 3:
-        if constexpr (WALL) return run_variant2<K, 128, 64>(h, p, n_sys, r, F, U, k, active, st);
+        if constexpr (WALL) return run_variant2<K, 128, 64>(h, p, n_sys, r, F, U, k, active, pk, st);
         else return set_error(h, RPBD_BAD_ARG, "batched: the packed variant needs the wall");
-    default: return run_variant<K, 128, 64, WALL>(h, p, n_sys, r, F, U, k, active, st);
+    default: return run_variant<K, 128, 64, WALL>(h, p, n_sys, r, F, U, k, active, pk, st);
     }
 }
 
 template <bool WALL, class In, class Out>
 static int run_dispatch(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r, const In* F, Out* U, int k,
-                        const int* active, cudaStream_t st)
+                        const int* active, int pk, cudaStream_t st)
 {
-    if (k <= 1) return run_k<1, WALL>(h, p, n_sys, r, F, U, k, active, st);
-    if (k <= 4) return run_k<4, WALL>(h, p, n_sys, r, F, U, k, active, st);
-    return run_k<16, WALL>(h, p, n_sys, r, F, U, k, active, st);
+    if (k <= 1) return run_k<1, WALL>(h, p, n_sys, r, F, U, k, active, pk, st);
+    if (k <= 4) return run_k<4, WALL>(h, p, n_sys, r, F, U, k, active, pk, st);
+    return run_k<16, WALL>(h, p, n_sys, r, F, U, k, active, pk, st);
 }
 
 // find or build the plan of this batch for the handle's chosen variant
@@ -699,16 +699,40 @@ int batched_apply_impl(rpbd_handle* h, int n_sys, const int64_t* off, const doub
     RPBD_TRY(get_plan(h, n_sys, off, k, variant, &p));
     const bool wall = h->p.wall != 0;
     if (io_double)
-        return wall ? run_dispatch<true>(h, p, n_sys, r, (const double*)F, (double*)U, k, active, st)
-                    : run_dispatch<false>(h, p, n_sys, r, (const double*)F, (double*)U, k, active, st);
-    return wall ? run_dispatch<true>(h, p, n_sys, r, (const float*)F, (float*)U, k, active, st)
-                : run_dispatch<false>(h, p, n_sys, r, (const float*)F, (float*)U, k, active, st);
+        return wall ? run_dispatch<true>(h, p, n_sys, r, (const double*)F, (double*)U, k, active, 2, st)
+                    : run_dispatch<false>(h, p, n_sys, r, (const double*)F, (double*)U, k, active, 2, st);
+    return wall ? run_dispatch<true>(h, p, n_sys, r, (const float*)F, (float*)U, k, active, 2, st)
+                : run_dispatch<false>(h, p, n_sys, r, (const float*)F, (float*)U, k, active, 2, st);
+}
+
+int single_packed_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* F, void* U, int k,
+                             bool io_double, cudaStream_t st)
+{
+    if (!h->p.wall || h->p.Lx > 0.0 || k < 1 || k > 4 || n <= 0 || n > (int64_t)1 << 30)
+        return set_error(h, RPBD_BAD_ARG, "packed one-direction matvec: wall, open cell, 1 <= k <= 4");
+    // the work list depends on n only; it is kept apart from the batch plans
+    // (which captured graphs may reference) and rebuilt when n changes
+    const int64_t off[2] = {0, n};
+    if (h->mv_plan && h->mv_plan->off[1] != n) {
+        RPBD_CU(h, cudaStreamSynchronize(st));
+        free_plan(h->mv_plan);
+        h->mv_plan = nullptr;
+    }
+    if (!h->mv_plan) RPBD_TRY(build_plan(h, off, 1, k, 3, &h->mv_plan));
+    BatchPlan* p = h->mv_plan;
+    if (io_double)
+        return k == 1 ? run_k<1, true>(h, p, 1, r, (const double*)F, (double*)U, k, nullptr, RPBD_F32, st)
+                      : run_k<4, true>(h, p, 1, r, (const double*)F, (double*)U, k, nullptr, RPBD_F32, st);
+    return k == 1 ? run_k<1, true>(h, p, 1, r, (const float*)F, (float*)U, k, nullptr, RPBD_F32, st)
+                  : run_k<4, true>(h, p, 1, r, (const float*)F, (float*)U, k, nullptr, RPBD_F32, st);
 }
 
 void batched_free_plans(rpbd_handle* h)
 {
     for (BatchPlan* p : h->bplans) free_plan(p);
     h->bplans.clear();
+    free_plan(h->mv_plan);
+    h->mv_plan = nullptr;
 }
 
 }  // namespace rpbd

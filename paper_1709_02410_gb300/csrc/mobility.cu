@@ -469,6 +469,10 @@ int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* 
     const double sym_bytes = (np_ / 256.0 + np_ / 2048.0 + 2.0) * 3.0 * (k <= 2 ? k : 4) * np_ * 4.0;
     if (dtype == RPBD_F32 && k <= 4 && h->use_sym[sym_class(k)] && sym_bytes <= 16.0 * (1ull << 30))
         return sym_apply_impl(h, n, r, F, U, k, io_double, st);
+    // one direction with the wall in the open cell: the packed tile (two
+    // targets per thread) for k = 1, 3, 4; k = 2 keeps its own K = 2 tile
+    if (dtype == RPBD_F32 && h->use_packed && h->p.wall && !(h->p.Lx > 0.0) && k <= 4 && k != 2)
+        return single_packed_apply_impl(h, n, r, F, U, k, io_double, st);
     if (io_double || dtype == RPBD_F64)
         return apply_typed<double, double>(h, n, r, (const double*)F, (double*)U, k, dtype, st);
     return apply_typed<float, float>(h, n, r, (const float*)F, (float*)U, k, dtype, st);

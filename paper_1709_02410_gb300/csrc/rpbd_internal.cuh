@@ -115,6 +115,7 @@ struct rpbd_handle {
     std::vector<rpbd::BatchPlan*> bplans;
     int batch_variant = -1;
     std::vector<rpbd::BatchGraph*> bgraphs;
+    rpbd::BatchPlan* mv_plan = nullptr;  // work list of the single-system packed matvec
     // symmetric FP32 kernel (k <= 4): on by default, work list cached per n
     // symmetric-kernel choice per right-hand-side class (k = 1, k = 2, 3 <= k <= 4):
     // use it (1) or the one-direction kernel (0); variant -1: default, 0..3:
@@ -207,6 +208,10 @@ int sym_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* F, vo
 // batched systems (concatenated SoA; host offsets)
 int batched_apply_impl(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, const void* F, void* U,
                        int k, bool io_double, const int* active, cudaStream_t st);
+// one system through the packed batched tile (two targets per thread): the
+// one-direction FP32 matvec with the wall in the open cell, k in {1, 3, 4}
+int single_packed_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* F, void* U, int k,
+                             bool io_double, cudaStream_t st);
 void batched_free_plans(rpbd_handle* h);
 void batched_free_graphs(rpbd_handle* h);
 

@@ -204,3 +204,27 @@ def test_f32_packed_variants(variant, k):
     h.set_sym_variant(variant)
     U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
     assert rel2(U, om.apply(r, F.astype(np.float64), oracle_params(s))) <= 1e-5
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
+def test_f32_one_direction_packed_tile(k):
+    """With the symmetric kernel off, k = 1, 3, 4 run on the packed tile (two
+    targets per thread; one system of the batched kernel) and k = 2 on its
+    own tile; packed and unpacked one-direction kernels against the oracle at
+    sizes across the 64-source tile and the 2048-source chunk, the work list
+    rebuilt as n changes, FP32 and FP64 vectors."""
+    s = synth.c0_boomerangs_1920()
+    h = handle_for(s)
+    h.set_symmetric(False)
+    for n in (1, 63, 129, 2049, 4500, 700):
+        rng = np.random.default_rng(13 * n + k)
+        box = max(2.0, np.sqrt(n))
+        r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
+        F = rng.standard_normal((k, 3, n)).astype(np.float32)
+        Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
+        h.set_packed(True)
+        Up = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+        Ud = h.mobility_apply(to_dev(r), to_dev(F.astype(np.float64)), dtype=F32).cpu().numpy()
+        h.set_packed(False)
+        Uu = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+        assert rel2(Up, Uo) <= 1e-5 and rel2(Ud, Uo) <= 1e-5 and rel2(Uu, Uo) <= 1e-5, n
