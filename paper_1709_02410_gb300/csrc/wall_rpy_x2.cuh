@@ -57,7 +57,15 @@ __device__ __forceinline__ void overlap_fix(float r2, float rinv, const PairCons
     }
 }
 
-// alpha, beta, gx, gz, Mzz of two pairs (see pair_factors for the formulas)
+// alpha, beta, gx, gz, Mzz of two pairs (see pair_factors for the formulas).
+// With a = 1 the wall scalars are polynomials in w = 1/|R|^2, y = e_z^2 and
+// u = zi zj, regrouped in Horner form around shared factors:
+//   B + 1 = w h1,               h1 = (6u + 2 - 10y) + w (70/3 y - 10/3)
+//   A     = -1 + w (2y - 2u - 2/3 + w (2/3 - 10/3 y))
+//   -P    = (B + 1) - 20/3 w^2
+//   Z     = w (y (20w - 4 - h1) - 8/3 w)
+// so Rinv A and Rinv Z become v (...) with v = Rinv w, and no term is formed
+// twice.  zi6 = 6 zi and m2zi = -2 zi depend on the target only.
 __device__ __forceinline__ void pair_factors_x2(float2 dx, float2 dy, float2 dz, float2 zi, float2 zj,
                                                 const PairConstX2& c, float2& alpha, float2& beta, float2& gx,
                                                 float2& gz, float2& Mzz)
@@ -73,6 +81,8 @@ __device__ __forceinline__ void pair_factors_x2(float2 dx, float2 dy, float2 dz,
         overlap_fix(r2.x, rinv.x, c, c1.x, c2.x);
         overlap_fix(r2.y, rinv.y, c, c1.y, c2.y);
     }
+    const float2 zi6 = mul2(bc2(6.0f), zi);
+    const float2 m2zi = mul2(bc2(-2.0f), zi);
     // wall part
     const float2 Rz = add2(zi, zj);
     const float2 q = mul2(Rz, Rz);
@@ -80,26 +90,24 @@ __device__ __forceinline__ void pair_factors_x2(float2 dx, float2 dy, float2 dz,
     const float2 Rinv = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
     const float2 w = mul2(Rinv, Rinv);
     const float2 v = mul2(Rinv, w);
-    // with a = 1: s^2 = w, so x1 = w (zi zj + 1/3), x2 = w (e_z^2 + w/3)
-    const float2 sg2 = mul2(w, w);     // s^4
-    const float2 y = mul2(q, w);       // e_z^2
-    const float2 x1 = mul2(w, fma2(zi, zj, c.third));
-    const float2 x2 = mul2(w, fma2(c.third, w, y));
-    const float2 x3 = mul2(sg2, y);
-    // A = 2 (x2 - x1) - 10/3 x3 - 1 ;  B + 1 = 6 x1 - 10 x2 + 70/3 x3
-    const float2 A = fma2(bc2(2.0f), fma2(c.m1, x1, x2), fma2(bc2(-10.0f / 3.0f), x3, c.m1));
-    const float2 Bp = fma2(bc2(6.0f), x1, fma2(bc2(-10.0f), x2, mul2(bc2(70.0f / 3.0f), x3)));
-    const float2 P = fma2(c.m1, Bp, mul2(bc2(20.0f / 3.0f), sg2));
-    // Z = 20 x3 - 4 x2 - 4/3 s^4 - e_z^2 (B + 1)
-    const float2 Zd = fma2(c.m1, mul2(y, Bp), fma2(bc2(20.0f), x3, fma2(bc2(-4.0f), x2, mul2(bc2(-4.0f / 3.0f), sg2))));
-    alpha = fma2(Rinv, A, c1);
+    const float2 y = mul2(q, w);  // e_z^2
+    const float2 a1 = fma2(bc2(-10.0f), y, fma2(zi6, zj, bc2(2.0f)));
+    const float2 b1 = fma2(bc2(70.0f / 3.0f), y, bc2(-10.0f / 3.0f));
+    const float2 h1 = fma2(w, b1, a1);
+    const float2 Bp = mul2(w, h1);  // B + 1
     const float2 c2v = fma2(c.m1, v, c2);
     beta = fma2(v, Bp, c2v);
+    const float2 eA = fma2(m2zi, zj, fma2(bc2(2.0f), y, bc2(-2.0f / 3.0f)));
+    const float2 iA = fma2(w, fma2(bc2(-10.0f / 3.0f), y, c.a23), eA);
+    alpha = fma2(v, iA, fma2(c.m1, Rinv, c1));
+    const float2 Pn = fma2(mul2(bc2(-20.0f / 3.0f), w), w, Bp);  // -P
     const float2 base = mul2(dz, c2v);
-    const float2 vRP = mul2(mul2(v, Rz), P);
-    gx = add2(base, vRP);
-    gz = fma2(c.m1, vRP, base);
-    Mzz = fma2(Rinv, Zd, fma2(dz, base, alpha));
+    const float2 vRPn = mul2(mul2(v, Rz), Pn);
+    gx = fma2(c.m1, vRPn, base);
+    gz = add2(base, vRPn);
+    const float2 tz = fma2(bc2(20.0f), w, fma2(c.m1, h1, bc2(-4.0f)));
+    const float2 iZ = fma2(y, tz, mul2(bc2(-8.0f / 3.0f), w));
+    Mzz = fma2(v, iZ, fma2(dz, base, alpha));
 }
 
 }  // namespace rpbd
