@@ -44,7 +44,7 @@ extern "C" {
 
 /* arithmetic of the pair kernels */
 #define RPBD_F64 0 /* FP64 pair math, FP64 accumulation */
-#define RPBD_F32 1 /* FP32 pair math, FP32 tile partials summed in FP64 */
+#define RPBD_F32 1 /* FP32 pair math; FP32 tile partials summed as compensated float pairs (two-sum, ~48 bits), then FP64 */
 
 typedef struct rpbd_handle rpbd_handle;
 

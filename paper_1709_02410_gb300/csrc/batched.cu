@@ -22,6 +22,7 @@
 #include <cstring>
 #include <vector>
 
+#include "accum.cuh"
 #include "rpbd_internal.cuh"
 #include "wall_rpy.cuh"
 #include "wall_rpy_x2.cuh"
@@ -430,9 +431,9 @@ __global__ void breduce_kernel(int n_sys, int64_t n_tot, int k, int kt, SysTab t
     const int ns = tab.nslots[s];
     const double sc = scale[i] * inv8pieta;
     for (int q = 0; q < 3 * k; ++q) {
-        double sum = 0.0;
-        for (int c = 0; c < ns; ++c) sum += (double)partial[((int64_t)c * 3 * kt + q) * n_tot + i];
-        U[(int64_t)q * n_tot + i] = (Out)(sc * sum);
+        float hs = 0.0f, hc = 0.0f;  // compensated FP32 pair
+        for (int c = 0; c < ns; ++c) two_sum_acc(hs, hc, partial[((int64_t)c * 3 * kt + q) * n_tot + i]);
+        U[(int64_t)q * n_tot + i] = (Out)(sc * two_sum_value(hs, hc));
     }
 }
 

@@ -19,6 +19,7 @@
 #include <algorithm>
 #include <cmath>
 
+#include "accum.cuh"
 #include "rpbd_internal.cuh"
 #include "wall_rpy.cuh"
 
@@ -361,7 +362,13 @@ __global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_chu
     const double s = scale[i] * inv8pieta;
     for (int q = 0; q < 3 * k; ++q) {
         double sum = 0.0;
-        for (int c = 0; c < n_chunks; ++c) sum += (double)partial[((int64_t)c * 3 * kt + q) * n_pad + i];
+        if constexpr (sizeof(P) == 4) {  // FP32 partials: compensated FP32 pair
+            float hs = 0.0f, hc = 0.0f;
+            for (int c = 0; c < n_chunks; ++c) two_sum_acc(hs, hc, partial[((int64_t)c * 3 * kt + q) * n_pad + i]);
+            sum = two_sum_value(hs, hc);
+        } else {
+            for (int c = 0; c < n_chunks; ++c) sum += (double)partial[((int64_t)c * 3 * kt + q) * n_pad + i];
+        }
         U[(int64_t)q * n + i] = (Out)(s * sum);
     }
 }

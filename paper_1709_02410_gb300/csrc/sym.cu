@@ -27,6 +27,7 @@
 #include <algorithm>
 #include <vector>
 
+#include "accum.cuh"
 #include "rpbd_internal.cuh"
 #include "wall_rpy.cuh"
 #include "wall_rpy_x2.cuh"
@@ -311,7 +312,9 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
 // home tiles before blob i's tile spreads over many threads (several loads in
 // flight each): pass 1 sums home tiles [s SEG, (s+1) SEG) for segment s =
 // blockIdx.y; pass 2 adds the segments and the home partials, then scales.
-// Both passes use a fixed order (deterministic).
+// Both passes use a fixed order (deterministic).  The FP32 partials are
+// accumulated as compensated float pairs (accum.cuh), widened to FP64 once
+// per segment.
 constexpr int SEG = 64;  // home tiles per segment
 
 template <int HTT, int KT, class P>
@@ -324,19 +327,19 @@ __global__ void reduce_visitors_kernel(int64_t n, int64_t n_pad, int k, const P*
     const int H0 = blockIdx.y * SEG;
     const int H1 = (H0 + SEG) < h ? (H0 + SEG) : h;
     if (H0 >= H1) return;
-    double acc[3 * KT];
+    float s[3 * KT], c[3 * KT];
 #pragma unroll
-    for (int q = 0; q < 3 * KT; ++q) acc[q] = 0.0;
+    for (int q = 0; q < 3 * KT; ++q) s[q] = c[q] = 0.0f;
+#pragma unroll 4
     for (int H = H0; H < H1; ++H)
 #pragma unroll
         for (int q = 0; q < 3 * KT; ++q)
-            if (q < 3 * k) acc[q] += (double)partial[((int64_t)H * 3 * KT + q) * n_pad + i];
+            if (q < 3 * k) two_sum_acc(s[q], c[q], partial[((int64_t)H * 3 * KT + q) * n_pad + i]);
 #pragma unroll
     for (int q = 0; q < 3 * KT; ++q)
-        if (q < 3 * k) segsum[((int64_t)blockIdx.y * 3 * KT + q) * n_pad + i] = acc[q];
+        if (q < 3 * k) segsum[((int64_t)blockIdx.y * 3 * KT + q) * n_pad + i] = two_sum_value(s[q], c[q]);
 }
 
-// U_i = s_i/(8 pi eta) [sum_{segments before tile(i)} + sum_c home partial(c)]
 template <int HTT, class P, class Out>
 __global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_home_tiles, int chunk,
                               const P* __restrict__ partial, const double* __restrict__ segsum,
@@ -352,8 +355,10 @@ __global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_hom
     for (int q = 0; q < 3 * k; ++q) {
         double sum = 0.0;
         for (int sg = 0; sg < nseg; ++sg) sum += segsum[((int64_t)sg * 3 * kt + q) * n_pad + i];
+        float hs = 0.0f, hc = 0.0f;
         for (int c = 0; c < home_slots; ++c)
-            sum += (double)partial[((int64_t)(n_home_tiles + c) * 3 * kt + q) * n_pad + i];
+            two_sum_acc(hs, hc, (float)partial[((int64_t)(n_home_tiles + c) * 3 * kt + q) * n_pad + i]);
+        sum += two_sum_value(hs, hc);
         U[(int64_t)q * n + i] = (Out)(sc * sum);
     }
 }
