@@ -36,11 +36,12 @@ K_RHS = 16
 F_GEOM = 76                  # algorithmic flops of one pair block (FMA = 2, rsqrt = 1)
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (read + write) per launch from one ncu capture of the current
-# kernels (profiles/pair_kernel_f32_k*_boomerangs_65535.md); None when not captured
-NCU_TRAFFIC = {"f32_k16": 22067968 + 343998464, "f32symf_k1": 4379392 + 55015936,
-               "f32symf_k2": 8208640 + 168576256}
+# kernels (profiles/pair_kernel_f32_k16_boomerangs_65535.md, profiles/sym_kernel_f32_k*_boomerangs_65535.md);
+# None when not captured
+NCU_TRAFFIC = {"f32_k16": 22067968 + 343998464, "f32symf_k1": 4349440 + 54785536,
+               "f32symf_k2": 7982336 + 168043520}
 # FMA-pipe activity (sm__pipe_fma_cycles_active) from the same captures
-NCU_FMA_PIPE = {"f32_k16": 0.781, "f32symf_k1": 0.778, "f32symf_k2": 0.749}
+NCU_FMA_PIPE = {"f32_k16": 0.781, "f32symf_k1": 0.761, "f32symf_k2": 0.731}
 
 
 F_ASSEMBLY = 12             # flops of forming the 9 entries from the block's 5 scalars
