@@ -18,7 +18,10 @@
  *    Krylov iteration (Lanczos, GMRES, steps) read a residual back to the
  *    host once per iteration and return only when done.
  *  - Return value: RPBD_OK (0) or a negative status; rpbd_last_error(h)
- *    gives a message.  Inputs with NaN/Inf positions give RPBD_BAD_INPUT.
+ *    gives a message.  The calls that synchronise (Lanczos, GMRES, time
+ *    steps) check the blob positions first and return RPBD_BAD_INPUT for
+ *    NaN/Inf; the asynchronous kernel-only calls do not read anything back,
+ *    so non-finite inputs there give non-finite outputs.
  *  - The handle owns a device workspace that grows on demand
  *    (cudaMalloc); rpbd_reserve() sizes it ahead of time.  A handle is used
  *    by one host thread at a time.
@@ -201,7 +204,10 @@ int rpbd_precond_apply(rpbd_handle* h, int mode, const double* x, double* out, v
 
 /* out[3][n] ~ L f(L^-1 M L^-T) W with f = sqrt, by Lanczos with full
  * reorthogonalisation from v_1 = W/|W|; stops when |y_m - y_{m-1}|/|y_m| < tol.
- * use_precond = 0 runs on M itself (L = I).  W, out: [3][n] FP64. */
+ * use_precond = 0 runs on M itself (L = I).  W, out: [3][n] FP64.
+ * 1 <= max_iter <= 80 (the basis and the tridiagonal square root are sized
+ * for 80); RPBD_NOT_CONVERGED when it stops at max_iter (out then holds the
+ * last iterate). */
 int rpbd_lanczos_sqrt_apply(rpbd_handle* h, int64_t n, const double* r, const double* W,
                             double* out, double tol, int max_iter, int dtype, int use_precond,
                             rpbd_stats* stats, void* stream);

@@ -167,7 +167,7 @@ class Handle:
         return out
 
     # ---- a4
-    def lanczos_sqrt_apply(self, r, W, tol, max_iter=100, dtype=F64, use_precond=True, out=None):
+    def lanczos_sqrt_apply(self, r, W, tol, max_iter=80, dtype=F64, use_precond=True, out=None):
         n = r.shape[1]
         out = torch.empty_like(W) if out is None else out
         st = Stats()

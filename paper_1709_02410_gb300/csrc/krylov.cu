@@ -304,6 +304,8 @@ int lanczos_multi_impl(rpbd_handle* h, int64_t n, const double* r, int nsys, con
     if (max_iter < 1 || max_iter > LANCZOS_MAX) return set_error(h, RPBD_BAD_ARG, "lanczos: max_iter must be in 1..80");
     if (use_precond && (!h->prec_valid || h->prec_nb * h->prec_nper != n))
         return set_error(h, RPBD_BAD_ARG, "lanczos: preconditioner not built for these blobs");
+    if (!r) return set_error(h, RPBD_BAD_ARG, "lanczos: null positions");
+    RPBD_TRY(check_finite(h, 3 * n, r, st));
     const int64_t len = 3 * n;
     const int mdim = LANCZOS_MAX + 1;
     const size_t small_count = Small::count(mdim) + 4 * (size_t)mdim;
@@ -477,6 +479,8 @@ int gmres_multi_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, cons
         if (probs[s].max_iter < 1 || !probs[s].lambda || !probs[s].U)
             return set_error(h, RPBD_BAD_ARG, "gmres: bad max_iter or null output");
     const int64_t n = nb * nper;
+    if (!r || !q) return set_error(h, RPBD_BAD_ARG, "gmres: null positions");
+    RPBD_TRY(check_finite(h, 3 * (int64_t)nb * nper, r, st));
     if (build_precond) RPBD_TRY(precond_build_impl(h, nb, nper, r, q, st));
     if (!h->prec_valid || h->prec_nb != nb || h->prec_nper != nper)
         return set_error(h, RPBD_BAD_ARG, "gmres: preconditioner not built for these bodies");
