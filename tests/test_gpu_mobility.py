@@ -228,3 +228,51 @@ def test_f32_one_direction_packed_tile(k):
         h.set_packed(False)
         Uu = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
         assert rel2(Up, Uo) <= 1e-5 and rel2(Ud, Uo) <= 1e-5 and rel2(Uu, Uo) <= 1e-5, n
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_f32_half_million_blobs_row_sampled(k):
+    """500,010 blobs (33,334 boomerangs at the same density): k = 1 keeps the
+    packed symmetric kernel (13 GB of visitor partials), k = 2 and k = 3 pass
+    the 16 GiB limit of those partials and take the one-direction kernels
+    (k = 2 its own tile, k = 3 the packed tile with K = 4); 32 sampled rows
+    against the oracle."""
+    nb = 33334
+    s = synth.boomerang_suspension(nb, 40.0 * np.sqrt(nb / 128), 44)
+    r = positions(s)
+    F = synth.gaussian(45 + k, (k, 3, s.n), np.float32)
+    h = handle_for(s)
+    U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    rows = np.random.default_rng(46).choice(s.n, 32, replace=False)
+    rows[0], rows[1] = 0, s.n - 1
+    Uo = om.apply(r, F.astype(np.float64), oracle_params(s), rows=rows)
+    h.close()
+    assert rel2(U[:, :, rows], Uo) <= 1e-5
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_f32_packed_far_from_origin_and_wide(k):
+    """Positions far from the origin and spread wide: the FP32 kernels carry
+    x, y as hi/lo float pairs, so a translation by 10^5 a leaves U unchanged
+    (to FP32 rounding of the pair blocks), and a 4,000 a wide scatter of
+    clusters still meets the oracle at 1e-5."""
+    s = synth.c0_boomerangs_1920()
+    r = positions(s)
+    F = synth.gaussian(47 + k, (k, 3, s.n), np.float32)
+    h = handle_for(s)
+    U0 = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    rt = r.copy()
+    rt[0] += 1.0e5 * s.a
+    rt[1] -= 3.0e5 * s.a
+    Ut = h.mobility_apply(to_dev(rt), to_dev(F, torch.float32)).cpu().numpy()
+    Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
+    assert rel2(U0, Uo) <= 1e-5 and rel2(Ut, Uo) <= 1e-5 and rel2(Ut, U0) <= 1e-6
+    # bodies in 16 clusters spread over 4,000 a
+    rng = np.random.default_rng(48)
+    shift = rng.uniform(-2000.0, 2000.0, (16, 2)) * s.a
+    rw = r.copy()
+    body = np.arange(s.n) // s.nper
+    rw[0] += shift[body % 16, 0]
+    rw[1] += shift[body % 16, 1]
+    Uw = h.mobility_apply(to_dev(rw), to_dev(F, torch.float32)).cpu().numpy()
+    assert rel2(Uw, om.apply(rw, F.astype(np.float64), oracle_params(s))) <= 1e-5
