@@ -470,10 +470,12 @@ int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* 
     if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "bad dtype");
     if (!r || !F || !U) return set_error(h, RPBD_BAD_ARG, "null pointer");
     // the symmetric kernels keep one visitor partial per (home tile, blob): about
-    // n^2 / 256 * 3k floats; beyond 16 GiB (n of order a million) the
-    // one-direction kernel, whose partials grow as n^2 / 2048, takes over
+    // n^2 / 256 * 3k floats, plus FP64 segment sums (one per 16 home tiles);
+    // beyond 16 GiB (n of order a million) the one-direction kernel, whose
+    // partials grow as n^2 / 2048, takes over
     const double np_ = (double)(n + 255);
-    const double sym_bytes = (np_ / 256.0 + np_ / 2048.0 + 2.0) * 3.0 * (k <= 2 ? k : 4) * np_ * 4.0;
+    const double sym_bytes =
+        (np_ / 256.0 + np_ / 2048.0 + 2.0 * np_ / 4096.0 + 4.0) * 3.0 * (k <= 2 ? k : 4) * np_ * 4.0;
     if (dtype == RPBD_F32 && k <= 4 && h->use_sym[sym_class(k)] && sym_bytes <= 16.0 * (1ull << 30))
         return sym_apply_impl(h, n, r, F, U, k, io_double, st);
     // one direction with the wall in the open cell: the packed tile (two

@@ -315,7 +315,7 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
 // Both passes use a fixed order (deterministic).  The FP32 partials are
 // accumulated as compensated float pairs (accum.cuh), widened to FP64 once
 // per segment.
-constexpr int SEG = 64;  // home tiles per segment
+constexpr int SEG = 16;  // home tiles per segment
 
 template <int HTT, int KT, class P>
 __global__ void reduce_visitors_kernel(int64_t n, int64_t n_pad, int k, const P* __restrict__ partial,
@@ -330,8 +330,21 @@ __global__ void reduce_visitors_kernel(int64_t n, int64_t n_pad, int k, const P*
     float s[3 * KT], c[3 * KT];
 #pragma unroll
     for (int q = 0; q < 3 * KT; ++q) s[q] = c[q] = 0.0f;
-#pragma unroll 4
-    for (int H = H0; H < H1; ++H)
+    // four home tiles' loads issued together, then added in home-tile order
+    int H = H0;
+    for (; H + 4 <= H1; H += 4) {
+        P v[4][3 * KT];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < 3 * KT; ++q)
+                v[u][q] = q < 3 * k ? partial[((int64_t)(H + u) * 3 * KT + q) * n_pad + i] : P(0);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < 3 * KT; ++q) two_sum_acc(s[q], c[q], v[u][q]);
+    }
+    for (; H < H1; ++H)
 #pragma unroll
         for (int q = 0; q < 3 * KT; ++q)
             if (q < 3 * k) two_sum_acc(s[q], c[q], partial[((int64_t)H * 3 * KT + q) * n_pad + i]);
