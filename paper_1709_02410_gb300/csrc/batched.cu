@@ -424,17 +424,28 @@ __global__ void breduce_kernel(int n_sys, int64_t n_tot, int k, int kt, SysTab t
                                const double* __restrict__ scale, const int* __restrict__ active, double inv8pieta,
                                Out* __restrict__ U)
 {
+    // one thread per (blob, component q = blockIdx.y < 3k); slots summed in
+    // order as a compensated FP32 pair, four slots' loads issued together
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_tot) return;
+    const int q = blockIdx.y;
+    if (i >= n_tot || q >= 3 * k) return;
     const int s = find_sys(tab.off, n_sys, i);
     if (active && !active[s]) return;
     const int ns = tab.nslots[s];
-    const double sc = scale[i] * inv8pieta;
-    for (int q = 0; q < 3 * k; ++q) {
-        float hs = 0.0f, hc = 0.0f;  // compensated FP32 pair
-        for (int c = 0; c < ns; ++c) two_sum_acc(hs, hc, partial[((int64_t)c * 3 * kt + q) * n_tot + i]);
-        U[(int64_t)q * n_tot + i] = (Out)(sc * two_sum_value(hs, hc));
+    const float* src = partial + (int64_t)q * n_tot + i;
+    const int64_t stride = (int64_t)3 * kt * n_tot;
+    float hs = 0.0f, hc = 0.0f;
+    int c = 0;
+    for (; c + 4 <= ns; c += 4) {
+        const float v0 = src[c * stride], v1 = src[(c + 1) * stride], v2 = src[(c + 2) * stride],
+                    v3 = src[(c + 3) * stride];
+        two_sum_acc(hs, hc, v0);
+        two_sum_acc(hs, hc, v1);
+        two_sum_acc(hs, hc, v2);
+        two_sum_acc(hs, hc, v3);
     }
+    for (; c < ns; ++c) two_sum_acc(hs, hc, src[c * stride]);
+    U[(int64_t)q * n_tot + i] = (Out)(scale[i] * inv8pieta * two_sum_value(hs, hc));
 }
 
 // ---------------------------------------------------------------------------
@@ -591,7 +602,7 @@ static int run_variant(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r,
         prof_end(h, st, prof_kind, K, pairs);
     }
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
-    breduce_kernel<Out><<<(unsigned)((n_tot + 255) / 256), 256, 0, st>>>(n_sys, n_tot, k, K, tab, partial, scale,
+    breduce_kernel<Out><<<dim3((unsigned)((n_tot + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(n_sys, n_tot, k, K, tab, partial, scale,
                                                                          active, inv8pieta, U);
     count_launch();
     RPBD_LAUNCH_CHECK(h);
@@ -636,7 +647,7 @@ static int run_variant2(rpbd_handle* h, BatchPlan* p, int n_sys, const double* r
     }
     // blocks were formed in units of a: M = M(a = 1) / a
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta * h->p.a);
-    breduce_kernel<Out><<<(unsigned)((n_tot + 255) / 256), 256, 0, st>>>(n_sys, n_tot, k, K, tab, partial, scale,
+    breduce_kernel<Out><<<dim3((unsigned)((n_tot + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(n_sys, n_tot, k, K, tab, partial, scale,
                                                                          active, inv8pieta, U);
     count_launch();
     RPBD_LAUNCH_CHECK(h);

@@ -352,25 +352,36 @@ static auto pick_pair_kernel()
 // ---------------------------------------------------------------------------
 // 3. reduce
 
+// one thread per (blob, component q = blockIdx.y < 3k): the chunk partials
+// summed in chunk order (deterministic), four chunks' loads issued together
 template <class P, class Out>
 __global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_chunks,
                               const P* __restrict__ partial, const double* __restrict__ scale,
                               double inv8pieta, Out* __restrict__ U)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
-    const double s = scale[i] * inv8pieta;
-    for (int q = 0; q < 3 * k; ++q) {
-        double sum = 0.0;
-        if constexpr (sizeof(P) == 4) {  // FP32 partials: compensated FP32 pair
-            float hs = 0.0f, hc = 0.0f;
-            for (int c = 0; c < n_chunks; ++c) two_sum_acc(hs, hc, partial[((int64_t)c * 3 * kt + q) * n_pad + i]);
-            sum = two_sum_value(hs, hc);
-        } else {
-            for (int c = 0; c < n_chunks; ++c) sum += (double)partial[((int64_t)c * 3 * kt + q) * n_pad + i];
+    const int q = blockIdx.y;
+    if (i >= n || q >= 3 * k) return;
+    const P* src = partial + (int64_t)q * n_pad + i;
+    const int64_t stride = (int64_t)3 * kt * n_pad;
+    double sum = 0.0;
+    int c = 0;
+    if constexpr (sizeof(P) == 4) {  // FP32 partials: compensated FP32 pair
+        float hs = 0.0f, hc = 0.0f;
+        for (; c + 4 <= n_chunks; c += 4) {
+            const float v0 = src[c * stride], v1 = src[(c + 1) * stride], v2 = src[(c + 2) * stride],
+                        v3 = src[(c + 3) * stride];
+            two_sum_acc(hs, hc, v0);
+            two_sum_acc(hs, hc, v1);
+            two_sum_acc(hs, hc, v2);
+            two_sum_acc(hs, hc, v3);
         }
-        U[(int64_t)q * n + i] = (Out)(s * sum);
+        for (; c < n_chunks; ++c) two_sum_acc(hs, hc, src[c * stride]);
+        sum = two_sum_value(hs, hc);
+    } else {
+        for (; c < n_chunks; ++c) sum += (double)src[c * stride];
     }
+    U[(int64_t)q * n + i] = (Out)(scale[i] * inv8pieta * sum);
 }
 
 // ---------------------------------------------------------------------------
@@ -431,7 +442,7 @@ static int apply_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out*
     if (h->profile) prof_end(h, st, sizeof(R) == 4 ? RPBD_F32 : RPBD_F64, K, (double)n * (double)n);
     RPBD_LAUNCH_CHECK(h);
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
-    reduce_kernel<typename PartialT<R>::type, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(
+    reduce_kernel<typename PartialT<R>::type, Out><<<dim3((unsigned)((n + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(
         n, n_pad, k, K, n_chunks, partial, scale, inv8pieta, U); count_launch();
     RPBD_LAUNCH_CHECK(h);
     return RPBD_OK;
@@ -583,8 +594,8 @@ static int apply(int sm_count, const rpbd_params& p, int64_t n, const double* r,
         rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, flag);
     count_launch();
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * p.eta);
-    reduce_kernel<float, float><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_chunks, partial, scale,
-                                                                          inv8pieta, U);
+    reduce_kernel<float, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(
+        n, n_pad, k, K, n_chunks, partial, scale, inv8pieta, U);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? RPBD_OK : RPBD_CUDA;
 }

@@ -358,22 +358,21 @@ __global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_hom
                               const P* __restrict__ partial, const double* __restrict__ segsum,
                               const double* __restrict__ scale, double inv8pieta, Out* __restrict__ U)
 {
+    // one thread per (blob, component q = blockIdx.y < 3k)
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n) return;
+    const int q = blockIdx.y;
+    if (i >= n || q >= 3 * k) return;
     const int h = (int)(i / HTT);
     const int nseg = (h + SEG - 1) / SEG;
     const int64_t vis = n_pad - (int64_t)(h + 1) * HTT;  // visitors of tile h
     const int home_slots = 1 + (int)((vis + chunk - 1) / chunk);
-    const double sc = scale[i] * inv8pieta;
-    for (int q = 0; q < 3 * k; ++q) {
-        double sum = 0.0;
-        for (int sg = 0; sg < nseg; ++sg) sum += segsum[((int64_t)sg * 3 * kt + q) * n_pad + i];
-        float hs = 0.0f, hc = 0.0f;
-        for (int c = 0; c < home_slots; ++c)
-            two_sum_acc(hs, hc, (float)partial[((int64_t)(n_home_tiles + c) * 3 * kt + q) * n_pad + i]);
-        sum += two_sum_value(hs, hc);
-        U[(int64_t)q * n + i] = (Out)(sc * sum);
-    }
+    double sum = 0.0;
+    for (int sg = 0; sg < nseg; ++sg) sum += segsum[((int64_t)sg * 3 * kt + q) * n_pad + i];
+    float hs = 0.0f, hc = 0.0f;
+    for (int c = 0; c < home_slots; ++c)
+        two_sum_acc(hs, hc, (float)partial[((int64_t)(n_home_tiles + c) * 3 * kt + q) * n_pad + i]);
+    sum += two_sum_value(hs, hc);
+    U[(int64_t)q * n + i] = (Out)(scale[i] * inv8pieta * sum);
 }
 
 // Work items of the symmetric kernels for home tiles of TILE blobs: per home
@@ -466,7 +465,7 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     reduce_visitors_kernel<HT, K, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)nseg), 256, 0, st>>>(
         n, n_pad, k, partial, segsum);
     count_launch();
-    reduce_kernel<HT, float, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_home, chunk,
+    reduce_kernel<HT, float, Out><<<dim3((unsigned)((n + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(n, n_pad, k, K, n_home, chunk,
                                                                                partial, segsum, scale, inv8pieta, U);
     count_launch();
     RPBD_LAUNCH_CHECK(h);
@@ -802,7 +801,7 @@ static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U,
     reduce_visitors_kernel<HT2, K, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)nseg), 256, 0, st>>>(
         n, n_pad, k, partial, segsum);
     count_launch();
-    reduce_kernel<HT2, float, Out><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, n_pad, k, K, n_home, chunk,
+    reduce_kernel<HT2, float, Out><<<dim3((unsigned)((n + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(n, n_pad, k, K, n_home, chunk,
                                                                                 partial, segsum, scale, inv8pieta, U);
     count_launch();
     RPBD_LAUNCH_CHECK(h);
