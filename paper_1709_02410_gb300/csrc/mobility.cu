@@ -11,9 +11,10 @@
 //              thread owns one target blob, forms the 3x3 block of every
 //              pair once and applies it to all k right-hand sides from
 //              registers.  FP32 kernels keep FP32 sums over one chunk.
-//   3. reduce: sums the chunk partials in FP64 in a fixed order (the
-//              result is deterministic), multiplies by s_i / (8 pi eta) and
-//              writes U in the caller's type.
+//   3. reduce: sums the chunk partials in a fixed order (FP64 partials
+//              in FP64, FP32 partials as compensated float pairs, about
+//              48 bits; the result is deterministic), multiplies by
+//              s_i / (8 pi eta) and writes U in the caller's type.
 #include <cuda_runtime.h>
 
 #include <algorithm>
