@@ -365,6 +365,11 @@ def run_ours(args, rank, world, local):
             "clocks": clk,
             "pair_kernels_in_step": prof,
             "solver_iterations_per_step": iters,
+            # M applications (right-hand sides) per T-S step, without the k = 16 batch; the
+            # paper's count is n_G per saddle solve x 3 + n_L + 2 (two RFD matvecs)
+            "m_applies_per_ts_step": {
+                "measured": (rhs_local - K_RHS * prof.get("f32_k16", {}).get("launches", 0)) / args.steps,
+                "iterations_plus_2": sum(sum(x) + 2 for x in iters) / max(1, len(iters))},
             "autotune_k1": {"choice": tuned[0], "ms_per_launch": tuned[1],
                             "legend": "0: one-direction kernel; 1 + v: symmetric kernel variant v"},
             "autotune_k2": {"choice": tuned2[0], "ms_per_launch": tuned2[1]},
