@@ -358,9 +358,11 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
  * pair blocks formed by two-wide FP32 instructions); 0: the one-home kernel. */
 #define RPBD_OPT_PACKED 3
 /* tile variant of the batched kernel (what rpbd_autotune_batched picks):
- * -1: the default (3 with the wall, else 0); 0: 128 targets x 64-source
+ * -1: the default (4 with the wall, else 0); 0: 128 targets x 64-source
  * tiles, 1: 64 x 64, 2: 256 x 32, 3 (wall only): 256 targets, two per thread
- * in packed two-wide FP32 x 64-source tiles. */
+ * in packed two-wide FP32 x 64-source tiles; 4 (wall only, k <= 4): the
+ * packed symmetric kernel over the batch (each system's unordered pairs
+ * formed once, applied both ways; k > 4 then runs on variant 3). */
 #define RPBD_OPT_BATCH_VARIANT 4
 int rpbd_set_option(rpbd_handle* h, int option, int value);
 

@@ -67,7 +67,8 @@ class Handle:
         return st
 
     def set_batch_variant(self, v: int):
-        """tile variant of the batched kernel (-1 default, 0..3; 3: packed two targets per thread)"""
+        """tile variant of the batched kernel (-1 default, 0..4; 3: packed two targets per thread;
+        4: packed symmetric kernel for k <= 4)"""
         self._check(self.lib.rpbd_set_option(self.h, 4, int(v)), "set_option")
 
     def set_packed(self, on: bool):

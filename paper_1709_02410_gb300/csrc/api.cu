@@ -249,8 +249,8 @@ int rpbd_set_option(rpbd_handle* h, int option, int value)
         return RPBD_OK;
     case RPBD_OPT_PACKED: h->use_packed = value != 0; return RPBD_OK;
     case RPBD_OPT_BATCH_VARIANT:
-        if (value < -1 || value > 3) return set_error(h, RPBD_BAD_ARG, "batched variant must be -1..3");
-        if (value == 3 && !h->p.wall) return set_error(h, RPBD_BAD_ARG, "the packed batched variant needs the wall");
+        if (value < -1 || value > 4) return set_error(h, RPBD_BAD_ARG, "batched variant must be -1..4");
+        if (value >= 3 && !h->p.wall) return set_error(h, RPBD_BAD_ARG, "the packed batched variants need the wall");
         h->batch_variant = value;
         return RPBD_OK;
     case RPBD_OPT_SYM_VARIANT:

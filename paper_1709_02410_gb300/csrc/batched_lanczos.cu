@@ -179,7 +179,11 @@ struct BatchGraph {
     double tol = 0.0;
     int use_precond = 0;
     bool with_apply = false;
-    void* sig[4] = {};
+    int variant = -1;
+    // every workspace buffer the captured kernels address: a buffer that has
+    // grown (moved) since the capture invalidates the graph
+    static constexpr int NSIG = 8;
+    void* sig[NSIG] = {};
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap = nullptr;
 };
@@ -333,25 +337,33 @@ int rpbd_lanczos_sqrt_apply_batched(rpbd_handle* h, int n_sys, const int64_t* of
         RPBD_TRY(blz_body(h, n_sys, offsets, n, B, tol, max_iter, use_precond, with_apply, st));
     } else {
         BatchGraph* G = nullptr;
-        void* sig[4] = {B.V, h->buf[BUF_BPACK], h->buf[BUF_BPARTIAL], h->buf[BUF_PREC_L]};
+        auto signature = [&](void** sg) {
+            const Buf bs[BatchGraph::NSIG] = {BUF_BLZ,     BUF_BLZ_SMALL, BUF_BPACK,  BUF_BPARTIAL,
+                                              BUF_BSCALE,  BUF_BSEG,      BUF_PREC_L, BUF_PREC_LINV};
+            for (int i = 0; i < BatchGraph::NSIG; ++i) sg[i] = h->buf[bs[i]];
+        };
+        void* sig[BatchGraph::NSIG];
+        signature(sig);
         for (BatchGraph* c : h->bgraphs)
             if (c->max_iter == max_iter && c->tol == tol && c->use_precond == use_precond &&
-                c->with_apply == with_apply && (int)c->off.size() == n_sys + 1 &&
-                std::equal(c->off.begin(), c->off.end(), offsets) && std::equal(sig, sig + 4, c->sig))
+                c->with_apply == with_apply && c->variant == h->batch_variant && (int)c->off.size() == n_sys + 1 &&
+                std::equal(c->off.begin(), c->off.end(), offsets) && std::equal(sig, sig + BatchGraph::NSIG, c->sig))
                 G = c;
         if (!G) {
             // run once eagerly so every workspace buffer and work list exists,
             // then capture the same sequence of kernels
             RPBD_TRY(blz_body(h, n_sys, offsets, n, B, tol, max_iter, use_precond, with_apply, st));
             RPBD_CU(h, cudaStreamSynchronize(st));
-            void* sig2[4] = {B.V, h->buf[BUF_BPACK], h->buf[BUF_BPARTIAL], h->buf[BUF_PREC_L]};
+            void* sig2[BatchGraph::NSIG];
+            signature(sig2);
             G = new BatchGraph();
             G->off.assign(offsets, offsets + n_sys + 1);
             G->max_iter = max_iter;
             G->tol = tol;
             G->use_precond = use_precond;
             G->with_apply = with_apply;
-            std::copy(sig2, sig2 + 4, G->sig);
+            G->variant = h->batch_variant;
+            std::copy(sig2, sig2 + BatchGraph::NSIG, G->sig);
             h->bgraphs.push_back(G);
             RPBD_CU(h, cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking));
             const bool prof = h->profile;

@@ -67,12 +67,13 @@ enum Buf {
     BUF_SYM_ITEMS,   // symmetric kernel: work items
     BUF_GMRES_MV,    // lockstep GMRES: gathered multi-RHS matvec operands
     BUF_SYM_SEG,     // symmetric kernel: segment sums of the visitor partials
-    BUF_SYM2_ITEMS,  // packed symmetric kernel: work items
+    BUF_BSEG,        // batched symmetric kernel: segment sums of the visitor partials
     BUF_COUNT
 };
 
 struct BatchPlan;
 struct BatchGraph;
+struct Sym2Plan;
 
 struct ProfRec {
     cudaEvent_t a, b;
@@ -116,13 +117,14 @@ struct rpbd_handle {
     int batch_variant = -1;
     std::vector<rpbd::BatchGraph*> bgraphs;
     rpbd::BatchPlan* mv_plan = nullptr;  // work list of the single-system packed matvec
+    std::vector<rpbd::Sym2Plan*> sym2_plans;  // work lists of the packed symmetric kernel, per offsets
     // symmetric FP32 kernel (k <= 4): on by default, work list cached per n
     // symmetric-kernel choice per right-hand-side class (k = 1, k = 2, 3 <= k <= 4):
     // use it (1) or the one-direction kernel (0); variant -1: default, 0..3:
     // loop unroll / occupancy variants
     int use_sym[3] = {1, 1, 1};
     int sym_variant[3] = {-1, -1, -1};
-    rpbd::SymPlan sym_plan[2];  // work lists of the symmetric kernels: 128- and 256-blob home tiles
+    rpbd::SymPlan sym_plan;     // work list of the one-home symmetric kernel (128-blob home tiles)
     int use_packed = 1;         // k <= 4 with the wall: the packed two-homes-per-thread symmetric kernel
 };
 
@@ -212,6 +214,10 @@ int batched_apply_impl(rpbd_handle* h, int n_sys, const int64_t* off, const doub
 // one-direction FP32 matvec with the wall in the open cell, k in {1, 3, 4}
 int single_packed_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* F, void* U, int k,
                              bool io_double, cudaStream_t st);
+// the packed symmetric kernel over a batch of systems (wall, open cell, k <= 4)
+int sym_batched_apply_impl(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, const void* F, void* U,
+                           int k, bool io_double, const int* active, cudaStream_t st);
+void free_sym2_plans(rpbd_handle* h);
 void batched_free_plans(rpbd_handle* h);
 void batched_free_graphs(rpbd_handle* h);
 

@@ -55,11 +55,40 @@ struct SymVar {
 };
 
 struct SymItem {
-    int home;   // home tile index
-    int v0;     // first visitor blob (multiple of VT)
+    int home;   // home tile index (global, in records)
+    int v0;     // first visitor record (multiple of VT)
     int ntile;  // visitor tiles
     int slot;   // home-partial slot (0: diagonal item)
+    int sys;    // system of a batch (0 for a single system)
 };
+
+// One system of the packed symmetric kernel's launch.  A single system has
+// B = g0 = P1 = S1 = 0; a batch concatenates the systems' records, each
+// padded to whole home tiles, and gives each its own partial and segment-sum
+// regions, so pairs never cross systems.
+struct SymSys {
+    int64_t B;      // first record (multiple of the home tile)
+    int64_t g0;     // first blob in the caller's concatenated vectors
+    int64_t n;      // blobs
+    int64_t n_pad;  // records (n rounded up to whole home tiles)
+    int64_t P1;     // first float of the visitor/home partials, divided by 3K
+    int64_t S1;     // first double of the segment sums, divided by 3K
+    int T;          // home tiles
+    int chunk;      // visitors per off-diagonal item
+};
+
+// system of global index x, given ascending starts base(s) (binary search)
+template <class F>
+__device__ __forceinline__ int sys_of(int n_sys, int64_t x, F base)
+{
+    int lo = 0, hi = n_sys - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (base(mid) <= x) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) { return static_cast<uint32_t>(__cvta_generic_to_shared(p)); }
 __device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t c)
@@ -379,12 +408,12 @@ __global__ void reduce_kernel(int64_t n, int64_t n_pad, int k, int kt, int n_hom
 // tile one diagonal item (slot 0) and one item per `chunk` visitors after it.
 // The chunk is CHUNK, halved (down to one visitor tile) while the items would
 // not fill 4 CTAs per SM, so small suspensions still spread over the GPU.
-// Cached per n in plan slot `ps` (0: 128-blob tiles, 1: 256-blob tiles).
+// Cached per n (the one-home kernel; the packed kernel's lists are Sym2Plan).
 template <int TILE>
-static int get_items(rpbd_handle* h, int ps, int64_t n, int64_t n_pad, SymItem** d_items, int* n_items, int* n_home,
+static int get_items(rpbd_handle* h, int64_t n, int64_t n_pad, SymItem** d_items, int* n_items, int* n_home,
                      int* max_slots, int* chunk_out)
 {
-    SymPlan& pl = h->sym_plan[ps];
+    SymPlan& pl = h->sym_plan;
     if (pl.n != n) {
         std::vector<SymItem> items;
         const int T = (int)(n_pad / TILE);
@@ -397,19 +426,18 @@ static int get_items(rpbd_handle* h, int ps, int64_t n, int64_t n_pad, SymItem**
         while (chunk > VT && count(chunk) < 4 * (int64_t)h->sm_count) chunk /= 2;
         int ms = 1;
         for (int H = 0; H < T; ++H) {
-            items.push_back(SymItem{H, H * TILE, TILE / VT, 0});
+            items.push_back(SymItem{H, H * TILE, TILE / VT, 0, 0});
             int c = 1;
             for (int64_t v0 = (int64_t)(H + 1) * TILE; v0 < n_pad; v0 += chunk, ++c) {
                 const int64_t v1 = std::min<int64_t>(n_pad, v0 + chunk);
-                items.push_back(SymItem{H, (int)v0, (int)((v1 - v0) / VT), c});
+                items.push_back(SymItem{H, (int)v0, (int)((v1 - v0) / VT), c, 0});
             }
             ms = std::max(ms, c);
         }
         // longest items first so the hardware scheduler fills the tail with short ones
         std::stable_sort(items.begin(), items.end(), [](const SymItem& a, const SymItem& b) { return a.ntile > b.ntile; });
         void* d = nullptr;
-        const Buf b = ps == 0 ? BUF_SYM_ITEMS : BUF_SYM2_ITEMS;
-        RPBD_TRY(ensure(h, b, items.size() * sizeof(SymItem), &d));
+        RPBD_TRY(ensure(h, BUF_SYM_ITEMS, items.size() * sizeof(SymItem), &d));
         RPBD_CU(h, cudaMemcpy(d, items.data(), items.size() * sizeof(SymItem), cudaMemcpyHostToDevice));
         pl.n = n;
         pl.n_items = (int)items.size();
@@ -417,7 +445,7 @@ static int get_items(rpbd_handle* h, int ps, int64_t n, int64_t n_pad, SymItem**
         pl.max_slots = ms;
         pl.chunk = chunk;
     }
-    *d_items = reinterpret_cast<SymItem*>(h->buf[ps == 0 ? BUF_SYM_ITEMS : BUF_SYM2_ITEMS]);
+    *d_items = reinterpret_cast<SymItem*>(h->buf[BUF_SYM_ITEMS]);
     *n_items = pl.n_items;
     *n_home = pl.n_home;
     *max_slots = pl.max_slots;
@@ -433,7 +461,7 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     SymItem* items;
     int n_items, n_home, max_slots;
     int chunk;
-    RPBD_TRY(get_items<HT>(h, 0, n, n_pad, &items, &n_items, &n_home, &max_slots, &chunk));
+    RPBD_TRY(get_items<HT>(h, n, n_pad, &items, &n_items, &n_home, &max_slots, &chunk));
     float* rec;
     double* scale;
     float* partial;
@@ -499,18 +527,25 @@ __host__ __device__ __forceinline__ int64_t rec2_off(int64_t i, int c, int len)
     return (i / VT) * VT * len + ((int64_t)c * VT + (i % VT)) * 4;
 }
 
+// One thread per record of the launch (all systems, padded to whole home
+// tiles); padding records sit far away with zero force.
 template <int K, class In>
-__global__ void pack2_kernel(int64_t n, int64_t n_pad, int k, const double* __restrict__ r, const In* __restrict__ F,
-                             double a, int wall, double s_min, float* __restrict__ rec, double* __restrict__ scale)
+__global__ void pack2_kernel(int n_sys, const SymSys* __restrict__ sys, int64_t rec_end, int64_t n_tot, int k,
+                             const double* __restrict__ r, const In* __restrict__ F, double a, int wall, double s_min,
+                             float* __restrict__ rec, double* __restrict__ scale)
 {
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (i >= n_pad) return;
+    const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (j >= rec_end) return;
     constexpr int NCH = Rec2<K>::NCH, LEN = Rec2<K>::LEN;
+    const int sx = n_sys == 1 ? 0 : sys_of(n_sys, j, [&](int m) { return sys[m].B; });
+    const int64_t l = j - sys[sx].B;
+    const bool real = l < sys[sx].n;
+    const int64_t i = sys[sx].g0 + l;  // the blob's index in the caller's vectors
     double x = 1.0e7, y = 1.0e7, zt = a, s = 0.0;
-    if (i < n) {
+    if (real) {
         x = r[i];
-        y = r[n + i];
-        const double z = r[2 * n + i];
+        y = r[n_tot + i];
+        const double z = r[2 * n_tot + i];
         if (wall) {
             zt = z > a ? z : a;
             const double t = z / a;
@@ -535,13 +570,13 @@ __global__ void pack2_kernel(int64_t n, int64_t n_pad, int k, const double* __re
     v[2] = (float)(x - (double)xh);
     v[3] = (float)(y - (double)yh);
     v[4] = (float)zt;
-    if (i < n)
+    if (real)
         for (int m = 0; m < k; ++m)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[5 + 3 * m + c] = (float)(s * (double)F[((int64_t)m * 3 + c) * n + i]);
+            for (int c = 0; c < 3; ++c) v[5 + 3 * m + c] = (float)(s * (double)F[((int64_t)m * 3 + c) * n_tot + i]);
 #pragma unroll
     for (int c = 0; c < NCH; ++c)
-        *reinterpret_cast<float4*>(rec + rec2_off(i, c, LEN)) = make_float4(v[2 * c], v[2 * c], v[2 * c + 1], v[2 * c + 1]);
+        *reinterpret_cast<float4*>(rec + rec2_off(j, c, LEN)) = make_float4(v[2 * c], v[2 * c], v[2 * c + 1], v[2 * c + 1]);
 }
 
 // record j of a staged tile -> packed operands (both lanes equal); value m
@@ -627,10 +662,15 @@ struct Sym2Var {
     static constexpr int MINB = PER ? (MINB0 > (K == 1 ? 4 : 2) ? (K == 1 ? 4 : 2) : MINB0) : MINB0;
 };
 
-template <int K, bool PER, int UNR, int MINB>
-__global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict__ rec, int64_t n, int64_t n_pad,
-                                                  const SymItem* __restrict__ items, int n_home_tiles, float Lx,
-                                                  float Ly, float* __restrict__ partial, int* __restrict__ err_flag)
+// BATCH: items of several systems (layout per item from sys[], converged
+// systems skipped); otherwise one system of n blobs, n_pad records and
+// n_home_tiles home tiles, given as arguments.
+template <int K, bool PER, int UNR, int MINB, bool BATCH>
+__global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict__ rec, const SymItem* __restrict__ items,
+                                                  int64_t n, int64_t n_pad, int n_home_tiles,
+                                                  const SymSys* __restrict__ sys, const int* __restrict__ active,
+                                                  float Lx, float Ly, float* __restrict__ partial,
+                                                  int* __restrict__ err_flag)
 {
     constexpr int LEN = Rec2<K>::LEN;
     constexpr uint32_t TILE_BYTES = VT * LEN * sizeof(float);
@@ -639,9 +679,14 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
     float* red = reinterpret_cast<float*>(smem_raw + NST * TILE_BYTES);  // [2 buffers][4 warps][VT][3K]
     uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + NST * TILE_BYTES + 2 * 4 * VT * 3 * K * sizeof(float));
     const SymItem it = items[blockIdx.x];
+    if constexpr (BATCH)
+        if (active && !active[it.sys]) return;  // a converged system: nothing in flight yet
+    // a batch's layout is read again where partials are written (cached
+    // loads), so none of it stays live in registers through the pair loop
+    const SymSys* const sd = sys + it.sys;
     const bool diag = it.slot == 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t i0 = (int64_t)it.home * HT2 + warp * 64 + lane, i1 = i0 + 32;  // home blobs (< n_pad)
+    const int64_t i0 = (int64_t)it.home * HT2 + warp * 64 + lane, i1 = i0 + 32;  // home records
     const PairConstX2 pc = PairConstX2::make_unit();
     const float2 m1 = pc.m1;
 
@@ -728,14 +773,18 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
         }
         if (!diag) {
             const float* rb = red + (t & 1) * (4 * VT * 3 * K);
-            const int64_t vbase = (int64_t)it.v0 + (int64_t)t * VT;
+            const int64_t sB = BATCH ? __ldg(&sd->B) : 0, sn = BATCH ? __ldg(&sd->n) : n;
+            const int64_t sn_pad = BATCH ? __ldg(&sd->n_pad) : n_pad;
+            float* const part = BATCH ? partial + (int64_t)3 * K * __ldg(&sd->P1) : partial;  // the system's partials
+            const int64_t hloc = (int64_t)it.home - sB / HT2;  // home tile within the system
+            const int64_t vbase = (int64_t)it.v0 + (int64_t)t * VT - sB;
             for (int e = tid; e < VT * 3 * K; e += HT) {
                 const int vl = e / (3 * K), q = e % (3 * K);
                 const int64_t vg = vbase + vl;
-                if (vg < n) {
+                if (vg < sn) {
                     const float sum = rb[(0 * VT + vl) * 3 * K + q] + rb[(1 * VT + vl) * 3 * K + q] +
                                       rb[(2 * VT + vl) * 3 * K + q] + rb[(3 * VT + vl) * 3 * K + q];
-                    partial[((int64_t)it.home * 3 * K + q) * n_pad + vg] = sum;
+                    part[(hloc * 3 * K + q) * sn_pad + vg] = sum;
                 }
             }
         }
@@ -753,59 +802,261 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
         }
         return;
     }
-    const int slot = n_home_tiles + it.slot;
+    const int64_t sB = BATCH ? __ldg(&sd->B) : 0, sn = BATCH ? __ldg(&sd->n) : n;
+    const int64_t sn_pad = BATCH ? __ldg(&sd->n_pad) : n_pad;
+    float* const part = BATCH ? partial + (int64_t)3 * K * __ldg(&sd->P1) : partial;
+    const int slot = (BATCH ? __ldg(&sd->T) : n_home_tiles) + it.slot;
+    const int64_t l0 = i0 - sB, l1 = i1 - sB;  // the home blobs within the system
 #pragma unroll
     for (int q = 0; q < 3 * K; ++q) {
-        if (i0 < n) partial[((int64_t)slot * 3 * K + q) * n_pad + i0] = acc[q].x;
-        if (i1 < n) partial[((int64_t)slot * 3 * K + q) * n_pad + i1] = acc[q].y;
+        if (l0 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l0] = acc[q].x;
+        if (l1 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l1] = acc[q].y;
     }
 }
 
+// Reductions of the packed kernel's partials, per system of the launch (the
+// same two passes as reduce_visitors_kernel / reduce_kernel): pass 1 sums the
+// visitor partials of home tiles [y SEG, (y+1) SEG) before the blob's tile;
+// pass 2 adds the segments and the blob's home partials, scales and writes U.
+template <int KT>
+__global__ void reduce2_visitors_kernel(int n_sys, const SymSys* __restrict__ sys, int64_t n_tot, int k,
+                                        const int* __restrict__ active, const float* __restrict__ partial,
+                                        double* __restrict__ segsum)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (g >= n_tot) return;
+    const int sx = n_sys == 1 ? 0 : sys_of(n_sys, g, [&](int m) { return sys[m].g0; });
+    if (active && !active[sx]) return;
+    const SymSys d = sys[sx];
+    const int64_t l = g - d.g0;
+    const int h = (int)(l / HT2);
+    const int H0 = blockIdx.y * SEG;
+    const int H1 = (H0 + SEG) < h ? (H0 + SEG) : h;
+    if (H0 >= H1) return;
+    const float* src = partial + (int64_t)3 * KT * d.P1 + l;
+    float s[3 * KT], c[3 * KT];
+#pragma unroll
+    for (int q = 0; q < 3 * KT; ++q) s[q] = c[q] = 0.0f;
+    int H = H0;
+    for (; H + 4 <= H1; H += 4) {
+        float v[4][3 * KT];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < 3 * KT; ++q) v[u][q] = q < 3 * k ? src[((int64_t)(H + u) * 3 * KT + q) * d.n_pad] : 0.0f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int q = 0; q < 3 * KT; ++q) two_sum_acc(s[q], c[q], v[u][q]);
+    }
+    for (; H < H1; ++H)
+#pragma unroll
+        for (int q = 0; q < 3 * KT; ++q)
+            if (q < 3 * k) two_sum_acc(s[q], c[q], src[((int64_t)H * 3 * KT + q) * d.n_pad]);
+    double* dst = segsum + (int64_t)3 * KT * d.S1 + l;
+#pragma unroll
+    for (int q = 0; q < 3 * KT; ++q)
+        if (q < 3 * k) dst[((int64_t)blockIdx.y * 3 * KT + q) * d.n_pad] = two_sum_value(s[q], c[q]);
+}
+
+template <class Out>
+__global__ void reduce2_kernel(int n_sys, const SymSys* __restrict__ sys, int64_t n_tot, int k, int kt,
+                               const int* __restrict__ active, const float* __restrict__ partial,
+                               const double* __restrict__ segsum, const double* __restrict__ scale, double inv8pieta,
+                               Out* __restrict__ U)
+{
+    // one thread per (blob, component q = blockIdx.y < 3k)
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (g >= n_tot || q >= 3 * k) return;
+    const int sx = n_sys == 1 ? 0 : sys_of(n_sys, g, [&](int m) { return sys[m].g0; });
+    if (active && !active[sx]) return;
+    const SymSys d = sys[sx];
+    const int64_t l = g - d.g0;
+    const int h = (int)(l / HT2);
+    const int nseg = (h + SEG - 1) / SEG;
+    const int64_t vis = d.n_pad - (int64_t)(h + 1) * HT2;  // visitors of tile h
+    const int home_slots = 1 + (int)((vis + d.chunk - 1) / d.chunk);
+    const double* sg = segsum + (int64_t)3 * kt * d.S1 + l;
+    const float* pt = partial + (int64_t)3 * kt * d.P1 + l;
+    double sum = 0.0;
+    for (int y = 0; y < nseg; ++y) sum += sg[((int64_t)y * 3 * kt + q) * d.n_pad];
+    float hs = 0.0f, hc = 0.0f;
+    for (int c = 0; c < home_slots; ++c) two_sum_acc(hs, hc, pt[((int64_t)(d.T + c) * 3 * kt + q) * d.n_pad]);
+    sum += two_sum_value(hs, hc);
+    U[(int64_t)q * n_tot + g] = (Out)(scale[g] * inv8pieta * sum);
+}
+
+}  // namespace sym
+
+// Work list of the packed symmetric kernel for one launch (one system, or a
+// batch of systems given by blob offsets), cached per offsets.
+struct Sym2Plan {
+    std::vector<int64_t> off;
+    std::vector<sym::SymSys> sys;
+    sym::SymItem* d_items = nullptr;
+    sym::SymSys* d_sys = nullptr;
+    int n_items = 0;
+    int max_nseg = 1;
+    int64_t rec_end = 0;    // records of the launch
+    int64_t part_rows = 0;  // sum over systems of (T + slots) n_pad: partial floats / (3K)
+    int64_t seg_rows = 0;   // sum over systems of nseg n_pad: segment doubles / (3K)
+};
+
+void free_sym2_plans(rpbd_handle* h)
+{
+    for (Sym2Plan* p : h->sym2_plans) {
+        cudaFree(p->d_items);
+        cudaFree(p->d_sys);
+        delete p;
+    }
+    h->sym2_plans.clear();
+}
+
+namespace sym {
+
+static int get_plan2(rpbd_handle* h, int n_sys, const int64_t* off, Sym2Plan** out)
+{
+    for (Sym2Plan* p : h->sym2_plans)
+        if ((int)p->off.size() == n_sys + 1 && std::equal(p->off.begin(), p->off.end(), off)) {
+            *out = p;
+            return RPBD_OK;
+        }
+    Sym2Plan* p = new Sym2Plan();
+    p->off.assign(off, off + n_sys + 1);
+    // chunk: halved (down to one visitor tile) while the launch would have
+    // fewer than 4 items per SM
+    auto count = [&](int c) {
+        int64_t m = 0;
+        for (int s = 0; s < n_sys; ++s) {
+            const int64_t np_ = (off[s + 1] - off[s] + HT2 - 1) / HT2 * HT2;
+            for (int64_t H = 0; H < np_ / HT2; ++H) m += 1 + (np_ - (H + 1) * HT2 + c - 1) / c;
+        }
+        return m;
+    };
+    int chunk = CHUNK;
+    while (chunk > VT && count(chunk) < 4 * (int64_t)h->sm_count) chunk /= 2;
+    std::vector<SymItem> items;
+    int64_t B = 0, P1 = 0, S1 = 0;
+    for (int s = 0; s < n_sys; ++s) {
+        SymSys d;
+        d.n = off[s + 1] - off[s];
+        d.g0 = off[s];
+        d.n_pad = (d.n + HT2 - 1) / HT2 * HT2;
+        d.B = B;
+        d.T = (int)(d.n_pad / HT2);
+        d.chunk = chunk;
+        d.P1 = P1;
+        d.S1 = S1;
+        const int slots = d.T > 0 ? 1 + (int)((d.n_pad - HT2 + chunk - 1) / chunk) : 0;
+        const int nseg = (d.T + SEG - 1) / SEG;
+        for (int H = 0; H < d.T; ++H) {
+            const int home = (int)(B / HT2) + H;
+            items.push_back(SymItem{home, (int)(B + (int64_t)H * HT2), HT2 / VT, 0, s});
+            int c = 1;
+            for (int64_t v0 = (int64_t)(H + 1) * HT2; v0 < d.n_pad; v0 += chunk, ++c) {
+                const int64_t v1 = std::min<int64_t>(d.n_pad, v0 + chunk);
+                items.push_back(SymItem{home, (int)(B + v0), (int)((v1 - v0) / VT), c, s});
+            }
+        }
+        p->max_nseg = std::max(p->max_nseg, nseg);
+        B += d.n_pad;
+        P1 += (int64_t)(d.T + slots) * d.n_pad;
+        S1 += (int64_t)nseg * d.n_pad;
+        p->sys.push_back(d);
+    }
+    // longest items first so the hardware scheduler fills the tail with short ones
+    std::stable_sort(items.begin(), items.end(), [](const SymItem& a, const SymItem& b) { return a.ntile > b.ntile; });
+    p->n_items = (int)items.size();
+    p->rec_end = B;
+    p->part_rows = P1;
+    p->seg_rows = S1;
+    if (B > ((int64_t)1 << 31) - HT2 || cudaMalloc(&p->d_items, sizeof(SymItem) * std::max<size_t>(1, items.size())) !=
+                                            cudaSuccess ||
+        cudaMalloc(&p->d_sys, sizeof(SymSys) * n_sys) != cudaSuccess ||
+        (!items.empty() &&
+         cudaMemcpy(p->d_items, items.data(), sizeof(SymItem) * items.size(), cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaMemcpy(p->d_sys, p->sys.data(), sizeof(SymSys) * n_sys, cudaMemcpyHostToDevice) != cudaSuccess) {
+        cudaFree(p->d_items);
+        cudaFree(p->d_sys);
+        delete p;
+        return set_error(h, RPBD_NO_MEM, "packed symmetric kernel: work list upload failed");
+    }
+    h->sym2_plans.push_back(p);
+    *out = p;
+    return RPBD_OK;
+}
+
+// the packed symmetric matvec of one system (n_sys = 1) or a batch; PER: the
+// pseudo-periodic cell (single systems only)
 template <int K, bool PER, class In, class Out>
-static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
+static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, const In* F, Out* U, int k,
+                const int* active, Buf b_rec, Buf b_part, Buf b_seg, cudaStream_t st)
 {
     constexpr int LEN = Rec2<K>::LEN;
-    const int64_t n_pad = (n + HT2 - 1) / HT2 * HT2;
-    SymItem* items;
-    int n_items, n_home, max_slots;
-    int chunk;
-    RPBD_TRY(get_items<HT2>(h, 1, n, n_pad, &items, &n_items, &n_home, &max_slots, &chunk));
+    const int64_t n_tot = off[n_sys];
+    if (n_tot <= 0) return RPBD_OK;
+    Sym2Plan* pl = nullptr;
+    RPBD_TRY(get_plan2(h, n_sys, off, &pl));
     float* rec;
     double* scale;
     float* partial;
-    RPBD_TRY(ensure_t(h, BUF_PACK, (size_t)n_pad * LEN, &rec));
-    RPBD_TRY(ensure_t(h, BUF_SCALE, (size_t)n_pad, &scale));
-    RPBD_TRY(ensure_t(h, BUF_PARTIAL, (size_t)(n_home + max_slots) * 3 * K * n_pad, &partial));
-    pack2_kernel<K, In><<<(unsigned)((n_pad + 255) / 256), 256, 0, st>>>(n, n_pad, k, r, F, h->p.a, h->p.wall,
-                                                                         h->p.s_min, rec, scale);
+    double* segsum;
+    RPBD_TRY(ensure_t(h, b_rec, (size_t)pl->rec_end * LEN, &rec));
+    RPBD_TRY(ensure_t(h, n_sys == 1 ? BUF_SCALE : BUF_BSCALE, (size_t)n_tot, &scale));
+    RPBD_TRY(ensure_t(h, b_part, (size_t)pl->part_rows * 3 * K, &partial));
+    RPBD_TRY(ensure_t(h, b_seg, (size_t)std::max<int64_t>(1, pl->seg_rows) * 3 * K, &segsum));
+    pack2_kernel<K, In><<<(unsigned)((pl->rec_end + 255) / 256), 256, 0, st>>>(
+        n_sys, pl->d_sys, pl->rec_end, n_tot, k, r, F, h->p.a, h->p.wall, h->p.s_min, rec, scale);
     count_launch();
     const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 2 * 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
     const float Lxa = (float)(h->p.Lx / h->p.a), Lya = (float)(h->p.Ly / h->p.a);  // periodic cell in units of a
     if (h->profile) prof_begin(h, st);
     const int sv = h->sym_variant[sym_class(K)];
-    switch (sv >= 0 ? sv : (K == 1 ? 2 : 3)) {  // tuning variants (unroll, min CTAs per SM), see Sym2Var;
-                                                 // -1: the measured default per K
-    case 1: sym2_kernel<K, PER, Sym2Var<K, 1, PER>::UNR, Sym2Var<K, 1, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, Lxa, Lya, partial, h->dev_flag); break;
-    case 2: sym2_kernel<K, PER, Sym2Var<K, 2, PER>::UNR, Sym2Var<K, 2, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, Lxa, Lya, partial, h->dev_flag); break;
-    case 3: sym2_kernel<K, PER, Sym2Var<K, 3, PER>::UNR, Sym2Var<K, 3, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, Lxa, Lya, partial, h->dev_flag); break;
-    default: sym2_kernel<K, PER, Sym2Var<K, 0, PER>::UNR, Sym2Var<K, 0, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, Lxa, Lya, partial, h->dev_flag); break;
+    const SymItem* items = pl->d_items;
+    const SymSys* sys = pl->d_sys;
+    const int ni = pl->n_items;
+    const int64_t n1 = pl->sys[0].n, np1 = pl->sys[0].n_pad;
+    const int T1 = pl->sys[0].T;
+    const int var = sv >= 0 ? sv : (K == 1 ? 2 : 3);  // tuning variants (unroll, min CTAs per SM), see
+                                                       // Sym2Var; -1: the measured default per K
+    if (n_sys > 1) {  // batches: the default variant
+        if constexpr (!PER)
+            sym2_kernel<K, false, Sym2Var<K, K == 1 ? 2 : 3>::UNR, Sym2Var<K, K == 1 ? 2 : 3>::MINB, true>
+                <<<ni, HT, smem, st>>>(rec, items, 0, 0, 0, sys, active, Lxa, Lya, partial, h->dev_flag);
+        else
+            return set_error(h, RPBD_BAD_ARG, "packed symmetric kernel: batches are open in x, y");
+    } else {
+        switch (var) {
+        case 1: sym2_kernel<K, PER, Sym2Var<K, 1, PER>::UNR, Sym2Var<K, 1, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag); break;
+        case 2: sym2_kernel<K, PER, Sym2Var<K, 2, PER>::UNR, Sym2Var<K, 2, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag); break;
+        case 3: sym2_kernel<K, PER, Sym2Var<K, 3, PER>::UNR, Sym2Var<K, 3, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag); break;
+        default: sym2_kernel<K, PER, Sym2Var<K, 0, PER>::UNR, Sym2Var<K, 0, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag); break;
+        }
     }
     count_launch();
-    if (h->profile) prof_end(h, st, PER ? 3 : 4 /* symmetric (images) or symmetric factored */, K,
-                             (double)n * (double)n);
+    if (h->profile) {
+        double pairs = 0.0;
+        for (int s = 0; s < n_sys; ++s) pairs += (double)(off[s + 1] - off[s]) * (double)(off[s + 1] - off[s]);
+        prof_end(h, st, n_sys > 1 ? 2 /* batched */ : (PER ? 3 : 4) /* symmetric (images) or factored */, K, pairs);
+    }
     // blocks were formed in units of a: M = M(a = 1) / a
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta * h->p.a);
-    const int nseg = (n_home + SEG - 1) / SEG;
-    double* segsum;
-    RPBD_TRY(ensure_t(h, BUF_SYM_SEG, (size_t)nseg * 3 * K * n_pad, &segsum));
-    reduce_visitors_kernel<HT2, K, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)nseg), 256, 0, st>>>(
-        n, n_pad, k, partial, segsum);
+    reduce2_visitors_kernel<K><<<dim3((unsigned)((n_tot + 255) / 256), (unsigned)pl->max_nseg), 256, 0, st>>>(
+        n_sys, sys, n_tot, k, active, partial, segsum);
     count_launch();
-    reduce_kernel<HT2, float, Out><<<dim3((unsigned)((n + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(n, n_pad, k, K, n_home, chunk,
-                                                                                partial, segsum, scale, inv8pieta, U);
+    reduce2_kernel<Out><<<dim3((unsigned)((n_tot + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(
+        n_sys, sys, n_tot, k, K, active, partial, segsum, scale, inv8pieta, U);
     count_launch();
     RPBD_LAUNCH_CHECK(h);
     return RPBD_OK;
+}
+
+template <int K, bool PER, class In, class Out>
+static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
+{
+    const int64_t off[2] = {0, n};
+    return run2<K, PER>(h, 1, off, r, F, U, k, nullptr, BUF_PACK, BUF_PARTIAL, BUF_SYM_SEG, st);
 }
 
 }  // namespace sym
@@ -832,6 +1083,24 @@ int sym_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* F, vo
 {
     if (io_double) return sym_dispatch(h, n, r, (const double*)F, (double*)U, k, st);
     return sym_dispatch(h, n, r, (const float*)F, (float*)U, k, st);
+}
+
+template <class In, class Out>
+static int sym_batched_dispatch(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, const In* F, Out* U,
+                                int k, const int* active, cudaStream_t st)
+{
+    if (k <= 1) return sym::run2<1, false>(h, n_sys, off, r, F, U, k, active, BUF_BPACK, BUF_BPARTIAL, BUF_BSEG, st);
+    if (k <= 2) return sym::run2<2, false>(h, n_sys, off, r, F, U, k, active, BUF_BPACK, BUF_BPARTIAL, BUF_BSEG, st);
+    return sym::run2<4, false>(h, n_sys, off, r, F, U, k, active, BUF_BPACK, BUF_BPARTIAL, BUF_BSEG, st);
+}
+
+int sym_batched_apply_impl(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, const void* F, void* U,
+                           int k, bool io_double, const int* active, cudaStream_t st)
+{
+    if (!h->p.wall || h->p.Lx > 0.0 || k < 1 || k > 4)
+        return set_error(h, RPBD_BAD_ARG, "batched symmetric variant: wall, open cell, 1 <= k <= 4");
+    if (io_double) return sym_batched_dispatch(h, n_sys, off, r, (const double*)F, (double*)U, k, active, st);
+    return sym_batched_dispatch(h, n_sys, off, r, (const float*)F, (float*)U, k, active, st);
 }
 
 }  // namespace rpbd

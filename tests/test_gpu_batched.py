@@ -22,11 +22,12 @@ def batch(counts, seed=0, box_per_body=2.5):
     return systems, rs, off, r
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
-@pytest.mark.parametrize("k", [1, 3, 16])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4])
+@pytest.mark.parametrize("k", [1, 2, 3, 16])
 def test_batched_matvec_matches_oracle_per_system(k, variant):
-    """every tile variant (3: two targets per thread, packed FP32), systems of
-    1 to 600 blobs (ragged against the 256-target packed tile)"""
+    """every tile variant (3: two targets per thread, packed FP32; 4: the packed
+    symmetric kernel per system, k > 4 on variant 3), systems of 1 to 600
+    blobs (ragged against the 256-blob home tile and the 256-target tile)"""
     systems, rs, off, r = batch([1, 2, 9, 40, 3])
     h = handle_for(systems[0])
     h.set_batch_variant(variant)
@@ -48,7 +49,7 @@ def test_autotune_and_variants_agree():
     F = to_dev(Fh, torch.float32)
     U0 = h.mobility_apply_batched(off, rd, F).cpu().numpy()
     v, ms = h.autotune_batched(off, rd, 1)
-    assert 0 <= v < 4 and ms > 0
+    assert 0 <= v <= 4 and ms > 0
     U1 = h.mobility_apply_batched(off, rd, F).cpu().numpy()
     assert rel2(U1, U0) <= 5e-6
     for s, (sy, rr) in enumerate(zip(systems, rs)):
@@ -57,11 +58,14 @@ def test_autotune_and_variants_agree():
         assert rel2(U0[:, :, sl], ref) <= 1e-5 and rel2(U1[:, :, sl], ref) <= 1e-5
 
 
+@pytest.mark.parametrize("variant", [-1, 4])
 @pytest.mark.parametrize("use_graph", [False, True])
-def test_batched_lanczos_matches_oracle(use_graph):
+def test_batched_lanczos_matches_oracle(use_graph, variant):
+    """default tile and the symmetric variant, eager and graph-replayed"""
     counts = [3, 11, 25, 6]
     systems, rs, off, r = batch(counts, seed=2)
     h = handle_for(systems[0])
+    h.set_batch_variant(variant)
     rd = to_dev(r)
     # block preconditioner over all bodies of the batch (bodies never couple systems)
     q = np.concatenate([s.q for s in systems])
