@@ -242,14 +242,6 @@ __global__ void lanczos_sqrt_kernel(int m1, const double* __restrict__ alpha, co
 // ---------------------------------------------------------------------------
 // host helpers
 
-static int read_scalar(rpbd_handle* h, const double* dev, double* out, cudaStream_t st)
-{
-    RPBD_CU(h, cudaMemcpyAsync(h->host_small, dev, sizeof(double), cudaMemcpyDeviceToHost, st));
-    RPBD_CU(h, cudaStreamSynchronize(st));
-    *out = h->host_small[0];
-    return RPBD_OK;
-}
-
 static int check_flag(rpbd_handle* h, cudaStream_t st)
 {
     int flag = 0;
