@@ -38,8 +38,8 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/pair_kernel_f32_k16_boomerangs_65535.md, profiles/sym_kernel_f32_k*_boomerangs_65535.md);
 # None when not captured
-NCU_TRAFFIC = {"f32_k16": 22067968 + 343998464, "f32symf_k1": 4349440 + 54785536,
-               "f32symf_k2": 7982336 + 168043520}
+NCU_TRAFFIC = {"f32_k16": 22067968 + 343998464, "f32symf_k1": 4396544 + 55015168,
+               "f32symf_k2": 8520192 + 168441600}
 # FMA-pipe activity (sm__pipe_fma_cycles_active) from the same captures
 NCU_FMA_PIPE = {"f32_k16": 0.781, "f32symf_k1": 0.761, "f32symf_k2": 0.731}
 
