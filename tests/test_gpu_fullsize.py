@@ -1,0 +1,81 @@
+"""Full-size parity in the launch configurations the bench times: the
+196,608-blob roller suspension (symmetric kernels at k = 1, 2, row-sampled),
+and the 64-system uneven boomerang batch (471,495 blobs: the batched matvec
+of the symmetric and the one-direction variants on sampled rows of every
+system, and the graph-captured batched Lanczos over the whole batch checked
+against the oracle's Lanczos on its smallest systems)."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import krylov, mobility as om, precond, rigid
+from paper_1709_02410_gb300 import synth
+
+from gpu_util import DEV, handle_for, oracle_params, rel2, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_rollers_196608_row_sampled(k):
+    s = synth.c3_rollers_196608()
+    r = rigid.blob_positions(s.q, s.theta, s.shape)
+    F = synth.gaussian(80 + k, (k, 3, s.n), np.float32)
+    h = handle_for(s)
+    U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    h.close()
+    rows = np.random.default_rng(81).choice(s.n, 32, replace=False)
+    rows[0], rows[1] = 0, s.n - 1
+    Uo = om.apply(r, F.astype(np.float64), oracle_params(s), rows=rows)
+    assert rel2(U[:, :, rows], Uo) <= 1e-5
+
+
+def _batch():
+    systems = synth.c4_uneven_batch()
+    rs = [rigid.blob_positions(sy.q, sy.theta, sy.shape) for sy in systems]
+    off = np.concatenate([[0], np.cumsum([x.shape[1] for x in rs])]).astype(np.int64)
+    return systems, rs, off, np.concatenate(rs, axis=1)
+
+
+@pytest.mark.parametrize("variant", [3, 4])
+def test_uneven_batch_471495_matvec_sampled(variant):
+    systems, rs, off, r = _batch()
+    assert off[-1] == 471495
+    h = handle_for(systems[0])
+    h.set_batch_variant(variant)
+    F = synth.gaussian(82, (1, 3, r.shape[1]), np.float32)
+    U = h.mobility_apply_batched(off, to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    h.close()
+    rng = np.random.default_rng(83)
+    for s, (sy, rr) in enumerate(zip(systems, rs)):
+        n = rr.shape[1]
+        rows = rng.choice(n, min(n, 4), replace=False)
+        rows[0] = n - 1
+        Fs = F[:, :, off[s]:off[s + 1]].astype(np.float64)
+        Uo = om.apply(rr, Fs, oracle_params(sy), rows=rows)
+        assert rel2(U[:, :, off[s] + rows], Uo) <= 1e-5, s
+
+
+def test_uneven_batch_471495_lanczos_graph():
+    systems, rs, off, r = _batch()
+    h = handle_for(systems[0])
+    rd = to_dev(r)
+    q = np.concatenate([sy.q for sy in systems])
+    h.precond_build(15, rd, to_dev(q))
+    W = synth.gaussian(84, (3, r.shape[1]))
+    F = synth.gaussian(85, (3, r.shape[1]))
+    out, U, iters = h.lanczos_sqrt_apply_batched(off, rd, to_dev(W), tol=1e-4, max_iter=60, use_graph=True,
+                                                 F=to_dev(F))
+    out, U = out.cpu().numpy(), U.cpu().numpy()
+    h.close()
+    assert all(1 <= it <= 60 for it in iters)
+    for s in np.argsort([rr.shape[1] for rr in rs])[:3]:  # the three smallest systems
+        sy, rr = systems[s], rs[s]
+        sl = slice(off[s], off[s + 1])
+        prm = oracle_params(sy)
+        pc = precond.BlockPrecond(rr, sy.q, sy.nper, prm)
+        G = lambda v: pc.Linv_apply(om.apply(rr, pc.LinvT_apply(v), prm))
+        y, it, _ = krylov.lanczos_sqrt(G, W[:, sl], 1e-4, 60)
+        assert abs(iters[s] - it) <= 1
+        assert rel2(out[:, sl], pc.L_apply(y)) <= 1e-3
+        assert rel2(U[:, sl], om.apply(rr, F[:, sl], prm)) <= 1e-5
