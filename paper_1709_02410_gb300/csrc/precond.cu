@@ -211,22 +211,37 @@ __global__ void __launch_bounds__(PREC_THREADS) prec_apply_kernel(int mode, int 
         v[e] = x[c * n + p * nper + b];
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    // row i's sum over its column range [j0, j1) split into `parts` pieces
+    // over the CTA's threads, then added in order
+    double* part = v + m;  // parts * span
+    const int span = (m + 31) & ~31, parts = PREC_THREADS / span;
+    const int q = threadIdx.x / span, i = threadIdx.x % span;
+    if (q < parts && i < m) {
+        const int j0 = mode == 2 ? i : 0, j1 = mode == 2 || mode == 3 ? m : i + 1;
+        const int per = (j1 - j0 + parts - 1) / parts;
+        const int a0 = j0 + q * per, a1 = a0 + per < j1 ? a0 + per : j1;
         double acc = 0.0;
-        if (mode == 2) {  // (L^-1)^T: sum_j Linv(j, i) v_j, j >= i
-            for (int j = i; j < m; ++j) acc += A[i * m + j] * v[j];
-        } else if (mode == 3) {
-            for (int j = 0; j < m; ++j) acc += A[j * m + i] * v[j];
-        } else {  // lower triangular: j <= i
-            for (int j = 0; j <= i; ++j) acc += A[j * m + i] * v[j];
-        }
-        const int b = i / 3, c = i % 3;
+        if (mode == 2)  // (L^-1)^T: sum_j Linv(j, i) v_j, j >= i
+            for (int j = a0; j < a1; ++j) acc += A[i * m + j] * v[j];
+        else            // M^-1, or lower triangular (j <= i)
+            for (int j = a0; j < a1; ++j) acc += A[j * m + i] * v[j];
+        part[q * span + i] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        double acc = part[threadIdx.x];
+        for (int q2 = 1; q2 < parts; ++q2) acc += part[q2 * span + threadIdx.x];
+        const int b = threadIdx.x / 3, c = threadIdx.x % 3;
         out[c * n + p * nper + b] = acc;
     }
 }
 
 // exact body-block saddle solve: [M(pp) -K_p; -K_p^T 0][lam; U] = [a; b]
 //   t = (M^-1 K)^T a + b,  U = -N t,  lam = M^-1 a + (M^-1 K) U
+// One CTA per body.  M^-1 and M^-1 K are read straight from global memory
+// (each entry once, coalesced along the row index); the six dot products of
+// t use one warp each with a shuffle reduction, and the m-row product is split
+// into column halves over the CTA's threads, then added.
 __global__ void __launch_bounds__(PREC_THREADS) prec_saddle_kernel(int nper, int64_t n, const double* __restrict__ Minv,
                                                                    const double* __restrict__ MinvK,
                                                                    const double* __restrict__ N,
@@ -237,38 +252,50 @@ __global__ void __launch_bounds__(PREC_THREADS) prec_saddle_kernel(int nper, int
     extern __shared__ double sm[];
     const int m = 3 * nper;
     const int64_t p = blockIdx.x;
-    double* A = sm;           // m*m
-    double* MK = A + m * m;   // 6m
-    double* va = MK + 6 * m;  // m
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    constexpr int NW = PREC_THREADS / 32;
+    const int span = (m + 31) & ~31;           // threads per column part
+    const int parts = PREC_THREADS / span;     // >= 1 since m <= PREC_MAX_M <= PREC_THREADS
+    double* va = sm;                           // m
+    double* part = va + m;                     // parts * span
     __shared__ double t6[6], u6[6];
-    const double* src = Minv + p * m * m;
-    for (int e = threadIdx.x; e < m * m; e += blockDim.x) A[e] = src[e];
-    for (int e = threadIdx.x; e < 6 * m; e += blockDim.x) MK[e] = MinvK[p * 6 * m + e];
-    for (int e = threadIdx.x; e < m; e += blockDim.x) {
+    const double* A = Minv + p * m * m;        // column-major: (i, j) at j * m + i
+    const double* MK = MinvK + p * 6 * m;      // (M^-1 K)^T rows: column c at c * m
+    for (int e = tid; e < m; e += PREC_THREADS) {
         const int bb = e / 3, c = e % 3;
         va[e] = a ? a[c * n + p * nper + bb] : 0.0;
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
-        const int e = threadIdx.x;
-        double v = b ? b[6 * p + e] : 0.0;
-        for (int k = 0; k < m; ++k) v += MK[e * m + k] * va[k];
-        t6[e] = v;
+    for (int e = warp; e < 6; e += NW) {
+        double v = 0.0;
+        for (int k = lane; k < m; k += 32) v += MK[e * m + k] * va[k];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if (lane == 0) t6[e] = v + (b ? b[6 * p + e] : 0.0);
     }
     __syncthreads();
-    if (threadIdx.x < 6) {
-        const int e = threadIdx.x;
+    if (tid < 6) {
         double v = 0.0;
-        for (int c = 0; c < 6; ++c) v -= N[p * 36 + c * 6 + e] * t6[c];
-        u6[e] = v;
-        U[6 * p + e] = v;
+        for (int c = 0; c < 6; ++c) v -= N[p * 36 + c * 6 + tid] * t6[c];
+        u6[tid] = v;
+        U[6 * p + tid] = v;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < m; i += blockDim.x) {
+    const int q = tid / span, i = tid % span;
+    if (q < parts && i < m) {
+        const int per = (m + parts - 1) / parts;
+        const int j0 = q * per, j1 = j0 + per < m ? j0 + per : m;
         double v = 0.0;
-        for (int j = 0; j < m; ++j) v += A[j * m + i] * va[j];
-        for (int c = 0; c < 6; ++c) v += MK[c * m + i] * u6[c];
-        const int bb = i / 3, c = i % 3;
+        for (int j = j0; j < j1; ++j) v += A[j * m + i] * va[j];
+        if (q == 0)
+            for (int c = 0; c < 6; ++c) v += MK[c * m + i] * u6[c];
+        part[q * span + i] = v;
+    }
+    __syncthreads();
+    if (tid < m) {
+        double v = part[tid];
+        for (int q2 = 1; q2 < parts; ++q2) v += part[q2 * span + tid];
+        const int bb = tid / 3, c = tid % 3;
         lam[c * n + p * nper + bb] = v;
     }
 }
@@ -325,7 +352,7 @@ int precond_apply_impl(rpbd_handle* h, int mode, const double* x, double* out, c
     const double* Mat = mode == 0 ? (const double*)h->buf[BUF_PREC_L]
                         : mode == 3 ? (const double*)h->buf[BUF_PREC_MINV]
                                     : (const double*)h->buf[BUF_PREC_LINV];
-    const size_t smem = (size_t)(m * m + m) * sizeof(double);
+    const size_t smem = (size_t)(m * m + m + PREC_THREADS) * sizeof(double);
     prec_apply_kernel<<<(unsigned)h->prec_nb, PREC_THREADS, smem, st>>>(mode, h->prec_nper,
                                                                         h->prec_nb * h->prec_nper, Mat, x, out); count_launch();
     RPBD_LAUNCH_CHECK(h);
@@ -336,7 +363,7 @@ int precond_saddle_impl(rpbd_handle* h, const double* a, const double* b, double
 {
     if (!h->prec_valid) return set_error(h, RPBD_BAD_ARG, "preconditioner not built");
     const int m = 3 * h->prec_nper;
-    const size_t smem = (size_t)(m * m + 7 * m) * sizeof(double);
+    const size_t smem = (size_t)(m + PREC_THREADS) * sizeof(double);
     prec_saddle_kernel<<<(unsigned)h->prec_nb, PREC_THREADS, smem, st>>>(
         h->prec_nper, h->prec_nb * h->prec_nper, (const double*)h->buf[BUF_PREC_MINV],
         (const double*)h->buf[BUF_PREC_MINVK], (const double*)h->buf[BUF_PREC_N], a, b, lam, U); count_launch();
