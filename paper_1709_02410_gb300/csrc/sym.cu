@@ -19,9 +19,12 @@
 //    tile, visitor); home sums are stored per chunk;
 //  * pairs inside a home tile (and the self block) are done by a diagonal
 //    item in the plain one-direction form.
-// A reduce kernel adds, for blob i, the visitor partials of every home tile
+// Two reduce kernels add, for blob i, the visitor partials of every home tile
 // before i's tile and the home partials of i's own tile in a fixed order
-// (FP64, deterministic), then applies s_i / (8 pi eta).
+// (compensated FP32 pairs widened to FP64; deterministic), then apply
+// s_i / (8 pi eta).  The packed variant below (two homes per thread) also
+// runs over a batch of independent systems: each system padded to whole home
+// tiles, with its own partial and segment-sum regions (SymSys).
 #include <cuda_runtime.h>
 
 #include <algorithm>
