@@ -228,9 +228,9 @@ static int blz_body(rpbd_handle* h, int n_sys, const int64_t* off, int64_t n, co
     for (int m = 0; m < max_iter; ++m) {
         const double* vm = B.V + (int64_t)m * len;
         if (use_precond) {
-            RPBD_TRY(precond_apply_impl(h, 2, vm, B.z, st));
+            RPBD_TRY(precond_apply_impl(h, 2, vm, B.z, st, B.active, B.doff, n_sys));
             RPBD_TRY(batched_apply_impl(h, n_sys, off, B.rin, B.z, B.y, 1, true, B.active, st));
-            RPBD_TRY(precond_apply_impl(h, 1, B.y, B.w, st));
+            RPBD_TRY(precond_apply_impl(h, 1, B.y, B.w, st, B.active, B.doff, n_sys));
         } else {
             RPBD_TRY(batched_apply_impl(h, n_sys, off, B.rin, vm, B.w, 1, true, B.active, st));
         }

@@ -194,14 +194,28 @@ __global__ void __launch_bounds__(PREC_THREADS) prec_build_kernel(int nper, int6
 }
 
 // out = A_p x_p per body, A_p one of the stored factors.
-// mode 0: L (lower), 1: L^-1 (lower), 2: L^-T, 3: M^-1
+// mode 0: L (lower), 1: L^-1 (lower), 2: L^-T, 3: M^-1.  With `active`
+// (batches: systems at blob offsets off[0..n_sys]), bodies of inactive
+// systems are skipped and their out left as it is.
 __global__ void __launch_bounds__(PREC_THREADS) prec_apply_kernel(int mode, int nper, int64_t n,
                                                                   const double* __restrict__ Mat,
-                                                                  const double* __restrict__ x, double* __restrict__ out)
+                                                                  const double* __restrict__ x, double* __restrict__ out,
+                                                                  const int* __restrict__ active,
+                                                                  const int64_t* __restrict__ off, int n_sys)
 {
     extern __shared__ double sm[];
     const int m = 3 * nper;
     const int64_t p = blockIdx.x;
+    if (active) {
+        const int64_t i = p * nper;  // the body's first blob; bodies never straddle systems
+        int lo = 0, hi = n_sys;
+        while (hi - lo > 1) {
+            const int mid = (lo + hi) >> 1;
+            if (off[mid] <= i) lo = mid;
+            else hi = mid;
+        }
+        if (!active[lo]) return;
+    }
     double* A = sm;
     double* v = sm + m * m;
     const double* src = Mat + p * m * m;
@@ -344,7 +358,8 @@ int precond_build_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, co
     return RPBD_OK;
 }
 
-int precond_apply_impl(rpbd_handle* h, int mode, const double* x, double* out, cudaStream_t st)
+int precond_apply_impl(rpbd_handle* h, int mode, const double* x, double* out, cudaStream_t st, const int* active,
+                       const int64_t* off, int n_sys)
 {
     if (!h->prec_valid) return set_error(h, RPBD_BAD_ARG, "preconditioner not built");
     if (mode < 0 || mode > 3 || !x || !out) return set_error(h, RPBD_BAD_ARG, "precond_apply: bad arguments");
@@ -353,8 +368,9 @@ int precond_apply_impl(rpbd_handle* h, int mode, const double* x, double* out, c
                         : mode == 3 ? (const double*)h->buf[BUF_PREC_MINV]
                                     : (const double*)h->buf[BUF_PREC_LINV];
     const size_t smem = (size_t)(m * m + m + PREC_THREADS) * sizeof(double);
-    prec_apply_kernel<<<(unsigned)h->prec_nb, PREC_THREADS, smem, st>>>(mode, h->prec_nper,
-                                                                        h->prec_nb * h->prec_nper, Mat, x, out); count_launch();
+    prec_apply_kernel<<<(unsigned)h->prec_nb, PREC_THREADS, smem, st>>>(
+        mode, h->prec_nper, h->prec_nb * h->prec_nper, Mat, x, out, active, off, n_sys);
+    count_launch();
     RPBD_LAUNCH_CHECK(h);
     return RPBD_OK;
 }

@@ -172,7 +172,10 @@ void launch_axpby(int64_t n, double a, const double* x, double b, const double* 
 void launch_scale_copy(int64_t n, double a, const double* x, double* out, cudaStream_t st);
 int check_finite(rpbd_handle* h, int64_t n, const double* x, cudaStream_t st);
 
-int precond_apply_impl(rpbd_handle* h, int mode, const double* x, double* out, cudaStream_t st);
+// active != nullptr (batches): bodies of systems with active[s] == 0 skipped,
+// systems at device blob offsets off[0..n_sys]
+int precond_apply_impl(rpbd_handle* h, int mode, const double* x, double* out, cudaStream_t st,
+                       const int* active = nullptr, const int64_t* off = nullptr, int n_sys = 0);
 // saddle block solve: (lam, U) = P^-1 (a, b)
 int precond_saddle_impl(rpbd_handle* h, const double* a, const double* b, double* lam,
                         double* U, cudaStream_t st);

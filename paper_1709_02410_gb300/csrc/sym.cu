@@ -535,12 +535,13 @@ __host__ __device__ __forceinline__ int64_t rec2_off(int64_t i, int c, int len)
 template <int K, class In>
 __global__ void pack2_kernel(int n_sys, const SymSys* __restrict__ sys, int64_t rec_end, int64_t n_tot, int k,
                              const double* __restrict__ r, const In* __restrict__ F, double a, int wall, double s_min,
-                             float* __restrict__ rec, double* __restrict__ scale)
+                             const int* __restrict__ active, float* __restrict__ rec, double* __restrict__ scale)
 {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= rec_end) return;
     constexpr int NCH = Rec2<K>::NCH, LEN = Rec2<K>::LEN;
     const int sx = n_sys == 1 ? 0 : sys_of(n_sys, j, [&](int m) { return sys[m].B; });
+    if (active && !active[sx]) return;  // a converged system of a batch: its records are not read
     const int64_t l = j - sys[sx].B;
     const bool real = l < sys[sx].n;
     const int64_t i = sys[sx].g0 + l;  // the blob's index in the caller's vectors
@@ -1010,7 +1011,7 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     RPBD_TRY(ensure_t(h, b_part, (size_t)pl->part_rows * 3 * K, &partial));
     RPBD_TRY(ensure_t(h, b_seg, (size_t)std::max<int64_t>(1, pl->seg_rows) * 3 * K, &segsum));
     pack2_kernel<K, In><<<(unsigned)((pl->rec_end + 255) / 256), 256, 0, st>>>(
-        n_sys, pl->d_sys, pl->rec_end, n_tot, k, r, F, h->p.a, h->p.wall, h->p.s_min, rec, scale);
+        n_sys, pl->d_sys, pl->rec_end, n_tot, k, r, F, h->p.a, h->p.wall, h->p.s_min, active, rec, scale);
     count_launch();
     const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 2 * 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
     const float Lxa = (float)(h->p.Lx / h->p.a), Lya = (float)(h->p.Ly / h->p.a);  // periodic cell in units of a
