@@ -1022,11 +1022,11 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     const int ni = pl->n_items;
     const int64_t n1 = pl->sys[0].n, np1 = pl->sys[0].n_pad;
     const int T1 = pl->sys[0].T;
-    const int var = sv >= 0 ? sv : (K == 1 ? 2 : 3);  // tuning variants (unroll, min CTAs per SM), see
-                                                       // Sym2Var; -1: the measured default per K
+    const int var = sv >= 0 ? sv : 2;  // tuning variants (unroll, min CTAs per SM), see Sym2Var; -1: variant 2,
+                                       // the one the autotuner picks for k = 1 and 2 at 65,535 blobs
     if (n_sys > 1) {  // batches: the default variant
         if constexpr (!PER)
-            sym2_kernel<K, false, Sym2Var<K, K == 1 ? 2 : 3>::UNR, Sym2Var<K, K == 1 ? 2 : 3>::MINB, true>
+            sym2_kernel<K, false, Sym2Var<K, 2>::UNR, Sym2Var<K, 2>::MINB, true>
                 <<<ni, HT, smem, st>>>(rec, items, 0, 0, 0, sys, active, Lxa, Lya, partial, h->dev_flag);
         else
             return set_error(h, RPBD_BAD_ARG, "packed symmetric kernel: batches are open in x, y");
