@@ -50,6 +50,7 @@ class Handle:
         self.h = h
 
     def close(self):
+        """Destroy the handle and free its device workspace (idempotent)."""
         if getattr(self, "h", None):
             self.lib.rpbd_destroy(self.h)
             self.h = None
@@ -80,6 +81,7 @@ class Handle:
         self._check(self.lib.rpbd_set_option(self.h, 1, int(bool(on))), "set_option")
 
     def set_sym_variant(self, v: int):
+        """Loop-unroll / occupancy variant 0..3 of the symmetric kernels (-1: the default)."""
         self._check(self.lib.rpbd_set_option(self.h, 2, int(v)), "set_option")
 
     def measure_fma_peak(self, dtype=F32):
@@ -98,6 +100,7 @@ class Handle:
 
     # ---- a1
     def blobs_from_bodies(self, shape, q, theta, out=None):
+        """Blob positions r = q_p + R(theta_p) s_i (Sec. 2.1) as [3, nb * nper] FP64 SoA."""
         nb, nper = q.shape[0], shape.shape[0]
         out = torch.empty((3, nb * nper), dtype=torch.float64, device=q.device) if out is None else out
         for t, n in ((shape, "shape"), (q, "q"), (theta, "theta")):
@@ -136,6 +139,7 @@ class Handle:
         return out
 
     def mobility_divergence(self, r, out=None):
+        """div M (the thermal drift that the RFD of Sec. 3 estimates), exact, FP64, [3, n]."""
         n = r.shape[1]
         out = torch.empty((3, n), dtype=torch.float64, device=r.device) if out is None else out
         self._check(self.lib.rpbd_mobility_divergence(self.h, n, _ptr(r), _ptr(out), _stream()),
@@ -144,6 +148,7 @@ class Handle:
 
     # ---- rigid
     def K_apply(self, nper, r, q, U, out=None):
+        """Blob velocities K U of rigid-body motions U [nb, 6] (Sec. 2.1), [3, n]."""
         nb = q.shape[0]
         out = torch.empty((3, nb * nper), dtype=torch.float64, device=r.device) if out is None else out
         self._check(self.lib.rpbd_K_apply(self.h, nb, nper, _ptr(r), _ptr(q), _ptr(U), _ptr(out), _stream()),
@@ -151,6 +156,7 @@ class Handle:
         return out
 
     def KT_apply(self, nper, r, q, lam, out=None):
+        """Total force and torque K^T lambda per body of blob forces lambda [3, n], [nb, 6]."""
         nb = q.shape[0]
         out = torch.empty((nb, 6), dtype=torch.float64, device=r.device) if out is None else out
         self._check(self.lib.rpbd_KT_apply(self.h, nb, nper, _ptr(r), _ptr(q), _ptr(lam), _ptr(out), _stream()),
@@ -159,16 +165,20 @@ class Handle:
 
     # ---- a3
     def precond_build(self, nper, r, q):
+        """Build the body-block-diagonal preconditioner (Sec. 2.2) at r; kept until the next build."""
         self._check(self.lib.rpbd_precond_build(self.h, q.shape[0], nper, _ptr(r), _ptr(q), _stream()),
                     "precond_build")
 
     def precond_apply(self, mode, x, out=None):
+        """Apply a stored factor per body: mode 0 L, 1 L^-1, 2 L^-T, 3 M~^-1."""
         out = torch.empty_like(x) if out is None else out
         self._check(self.lib.rpbd_precond_apply(self.h, mode, _ptr(x), _ptr(out), _stream()), "precond_apply")
         return out
 
     # ---- a4
     def lanczos_sqrt_apply(self, r, W, tol, max_iter=80, dtype=F64, use_precond=True, out=None):
+        """M^{1/2} W by preconditioned Lanczos (Sec. 2.2); returns (out, stats).  A run that stops
+        at max_iter returns its last iterate with stats status -4 (not converged)."""
         n = r.shape[1]
         out = torch.empty_like(W) if out is None else out
         st = Stats()
@@ -236,6 +246,7 @@ class Handle:
 
     # ---- a6
     def rfd_drift(self, r, W, delta, dtype=F64, out=None):
+        """Blob-level centred RFD (Sec. 3): [M(r + delta/2 W) - M(r - delta/2 W)] W / delta; mean div M."""
         n = r.shape[1]
         out = torch.empty_like(W) if out is None else out
         self._check(self.lib.rpbd_rfd_drift(self.h, n, _ptr(r), _ptr(W), delta, _ptr(out), dtype, _stream()),
@@ -250,6 +261,7 @@ class Handle:
         return off, off.ctypes.data_as(C.c_void_p)
 
     def mobility_apply_batched(self, offsets, r, F, out=None):
+        """U = M(r_s) F_s for independent systems concatenated at blob offsets (FP32 [k, 3, n])."""
         off, op = self._offsets(offsets)
         n_sys = off.size - 1
         k = 1 if F.dim() == 2 else F.shape[0]
@@ -260,6 +272,7 @@ class Handle:
         return out
 
     def autotune_batched(self, offsets, r, k=1):
+        """Time the batched variants on this batch and keep the fastest; returns (variant, ms)."""
         off, op = self._offsets(offsets)
         ms = C.c_double()
         v = self.lib.rpbd_autotune_batched(self.h, off.size - 1, op, _ptr(r), k, C.byref(ms), _stream())
@@ -269,6 +282,8 @@ class Handle:
 
     def lanczos_sqrt_apply_batched(self, offsets, r, W, tol, max_iter=40, use_precond=True, use_graph=True,
                                    F=None, out=None, U=None):
+        """One preconditioned Lanczos M^{1/2} W per system of a batch, in lockstep (one CUDA graph when
+        use_graph), and optionally U = M F per system; returns (out, U, iterations per system)."""
         off, op = self._offsets(offsets)
         n_sys = off.size - 1
         out = torch.empty_like(W) if out is None else out
@@ -283,6 +298,7 @@ class Handle:
 
     # ---- random numbers
     def philox_normals(self, n, seed, step, sid, device="cuda"):
+        """n N(0,1) draws of Philox4x32-10 keyed by (seed, step, stream id), as the time steps draw them."""
         out = torch.empty(n, dtype=torch.float64, device=device)
         self._check(self.lib.rpbd_philox_normals(self.h, seed, step, sid, n, _ptr(out), _stream()),
                     "philox_normals")
@@ -298,18 +314,23 @@ class Handle:
         return [x.as_dict() for x in st], s
 
     def step_ts(self, shape, q, theta, forces, sp):
+        """One trapezoidal-slip step (Alg. 2) in place on q, theta; returns (statistics per solve, status)."""
         return self._step(self.lib.rpbd_step_ts, 4, shape, q, theta, forces, sp)
 
     def step_emt(self, shape, q, theta, forces, sp):
+        """One Euler-Maruyama traction step (Alg. 1) in place on q, theta; returns (statistics per solve, status)."""
         return self._step(self.lib.rpbd_step_emt, 3, shape, q, theta, forces, sp)
 
     def step_emrfd(self, shape, q, theta, forces, sp):
+        """One Euler-Maruyama RFD step (Alg. 3, App. A) in place on q, theta; returns (statistics per solve, status)."""
         return self._step(self.lib.rpbd_step_emrfd, 4, shape, q, theta, forces, sp)
 
     def step_tt(self, shape, q, theta, forces, sp):
+        """One trapezoidal traction step (Sec. 3.2) in place on q, theta; returns (statistics per solve, status)."""
         return self._step(self.lib.rpbd_step_tt, 4, shape, q, theta, forces, sp)
 
     def blob_forces(self, r, forces: Forces, nper=0, dtype=F64, out=None):
+        """Per-blob forces (gravity, blob-wall and, with nper, blob-blob Yukawa repulsion; Sec. 4.1), [3, n]."""
         out = torch.empty_like(r) if out is None else out
         self._check(self.lib.rpbd_blob_forces(self.h, r.shape[1], nper, _ptr(r), C.byref(forces), dtype,
                                               _ptr(out), _stream()), "blob_forces")
