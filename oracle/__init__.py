@@ -21,5 +21,9 @@ Parity status per function (pins live in tests/test_oracle_*.py):
   GMRES saddle solve                     pinned: dense Schur form (eq. sysDense)
   RFD drift                              pinned: exact divergence in the mean
   Philox4x32-10 / Box-Muller             pinned: published known-answer vectors
-  T-S / EM-T steps                       pinned: dense linear algebra at tiny N
+  T-S, EM-T, EM-RFD, T-T steps           pinned: deterministic orders (kT = 0);
+      drift consistency -- the mean step equals the Ito drift
+      kT d_Q.(Psi N Psi^T) of App. B (eq. quatLangevin) at two bodies, from
+      a dense N and finite differences that share no code with the steps,
+      and a variant with D^S or D^F negated fails it
 """
