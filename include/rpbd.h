@@ -158,7 +158,10 @@ int rpbd_mobility_apply_mixed(rpbd_handle* h, int64_t n, const double* r, const 
  *    overlap on the GPU (different streams, or different host threads) race
  *    on it and corrupt each other's results; order them.
  *  - Asynchronous on `stream`; returns RPBD_OK, RPBD_TOO_LARGE, RPBD_BAD_ARG
- *    or RPBD_CUDA (no handle, so no message beyond rpbd_status_string). */
+ *    or RPBD_CUDA (no handle, so no message beyond rpbd_status_string).
+ *  - The pair kernel's waits for its source copies are bounded (~2 s); if
+ *    one runs out, every value of U is set to NaN, since the status has
+ *    already been returned when the kernel runs. */
 int rpbd_mobility_apply_f32_noalloc(const rpbd_params* p, int64_t n, const double* r, const float* F,
                                     float* U, int k, void* stream);
 
@@ -173,6 +176,15 @@ int rpbd_mobility_adjoint(rpbd_handle* h, int64_t n, const double* r, const doub
  * (position differences formed in FP64 first; sums in FP64). */
 int rpbd_mobility_adjoint_f32(rpbd_handle* h, int64_t n, const double* r, const double* u,
                               const double* F, double* grad, void* stream);
+
+/* grad[3][n] = d( sum_m u_m^T M(r) F_m )/dr for k right-hand-side pairs
+ * (1 <= k <= 16; u, F [k][3][n] FP64): the gradient of a loss of the k-RHS
+ * matvec of Sec. 2.1, summed over the pairs on the device.  Each pair block
+ * and its derivative are formed once for all k (FP32: in passes of up to four
+ * pairs).  dtype RPBD_F64 or RPBD_F32 selects the pair arithmetic as in the
+ * two calls above; sums are FP64. */
+int rpbd_mobility_adjoint_multi(rpbd_handle* h, int64_t n, const double* r, const double* u,
+                                const double* F, int k, double* grad, int dtype, void* stream);
 
 /* div[3][n] = sum_j d_{r_j} . M_ij (the quantity the RFD of Sec. 3 estimates
  * with B = M), FP64. */
@@ -364,6 +376,16 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
  * packed symmetric kernel over the batch (each system's unordered pairs
  * formed once, applied both ways; k > 4 then runs on variant 3). */
 #define RPBD_OPT_BATCH_VARIANT 4
+/* Failure-path test of the bounded waits (value != 0; default 0): the
+ * pair kernels of the handle (one-direction, symmetric, packed symmetric --
+ * the last also as batched variant 4; not the persistent batched tiles of
+ * variants 0-3) leave the barrier of their first source stage without a
+ * copy and wait on it for about 0.1 ms instead of ~2 s, so the wait runs out:
+ * the kernel records the timeout, lets its other copies land and exits, and
+ * the synchronising calls (Lanczos, GMRES, steps, batched Lanczos with iters)
+ * return RPBD_TIMEOUT.  The kernel-only calls then return garbage without a
+ * status.  For tests of the error path only; set it back to 0 afterwards. */
+#define RPBD_OPT_TEST_STALL 5
 int rpbd_set_option(rpbd_handle* h, int option, int value);
 
 /* Times the FP32 matvec kernels on n blobs at r (k right-hand sides, zero

@@ -49,6 +49,7 @@ SIGNATURES = [
     ("rpbd_mobility_apply_mixed", _I, [_P, _I64, _P, _P, _P, _I, _I, _P]),
     ("rpbd_mobility_adjoint", _I, [_P, _I64, _P, _P, _P, _P, _P]),
     ("rpbd_mobility_adjoint_f32", _I, [_P, _I64, _P, _P, _P, _P, _P]),
+    ("rpbd_mobility_adjoint_multi", _I, [_P, _I64, _P, _P, _P, _I, _P, _I, _P]),
     ("rpbd_mobility_divergence", _I, [_P, _I64, _P, _P, _P]),
     ("rpbd_K_apply", _I, [_P, _I64, _I, _P, _P, _P, _P, _P]),
     ("rpbd_KT_apply", _I, [_P, _I64, _I, _P, _P, _P, _P, _P]),

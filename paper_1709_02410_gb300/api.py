@@ -3,6 +3,8 @@
 Tensors must be contiguous CUDA tensors on the handle's device; positions
 are [3, n] float64 (SoA), blob vectors [k, 3, n] or [3, n], body vectors
 [nb, 6], q [nb, 3], theta [nb, 4].  Calls run on torch's current stream.
+Every tensor's dtype, shape and device is checked here before the library is
+called, so a wrong argument raises RpbdError and launches nothing.
 """
 import ctypes as C
 
@@ -16,33 +18,27 @@ class RpbdError(RuntimeError):
     pass
 
 
-def _ptr(t):
-    if t is None:
-        return None
-    if not t.is_cuda:
-        raise RpbdError("expected a CUDA tensor")
-    if not t.is_contiguous():
-        raise RpbdError("expected a contiguous tensor")
-    return C.c_void_p(t.data_ptr())
-
-
 def _stream():
     return C.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
-def _need(t, dtype, shape=None, name="tensor"):
-    if t.dtype != dtype:
-        raise RpbdError(f"{name}: expected {dtype}, got {t.dtype}")
-    if shape is not None and tuple(t.shape) != tuple(shape):
-        raise RpbdError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+def _kvec(t, n, name):
+    """k of a blob vector [3, n] (k = 1) or [k, 3, n] (1 <= k <= 16)."""
+    if t.dim() == 2 and tuple(t.shape) == (3, n):
+        return 1
+    if t.dim() == 3 and t.shape[1:] == (3, n) and 1 <= t.shape[0] <= 16:
+        return t.shape[0]
+    raise RpbdError(f"{name}: expected shape (3, {n}) or (k, 3, {n}) with 1 <= k <= 16, got {tuple(t.shape)}")
 
 
 class Handle:
-    """Owns an rpbd_handle (device workspace + physical parameters)."""
+    """Owns an rpbd_handle (device workspace + physical parameters), bound to
+    the CUDA device that is current when it is created."""
 
     def __init__(self, eta, a, kT=0.0, wall=True, s_min=1e-3, Lx=0.0, Ly=0.0):
         self.lib = _native.load()
         self.params = Params(eta, a, kT, int(bool(wall)), s_min, Lx, Ly)
+        self.device = torch.device("cuda", torch.cuda.current_device())
         h = C.c_void_p()
         st = self.lib.rpbd_create(C.byref(h), C.byref(self.params))
         if st != 0:
@@ -67,6 +63,28 @@ class Handle:
             raise RpbdError(f"{what}: {_native.STATUS.get(st, st)}: {msg}")
         return st
 
+    def _p(self, t, name, dtypes=(torch.float64,), shape=None):
+        """Device pointer of t after checking dtype, shape, device and layout
+        (None passes through as NULL)."""
+        if t is None:
+            return None
+        if not isinstance(t, torch.Tensor):
+            raise RpbdError(f"{name}: expected a torch tensor")
+        if not t.is_cuda or t.device != self.device:
+            raise RpbdError(f"{name}: expected a tensor on {self.device}, got {t.device}")
+        if t.dtype not in dtypes:
+            raise RpbdError(f"{name}: expected dtype {' or '.join(str(d) for d in dtypes)}, got {t.dtype}")
+        if shape is not None and tuple(t.shape) != tuple(shape):
+            raise RpbdError(f"{name}: expected shape {tuple(shape)}, got {tuple(t.shape)}")
+        if not t.is_contiguous():
+            raise RpbdError(f"{name}: expected a contiguous tensor")
+        return C.c_void_p(t.data_ptr())
+
+    def _r(self, r):
+        if not isinstance(r, torch.Tensor) or r.dim() != 2 or r.shape[0] != 3:
+            raise RpbdError(f"r: expected positions of shape (3, n), got {getattr(r, 'shape', type(r))}")
+        return r.shape[1], self._p(r, "r", shape=(3, r.shape[1]))
+
     def set_batch_variant(self, v: int):
         """tile variant of the batched kernel (-1 default, 0..4; 3: packed two targets per thread;
         4: packed symmetric kernel for k <= 4)"""
@@ -84,6 +102,11 @@ class Handle:
         """Loop-unroll / occupancy variant 0..3 of the symmetric kernels (-1: the default)."""
         self._check(self.lib.rpbd_set_option(self.h, 2, int(v)), "set_option")
 
+    def set_test_stall(self, on: bool):
+        """Failure-path test only: the pair kernels' first source wait runs out
+        (RPBD_TIMEOUT from the synchronising calls) until this is set back off."""
+        self._check(self.lib.rpbd_set_option(self.h, 5, int(bool(on))), "set_option")
+
     def measure_fma_peak(self, dtype=F32):
         """FMA throughput of this GPU in TFLOP/s (FMA = 2), measured by the library."""
         v = C.c_double()
@@ -92,8 +115,9 @@ class Handle:
 
     def autotune(self, r, k=1):
         """Pick the fastest FP32 kernel for this n and k; returns (choice, ms per launch)."""
+        n, rp = self._r(r)
         ms = C.c_double()
-        c = self.lib.rpbd_autotune(self.h, r.shape[1], _ptr(r), k, C.byref(ms), _stream())
+        c = self.lib.rpbd_autotune(self.h, n, rp, k, C.byref(ms), _stream())
         if c < 0:
             self._check(c, "autotune")
         return c, ms.value
@@ -103,87 +127,107 @@ class Handle:
         """Blob positions r = q_p + R(theta_p) s_i (Sec. 2.1) as [3, nb * nper] FP64 SoA."""
         nb, nper = q.shape[0], shape.shape[0]
         out = torch.empty((3, nb * nper), dtype=torch.float64, device=q.device) if out is None else out
-        for t, n in ((shape, "shape"), (q, "q"), (theta, "theta")):
-            _need(t, torch.float64, name=n)
-        self._check(self.lib.rpbd_blobs_from_bodies(self.h, nb, nper, _ptr(shape), _ptr(q), _ptr(theta),
-                                                    _ptr(out), _stream()), "blobs_from_bodies")
+        args = (self._p(shape, "shape", shape=(nper, 3)), self._p(q, "q", shape=(nb, 3)),
+                self._p(theta, "theta", shape=(nb, 4)), self._p(out, "out", shape=(3, nb * nper)))
+        self._check(self.lib.rpbd_blobs_from_bodies(self.h, nb, nper, *args, _stream()), "blobs_from_bodies")
         return out
 
     # ---- a2
     def mobility_apply(self, r, F, dtype=None, out=None):
         """U = M(r) F.  F [k,3,n] or [3,n]; float64 -> FP64 kernel, float32 ->
         FP32 kernel.  dtype=F32 with float64 F runs FP32 pairs on FP64 vectors."""
-        n = r.shape[1]
-        _need(r, torch.float64, (3, n), "r")
-        squeeze = F.dim() == 2
-        k = 1 if squeeze else F.shape[0]
-        out = torch.empty_like(F) if out is None else out
+        n, rp = self._r(r)
+        k = _kvec(F, n, "F")
         if dtype is None:
+            Fp = self._p(F, "F", (torch.float32, torch.float64))
             dt = F64 if F.dtype == torch.float64 else F32
             fn = self.lib.rpbd_mobility_apply
         else:
+            if dtype not in (F32, F64):
+                raise RpbdError("dtype: expected F32 or F64")
+            Fp = self._p(F, "F (mixed mode)")
             dt = dtype
-            if F.dtype != torch.float64:
-                raise RpbdError("mixed mode needs float64 vectors")
             fn = self.lib.rpbd_mobility_apply_mixed
-        self._check(fn(self.h, n, _ptr(r), _ptr(F), _ptr(out), k, dt, _stream()), "mobility_apply")
+        out = torch.empty_like(F) if out is None else out
+        Up = self._p(out, "out", (F.dtype,), tuple(F.shape))
+        self._check(fn(self.h, n, rp, Fp, Up, k, dt, _stream()), "mobility_apply")
         return out
 
     # ---- a7
     def mobility_adjoint(self, r, u, F, out=None, dtype=F64):
-        """d(u^T M(r) F)/dr, FP64 vectors; dtype F32 evaluates the pair derivative in FP32."""
-        n = r.shape[1]
+        """d(sum_m u_m^T M(r) F_m)/dr, FP64 vectors u, F of shape [3, n] or [k, 3, n]
+        (the sum over the k pairs runs on the device); dtype F32 evaluates the pair
+        derivative in FP32."""
+        n, rp = self._r(r)
+        k = _kvec(F, n, "F")
+        if tuple(u.shape) != tuple(F.shape):
+            raise RpbdError(f"u: expected the shape of F {tuple(F.shape)}, got {tuple(u.shape)}")
+        if dtype not in (F32, F64):
+            raise RpbdError("dtype: expected F32 or F64")
         out = torch.empty((3, n), dtype=torch.float64, device=r.device) if out is None else out
-        fn = self.lib.rpbd_mobility_adjoint_f32 if dtype == F32 else self.lib.rpbd_mobility_adjoint
-        self._check(fn(self.h, n, _ptr(r), _ptr(u), _ptr(F), _ptr(out), _stream()), "mobility_adjoint")
+        args = (self._p(u, "u"), self._p(F, "F"), k, self._p(out, "out", shape=(3, n)))
+        self._check(self.lib.rpbd_mobility_adjoint_multi(self.h, n, rp, *args, dtype, _stream()), "mobility_adjoint")
         return out
 
     def mobility_divergence(self, r, out=None):
         """div M (the thermal drift that the RFD of Sec. 3 estimates), exact, FP64, [3, n]."""
-        n = r.shape[1]
+        n, rp = self._r(r)
         out = torch.empty((3, n), dtype=torch.float64, device=r.device) if out is None else out
-        self._check(self.lib.rpbd_mobility_divergence(self.h, n, _ptr(r), _ptr(out), _stream()),
+        self._check(self.lib.rpbd_mobility_divergence(self.h, n, rp, self._p(out, "out", shape=(3, n)), _stream()),
                     "mobility_divergence")
         return out
 
     # ---- rigid
+    def _bodies(self, nper, r, q):
+        n, rp = self._r(r)
+        nb = q.shape[0]
+        if nper <= 0 or nb * nper != n:
+            raise RpbdError(f"bodies: {nb} bodies of {nper} blobs do not match r with {n} blobs")
+        return n, nb, rp, self._p(q, "q", shape=(nb, 3))
+
     def K_apply(self, nper, r, q, U, out=None):
         """Blob velocities K U of rigid-body motions U [nb, 6] (Sec. 2.1), [3, n]."""
-        nb = q.shape[0]
-        out = torch.empty((3, nb * nper), dtype=torch.float64, device=r.device) if out is None else out
-        self._check(self.lib.rpbd_K_apply(self.h, nb, nper, _ptr(r), _ptr(q), _ptr(U), _ptr(out), _stream()),
-                    "K_apply")
+        n, nb, rp, qp = self._bodies(nper, r, q)
+        out = torch.empty((3, n), dtype=torch.float64, device=r.device) if out is None else out
+        self._check(self.lib.rpbd_K_apply(self.h, nb, nper, rp, qp, self._p(U, "U", shape=(nb, 6)),
+                                          self._p(out, "out", shape=(3, n)), _stream()), "K_apply")
         return out
 
     def KT_apply(self, nper, r, q, lam, out=None):
         """Total force and torque K^T lambda per body of blob forces lambda [3, n], [nb, 6]."""
-        nb = q.shape[0]
+        n, nb, rp, qp = self._bodies(nper, r, q)
         out = torch.empty((nb, 6), dtype=torch.float64, device=r.device) if out is None else out
-        self._check(self.lib.rpbd_KT_apply(self.h, nb, nper, _ptr(r), _ptr(q), _ptr(lam), _ptr(out), _stream()),
-                    "KT_apply")
+        self._check(self.lib.rpbd_KT_apply(self.h, nb, nper, rp, qp, self._p(lam, "lam", shape=(3, n)),
+                                           self._p(out, "out", shape=(nb, 6)), _stream()), "KT_apply")
         return out
 
     # ---- a3
     def precond_build(self, nper, r, q):
         """Build the body-block-diagonal preconditioner (Sec. 2.2) at r; kept until the next build."""
-        self._check(self.lib.rpbd_precond_build(self.h, q.shape[0], nper, _ptr(r), _ptr(q), _stream()),
-                    "precond_build")
+        n, nb, rp, qp = self._bodies(nper, r, q)
+        self._n_prec = n
+        self._check(self.lib.rpbd_precond_build(self.h, nb, nper, rp, qp, _stream()), "precond_build")
 
     def precond_apply(self, mode, x, out=None):
         """Apply a stored factor per body: mode 0 L, 1 L^-1, 2 L^-T, 3 M~^-1."""
+        n = getattr(self, "_n_prec", None)
+        if n is None:
+            raise RpbdError("precond_apply: no preconditioner built through this handle")
         out = torch.empty_like(x) if out is None else out
-        self._check(self.lib.rpbd_precond_apply(self.h, mode, _ptr(x), _ptr(out), _stream()), "precond_apply")
+        self._check(self.lib.rpbd_precond_apply(self.h, mode, self._p(x, "x", shape=(3, n)),
+                                                self._p(out, "out", shape=(3, n)), _stream()), "precond_apply")
         return out
 
     # ---- a4
     def lanczos_sqrt_apply(self, r, W, tol, max_iter=80, dtype=F64, use_precond=True, out=None):
         """M^{1/2} W by preconditioned Lanczos (Sec. 2.2); returns (out, stats).  A run that stops
         at max_iter returns its last iterate with stats status -4 (not converged)."""
-        n = r.shape[1]
+        n, rp = self._r(r)
+        Wp = self._p(W, "W", shape=(3, n))
         out = torch.empty_like(W) if out is None else out
         st = Stats()
-        s = self.lib.rpbd_lanczos_sqrt_apply(self.h, n, _ptr(r), _ptr(W), _ptr(out), tol, max_iter, dtype,
-                                             int(bool(use_precond)), C.byref(st), _stream())
+        s = self.lib.rpbd_lanczos_sqrt_apply(self.h, n, rp, Wp, self._p(out, "out", shape=(3, n)), tol, max_iter,
+                                             dtype, int(bool(use_precond)), C.byref(st), _stream())
         if s not in (0, -4):
             self._check(s, "lanczos_sqrt_apply")
         return out, st.as_dict()
@@ -192,17 +236,19 @@ class Handle:
     def gmres_rigid_solve(self, nper, r, q, slip=None, FT=None, tol=1e-6, max_iter=200, restart=50, dtype=F64,
                           build_precond=True, x0=None):
         """x0 = (lambda0, U0): initial guess (GMRES warm start); default zero."""
-        nb = q.shape[0]
-        n = nb * nper
+        n, nb, rp, qp = self._bodies(nper, r, q)
         if x0 is None:
             lam = torch.empty((3, n), dtype=torch.float64, device=r.device)
             U = torch.empty((nb, 6), dtype=torch.float64, device=r.device)
         else:
             lam, U = x0[0].clone(), x0[1].clone()
         st = Stats()
-        s = self.lib.rpbd_gmres_rigid_solve(self.h, nb, nper, _ptr(r), _ptr(q), _ptr(slip), _ptr(FT), _ptr(lam),
-                                            _ptr(U), tol, max_iter, restart, dtype, int(bool(build_precond)),
-                                            int(x0 is not None), C.byref(st), _stream())
+        if build_precond:
+            self._n_prec = n
+        s = self.lib.rpbd_gmres_rigid_solve(self.h, nb, nper, rp, qp, self._p(slip, "slip", shape=(3, n)),
+                                            self._p(FT, "FT", shape=(nb, 6)), self._p(lam, "lambda", shape=(3, n)),
+                                            self._p(U, "U", shape=(nb, 6)), tol, max_iter, restart, dtype,
+                                            int(bool(build_precond)), int(x0 is not None), C.byref(st), _stream())
         if s not in (0, -4):
             self._check(s, "gmres_rigid_solve")
         return lam, U, st.as_dict()
@@ -210,13 +256,16 @@ class Handle:
     def lanczos_sqrt_apply_multi(self, r, Ws, tol=1e-4, max_iter=60, dtype=F64, use_precond=True):
         """1..4 Lanczos square roots M^{1/2} W at the same positions, in lockstep
         (shared multi-RHS matvecs).  Returns a list of (out, stats)."""
-        n = r.shape[1]
+        n, rp = self._r(r)
         ns = len(Ws)
+        if not 1 <= ns <= 4:
+            raise RpbdError("lanczos_sqrt_apply_multi: 1..4 vectors W")
         outs = [torch.empty((3, n), dtype=torch.float64, device=r.device) for _ in range(ns)]
         arr = C.c_void_p * ns
         st = (Stats * ns)()
-        s = self.lib.rpbd_lanczos_sqrt_apply_multi(self.h, n, _ptr(r), ns, arr(*[_ptr(w) for w in Ws]),
-                                                   arr(*[_ptr(o) for o in outs]), tol, max_iter, dtype,
+        s = self.lib.rpbd_lanczos_sqrt_apply_multi(self.h, n, rp, ns,
+                                                   arr(*[self._p(w, "W", shape=(3, n)) for w in Ws]),
+                                                   arr(*[self._p(o, "out") for o in outs]), tol, max_iter, dtype,
                                                    int(bool(use_precond)), st, _stream())
         if s not in (0, -4):
             self._check(s, "lanczos_sqrt_apply_multi")
@@ -227,18 +276,21 @@ class Handle:
         """problems: list of 1..4 (slip, FT) pairs (either None) at the same
         positions; solved in lockstep with shared multi-RHS matvecs.  Returns a
         list of (lambda, U, stats)."""
-        nb = q.shape[0]
-        n = nb * nper
+        n, nb, rp, qp = self._bodies(nper, r, q)
         ns = len(problems)
+        if not 1 <= ns <= 4:
+            raise RpbdError("gmres_rigid_solve_multi: 1..4 problems")
         outs = [(torch.empty((3, n), dtype=torch.float64, device=r.device),
                  torch.empty((nb, 6), dtype=torch.float64, device=r.device)) for _ in range(ns)]
         arr = C.c_void_p * ns
-        slips = arr(*[_ptr(p[0]) for p in problems])
-        fts = arr(*[_ptr(p[1]) for p in problems])
-        lams = arr(*[_ptr(o[0]) for o in outs])
-        us = arr(*[_ptr(o[1]) for o in outs])
+        slips = arr(*[self._p(p[0], "slip", shape=(3, n)) for p in problems])
+        fts = arr(*[self._p(p[1], "FT", shape=(nb, 6)) for p in problems])
+        lams = arr(*[self._p(o[0], "lambda") for o in outs])
+        us = arr(*[self._p(o[1], "U") for o in outs])
         st = (Stats * ns)()
-        s = self.lib.rpbd_gmres_rigid_solve_multi(self.h, nb, nper, _ptr(r), _ptr(q), ns, slips, fts, lams, us, tol,
+        if build_precond:
+            self._n_prec = n
+        s = self.lib.rpbd_gmres_rigid_solve_multi(self.h, nb, nper, rp, qp, ns, slips, fts, lams, us, tol,
                                                   max_iter, restart, dtype, int(bool(build_precond)), st, _stream())
         if s not in (0, -4):
             self._check(s, "gmres_rigid_solve_multi")
@@ -247,10 +299,11 @@ class Handle:
     # ---- a6
     def rfd_drift(self, r, W, delta, dtype=F64, out=None):
         """Blob-level centred RFD (Sec. 3): [M(r + delta/2 W) - M(r - delta/2 W)] W / delta; mean div M."""
-        n = r.shape[1]
+        n, rp = self._r(r)
+        Wp = self._p(W, "W", shape=(3, n))
         out = torch.empty_like(W) if out is None else out
-        self._check(self.lib.rpbd_rfd_drift(self.h, n, _ptr(r), _ptr(W), delta, _ptr(out), dtype, _stream()),
-                    "rfd_drift")
+        self._check(self.lib.rpbd_rfd_drift(self.h, n, rp, Wp, delta, self._p(out, "out", shape=(3, n)), dtype,
+                                            _stream()), "rfd_drift")
         return out
 
     # ---- batched suspensions
@@ -258,24 +311,33 @@ class Handle:
     def _offsets(offsets):
         import numpy as np
         off = np.ascontiguousarray(offsets, dtype=np.int64)
+        if off.ndim != 1 or off.size < 2 or off[0] != 0 or np.any(np.diff(off) < 0):
+            raise RpbdError("offsets: expected a non-decreasing 1-D array starting at 0 with >= 2 entries")
         return off, off.ctypes.data_as(C.c_void_p)
 
     def mobility_apply_batched(self, offsets, r, F, out=None):
         """U = M(r_s) F_s for independent systems concatenated at blob offsets (FP32 [k, 3, n])."""
         off, op = self._offsets(offsets)
         n_sys = off.size - 1
-        k = 1 if F.dim() == 2 else F.shape[0]
-        _need(F, torch.float32, name="F")
+        n, rp = self._r(r)
+        if n != off[-1]:
+            raise RpbdError(f"r: {n} blobs, offsets end at {off[-1]}")
+        k = _kvec(F, n, "F")
+        Fp = self._p(F, "F", (torch.float32,))
         out = torch.empty_like(F) if out is None else out
-        self._check(self.lib.rpbd_mobility_apply_batched(self.h, n_sys, op, _ptr(r), _ptr(F), _ptr(out), k,
+        self._check(self.lib.rpbd_mobility_apply_batched(self.h, n_sys, op, rp, Fp,
+                                                         self._p(out, "out", (torch.float32,), tuple(F.shape)), k,
                                                          _stream()), "mobility_apply_batched")
         return out
 
     def autotune_batched(self, offsets, r, k=1):
         """Time the batched variants on this batch and keep the fastest; returns (variant, ms)."""
         off, op = self._offsets(offsets)
+        n, rp = self._r(r)
+        if n != off[-1]:
+            raise RpbdError(f"r: {n} blobs, offsets end at {off[-1]}")
         ms = C.c_double()
-        v = self.lib.rpbd_autotune_batched(self.h, off.size - 1, op, _ptr(r), k, C.byref(ms), _stream())
+        v = self.lib.rpbd_autotune_batched(self.h, off.size - 1, op, rp, k, C.byref(ms), _stream())
         if v < 0:
             self._check(v, "autotune_batched")
         return v, ms.value
@@ -286,29 +348,39 @@ class Handle:
         use_graph), and optionally U = M F per system; returns (out, U, iterations per system)."""
         off, op = self._offsets(offsets)
         n_sys = off.size - 1
+        n, rp = self._r(r)
+        if n != off[-1]:
+            raise RpbdError(f"r: {n} blobs, offsets end at {off[-1]}")
+        Wp = self._p(W, "W", shape=(3, n))
         out = torch.empty_like(W) if out is None else out
         if F is not None and U is None:
             U = torch.empty_like(F)
         iters = (C.c_int * n_sys)()
-        self._check(self.lib.rpbd_lanczos_sqrt_apply_batched(self.h, n_sys, op, _ptr(r), _ptr(W), _ptr(out), _ptr(F),
-                                                             _ptr(U), tol, max_iter, int(bool(use_precond)),
-                                                             int(bool(use_graph)), iters, _stream()),
+        self._check(self.lib.rpbd_lanczos_sqrt_apply_batched(self.h, n_sys, op, rp, Wp,
+                                                             self._p(out, "out", shape=(3, n)),
+                                                             self._p(F, "F", shape=(3, n)),
+                                                             self._p(U, "U", shape=(3, n)), tol, max_iter,
+                                                             int(bool(use_precond)), int(bool(use_graph)), iters,
+                                                             _stream()),
                     "lanczos_sqrt_apply_batched")
         return out, U, list(iters)
 
     # ---- random numbers
-    def philox_normals(self, n, seed, step, sid, device="cuda"):
+    def philox_normals(self, n, seed, step, sid, device=None):
         """n N(0,1) draws of Philox4x32-10 keyed by (seed, step, stream id), as the time steps draw them."""
-        out = torch.empty(n, dtype=torch.float64, device=device)
-        self._check(self.lib.rpbd_philox_normals(self.h, seed, step, sid, n, _ptr(out), _stream()),
+        out = torch.empty(n, dtype=torch.float64, device=self.device if device is None else device)
+        self._check(self.lib.rpbd_philox_normals(self.h, seed, step, sid, n, self._p(out, "out"), _stream()),
                     "philox_normals")
         return out
 
     # ---- a8
     def _step(self, fn, nstats, shape, q, theta, forces: Forces, sp: StepParams):
+        nb, nper = q.shape[0], shape.shape[0]
+        args = (self._p(shape, "shape", shape=(nper, 3)), self._p(q, "q", shape=(nb, 3)),
+                self._p(theta, "theta", shape=(nb, 4)))
         st = (Stats * nstats)()
-        s = fn(self.h, q.shape[0], shape.shape[0], _ptr(shape), _ptr(q), _ptr(theta), C.byref(forces),
-               C.byref(sp), st, _stream())
+        self._n_prec = nb * nper  # every step builds the preconditioner
+        s = fn(self.h, nb, nper, *args, C.byref(forces), C.byref(sp), st, _stream())
         if s not in (0, -4):
             self._check(s, "step")
         return [x.as_dict() for x in st], s
@@ -331,7 +403,8 @@ class Handle:
 
     def blob_forces(self, r, forces: Forces, nper=0, dtype=F64, out=None):
         """Per-blob forces (gravity, blob-wall and, with nper, blob-blob Yukawa repulsion; Sec. 4.1), [3, n]."""
+        n, rp = self._r(r)
         out = torch.empty_like(r) if out is None else out
-        self._check(self.lib.rpbd_blob_forces(self.h, r.shape[1], nper, _ptr(r), C.byref(forces), dtype,
-                                              _ptr(out), _stream()), "blob_forces")
+        self._check(self.lib.rpbd_blob_forces(self.h, n, nper, rp, C.byref(forces), dtype,
+                                              self._p(out, "out", shape=(3, n)), _stream()), "blob_forces")
         return out

@@ -1,7 +1,7 @@
 """torch.autograd.Function around the wall-RPY matvec (FP64).
 
 forward:  U = M(r) F                      (rpbd_mobility_apply)
-backward: dL/dr = d(G^T M(r) F)/dr        (rpbd_mobility_adjoint, G = dL/dU)
+backward: dL/dr = d(sum_m G_m^T M(r) F_m)/dr  (rpbd_mobility_adjoint_multi, G = dL/dU)
           dL/dF = M(r)^T G = M(r) G       (M is symmetric)
 Both derivatives run in the CUDA library.
 """
@@ -22,12 +22,9 @@ class MobilityApply(torch.autograd.Function):
         G = G.contiguous()
         gr = gF = None
         if ctx.needs_input_grad[0]:
-            if F.dim() == 2:
-                gr = h.mobility_adjoint(r, G, F)
-            else:  # k right-hand sides: sum of the per-RHS adjoints
-                gr = torch.zeros_like(r)
-                for m in range(F.shape[0]):
-                    gr += h.mobility_adjoint(r, G[m].contiguous(), F[m].contiguous())
+            # one library call: for k right-hand sides the sum over them of
+            # d(G_m^T M F_m)/dr is formed on the device
+            gr = h.mobility_adjoint(r, G, F)
         if ctx.needs_input_grad[1]:
             gF = h.mobility_apply(r, G)
         return gr, gF, None

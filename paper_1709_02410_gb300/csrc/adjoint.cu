@@ -65,8 +65,11 @@ __device__ __forceinline__ void dual_block(const RegBlob& t, const RegBlob& s, c
     M[6] = Mzx; M[7] = Mzy; M[8] = Mzz;
 }
 
+// nr right-hand-side pairs (u_m, F_m), [nr][3][n] each: the weights
+// w_cd = sum_m (u_mk)_c (s_j F_mj)_d + (F_mk)_c (s_j u_mj)_d of one pair are
+// summed over m before they meet the block, which is formed once.
 template <bool WALL, bool PER, class S>
-__global__ void adjoint_kernel(int64_t n, const double* __restrict__ r, const double* __restrict__ u,
+__global__ void adjoint_kernel(int64_t n, int nr, const double* __restrict__ r, const double* __restrict__ u,
                                const double* __restrict__ F, double a, double s_min, double Lx, double Ly,
                                double inv8pieta, double* __restrict__ g)
 {
@@ -74,24 +77,30 @@ __global__ void adjoint_kernel(int64_t n, const double* __restrict__ r, const do
     if (k >= n) return;
     const PairConst<S> pc = PairConst<S>::make(a, Lx, Ly);
     const RegBlob bk = reg_blob(r, n, k, a, WALL, s_min);
-    const double uk[3] = {u[k], u[n + k], u[2 * n + k]};
-    const double Fk[3] = {F[k], F[n + k], F[2 * n + k]};
     double psi = 0.0, gr[3] = {0.0, 0.0, 0.0};
     for (int64_t j = 0; j < n; ++j) {
         const RegBlob bj = reg_blob(r, n, j, a, WALL, s_min);
-        const double Fj[3] = {bj.s * F[j], bj.s * F[n + j], bj.s * F[2 * n + j]};
-        const double uj[3] = {bj.s * u[j], bj.s * u[n + j], bj.s * u[2 * n + j]};
+        double w[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+        for (int m = 0; m < nr; ++m) {
+            const double* um = u + (int64_t)m * 3 * n;
+            const double* Fm = F + (int64_t)m * 3 * n;
+            const double uk[3] = {um[k], um[n + k], um[2 * n + k]};
+            const double Fk[3] = {Fm[k], Fm[n + k], Fm[2 * n + k]};
+            const double Fj[3] = {bj.s * Fm[j], bj.s * Fm[n + j], bj.s * Fm[2 * n + j]};
+            const double uj[3] = {bj.s * um[j], bj.s * um[n + j], bj.s * um[2 * n + j]};
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+#pragma unroll
+                for (int d = 0; d < 3; ++d) w[c * 3 + d] += uk[c] * Fj[d] + Fk[c] * uj[d];
+        }
         Dual<3, S> M[9];
         dual_block<WALL, PER, S>(bk, bj, pc, M);
 #pragma unroll
-        for (int c = 0; c < 3; ++c)
+        for (int cd = 0; cd < 9; ++cd) {
+            psi += w[cd] * (double)M[cd].v;
 #pragma unroll
-            for (int d = 0; d < 3; ++d) {
-                const double w = uk[c] * Fj[d] + Fk[c] * uj[d];
-                psi += w * (double)M[c * 3 + d].v;
-#pragma unroll
-                for (int e = 0; e < 3; ++e) gr[e] += w * (double)M[c * 3 + d].g[e];
-            }
+            for (int e = 0; e < 3; ++e) gr[e] += w[cd] * (double)M[cd].g[e];
+        }
     }
     g[k] = inv8pieta * bk.s * gr[0];
     g[n + k] = inv8pieta * bk.s * gr[1];
@@ -100,13 +109,14 @@ __global__ void adjoint_kernel(int64_t n, const double* __restrict__ r, const do
 
 // ---------------------------------------------------------------------------
 // FP32 adjoint: the same psi_k and target-slot derivative as adjoint_kernel,
-// computed with FP32 pair arithmetic.  Sources are packed once into 48-byte
-// records [x_hi, y_hi, x_lo, y_lo | zt, s F | s u, 0] (hi/lo split of x, y
-// so separations keep FP64-level accuracy), staged through shared memory in
-// tiles of 128 and split into chunks of 2048 sources (FP32 sums per chunk,
-// FP64 across chunks in a fixed order).  Instead of assembling the nine
-// dual-number entries, psi is contracted directly against the five block
-// scalars of pair_factors: with d = (dx, dy),
+// computed with FP32 pair arithmetic, for k right-hand-side pairs in passes
+// of up to four (their target vectors stay in registers).  Sources are packed
+// per pass into records [x_hi, y_hi, x_lo, y_lo | zt | s F_m, s u_m ...]
+// (hi/lo split of x, y so separations keep FP64-level accuracy), staged
+// through shared memory in tiles of 128 and split into chunks of 2048 sources
+// (FP32 sums per chunk, FP64 across chunks and passes in a fixed order).
+// Instead of assembling the nine dual-number entries, psi is contracted
+// directly against the five block scalars of pair_factors: with d = (dx, dy),
 //   a^T M c = alpha (a_x c_x + a_y c_y) + beta (a.d)(d.c) + gx (a.d) c_z
 //             + gz a_z (d.c) + Mzz a_z c_z,
 // and the explicit d-dependence of (a.d), (d.c) is differentiated by hand.
@@ -114,28 +124,54 @@ namespace adjf32 {
 
 constexpr int BT = 128;    // targets per CTA = sources per shared tile
 constexpr int CH = 2048;   // sources per chunk
+constexpr int KCMAX = 4;   // right-hand-side pairs per pass (target vectors held in registers)
 
-__global__ void pack_kernel(int64_t n, const double* __restrict__ r, const double* __restrict__ u,
-                            const double* __restrict__ F, double a, int wall, double s_min, float4* __restrict__ rec)
+// Source record of one pass over kc <= KCT right-hand-side pairs:
+// [x_hi, y_hi, x_lo, y_lo | zt, 0, 0, 0 | c_0, e_0, c_1, e_1, ...] with
+// c_m = s_j F_mj and e_m = s_j u_mj (3 floats each), padded to whole float4s.
+template <int KCT>
+struct ARec {
+    static constexpr int LEN = 8 + (6 * KCT + 3) / 4 * 4;
+};
+
+// u, F point at the pass's first right-hand side; stride 3n between pairs
+template <int KCT>
+__global__ void pack_kernel(int64_t n, int kc, const double* __restrict__ r, const double* __restrict__ u,
+                            const double* __restrict__ F, double a, int wall, double s_min, float* __restrict__ rec)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n) return;
+    constexpr int LEN = ARec<KCT>::LEN;
     const RegBlob b = reg_blob(r, n, i, a, wall, s_min);
+    float v[LEN];
+#pragma unroll
+    for (int q = 0; q < LEN; ++q) v[q] = 0.0f;
     const float xh = (float)b.x, yh = (float)b.y;
-    rec[3 * i] = make_float4(xh, yh, (float)(b.x - (double)xh), (float)(b.y - (double)yh));
-    rec[3 * i + 1] = make_float4((float)b.zt, (float)(b.s * F[i]), (float)(b.s * F[n + i]), (float)(b.s * F[2 * n + i]));
-    rec[3 * i + 2] = make_float4((float)(b.s * u[i]), (float)(b.s * u[n + i]), (float)(b.s * u[2 * n + i]), 0.0f);
+    v[0] = xh;
+    v[1] = yh;
+    v[2] = (float)(b.x - (double)xh);
+    v[3] = (float)(b.y - (double)yh);
+    v[4] = (float)b.zt;
+#pragma unroll
+    for (int m = 0; m < KCT; ++m)
+        if (m < kc)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[8 + 6 * m + c] = (float)(b.s * F[((int64_t)m * 3 + c) * n + i]);
+                v[8 + 6 * m + 3 + c] = (float)(b.s * u[((int64_t)m * 3 + c) * n + i]);
+            }
+    float4* o = reinterpret_cast<float4*>(rec + i * LEN);
+#pragma unroll
+    for (int q = 0; q < LEN / 4; ++q) o[q] = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
 }
 
-struct Vecs {
-    float ax, ay, az, bx, by, bz;  // target: a = u_k, b = F_k
-    float cx, cy, cz, ex, ey, ez;  // source: c = s_j F_j, e = s_j u_j
-    float S1, S3;                  // a_xy.c_xy + b_xy.e_xy, a_z c_z + b_z e_z
-};
-
-template <bool WALL>
+// psi and the target-slot gradient of one pair summed over the pass's
+// right-hand-side pairs: the dual-number block scalars are formed once, and
+// each pair m (target a = u_m, b = F_m; source c = s_j F_m, e = s_j u_m)
+// adds to the scalars they are contracted with.
+template <bool WALL, int KCT>
 __device__ __forceinline__ void contract(float dxv, float dyv, float dzv, float zi, float zj, const PairConst<float>& pc,
-                                         const Vecs& w, float& psi, float g[3])
+                                         const float* A, const float* B, const float* src, float& psi, float g[3])
 {
     using D3 = Dual<3, float>;
     D3 dx(dxv), dy(dyv), dz(dzv), Zi(zi), Zj(zj);
@@ -145,64 +181,82 @@ __device__ __forceinline__ void contract(float dxv, float dyv, float dzv, float 
     Zi.g[2] = 1.0f;
     D3 al, be, gx, gz, mzz;
     pair_factors<D3, float, WALL>(dx, dy, dz, Zi, Zj, pc, al, be, gx, gz, mzz);
-    const float P1 = fmaf(w.ay, dyv, w.ax * dxv), D1 = fmaf(w.cy, dyv, w.cx * dxv);
-    const float P2 = fmaf(w.by, dyv, w.bx * dxv), D2 = fmaf(w.ey, dyv, w.ex * dxv);
-    const float Q = fmaf(P2, D2, P1 * D1);
-    const float Rr = fmaf(w.ez, P2, w.cz * P1);
-    const float Zz = fmaf(w.bz, D2, w.az * D1);
-    psi += al.v * w.S1 + be.v * Q + gx.v * Rr + gz.v * Zz + mzz.v * w.S3;
-#pragma unroll
-    for (int q = 0; q < 3; ++q)
-        g[q] += al.g[q] * w.S1 + be.g[q] * Q + gx.g[q] * Rr + gz.g[q] * Zz + mzz.g[q] * w.S3;
+    // S1 = a_xy.c_xy + b_xy.e_xy, S3 = a_z c_z + b_z e_z, Q = (a.d)(d.c) + (b.d)(d.e),
+    // Rr = c_z (a.d) + e_z (b.d), Zz = a_z (d.c) + b_z (d.e), and the explicit
     // d/d(dx), d/d(dy) of Q, Rr, Zz
-    const float dQx = w.ax * D1 + w.cx * P1 + w.bx * D2 + w.ex * P2;
-    const float dQy = w.ay * D1 + w.cy * P1 + w.by * D2 + w.ey * P2;
-    g[0] += be.v * dQx + gx.v * (w.cz * w.ax + w.ez * w.bx) + gz.v * (w.az * w.cx + w.bz * w.ex);
-    g[1] += be.v * dQy + gx.v * (w.cz * w.ay + w.ez * w.by) + gz.v * (w.az * w.cy + w.bz * w.ey);
+    float S1 = 0.0f, S3 = 0.0f, Q = 0.0f, Rr = 0.0f, Zz = 0.0f, dQx = 0.0f, dQy = 0.0f;
+    float Gx0 = 0.0f, Gx1 = 0.0f, Gz0 = 0.0f, Gz1 = 0.0f;
+#pragma unroll
+    for (int m = 0; m < KCT; ++m) {
+        const float ax = A[3 * m], ay = A[3 * m + 1], az = A[3 * m + 2];
+        const float bx = B[3 * m], by = B[3 * m + 1], bz = B[3 * m + 2];
+        const float* cs = src + 8 + 6 * m;
+        const float cx = cs[0], cy = cs[1], cz = cs[2], ex = cs[3], ey = cs[4], ez = cs[5];
+        S1 += fmaf(ay, cy, ax * cx) + fmaf(by, ey, bx * ex);
+        S3 += fmaf(bz, ez, az * cz);
+        const float P1 = fmaf(ay, dyv, ax * dxv), D1 = fmaf(cy, dyv, cx * dxv);
+        const float P2 = fmaf(by, dyv, bx * dxv), D2 = fmaf(ey, dyv, ex * dxv);
+        Q += fmaf(P2, D2, P1 * D1);
+        Rr += fmaf(ez, P2, cz * P1);
+        Zz += fmaf(bz, D2, az * D1);
+        dQx += ax * D1 + cx * P1 + bx * D2 + ex * P2;
+        dQy += ay * D1 + cy * P1 + by * D2 + ey * P2;
+        Gx0 += cz * ax + ez * bx;
+        Gx1 += cz * ay + ez * by;
+        Gz0 += az * cx + bz * ex;
+        Gz1 += az * cy + bz * ey;
+    }
+    psi += al.v * S1 + be.v * Q + gx.v * Rr + gz.v * Zz + mzz.v * S3;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) g[q] += al.g[q] * S1 + be.g[q] * Q + gx.g[q] * Rr + gz.g[q] * Zz + mzz.g[q] * S3;
+    g[0] += be.v * dQx + gx.v * Gx0 + gz.v * Gz0;
+    g[1] += be.v * dQy + gx.v * Gx1 + gz.v * Gz1;
 }
 
-template <bool WALL, bool PER>
-__global__ void __launch_bounds__(BT) adjoint_f32_kernel(int64_t n, const float4* __restrict__ rec,
+// one pass: kc <= KCT right-hand-side pairs, partials of chunk blockIdx.y
+// written to part[(blockIdx.y * 4 + q) * n + k], q = (psi, g_x, g_y, g_z)
+template <bool WALL, bool PER, int KCT>
+__global__ void __launch_bounds__(BT) adjoint_f32_kernel(int64_t n, int kc, const float* __restrict__ rec,
                                                          const double* __restrict__ u, const double* __restrict__ F,
                                                          PairConst<float> pc, float* __restrict__ part)
 {
-    __shared__ float4 tile[3 * BT];
+    constexpr int LEN = ARec<KCT>::LEN;
+    __shared__ __align__(16) float tile[BT * LEN];
     const int tid = threadIdx.x;
     const int64_t k = blockIdx.x * (int64_t)BT + tid;
     const int64_t kk = k < n ? k : n - 1;
-    const float4 t0 = rec[3 * kk], t1 = rec[3 * kk + 1];
-    Vecs w;
-    w.ax = (float)u[kk]; w.ay = (float)u[n + kk]; w.az = (float)u[2 * n + kk];
-    w.bx = (float)F[kk]; w.by = (float)F[n + kk]; w.bz = (float)F[2 * n + kk];
+    const float4 t0 = *reinterpret_cast<const float4*>(rec + kk * LEN);
+    const float zi = rec[kk * LEN + 4];
+    float A[3 * KCT], B[3 * KCT];
+#pragma unroll
+    for (int m = 0; m < KCT; ++m)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            A[3 * m + c] = m < kc ? (float)u[((int64_t)m * 3 + c) * n + kk] : 0.0f;
+            B[3 * m + c] = m < kc ? (float)F[((int64_t)m * 3 + c) * n + kk] : 0.0f;
+        }
     const int64_t j0 = (int64_t)blockIdx.y * CH;
     const int64_t j1 = (j0 + CH) < n ? (j0 + CH) : n;
     float psi = 0.0f, g[3] = {0.0f, 0.0f, 0.0f};
     for (int64_t base = j0; base < j1; base += BT) {
-        const int64_t j = base + tid;
-        if (j < j1) {
-            tile[3 * tid] = rec[3 * j];
-            tile[3 * tid + 1] = rec[3 * j + 1];
-            tile[3 * tid + 2] = rec[3 * j + 2];
-        }
-        __syncthreads();
         const int cnt = (int)((j1 - base) < BT ? (j1 - base) : BT);
+        const float4* srcv = reinterpret_cast<const float4*>(rec + base * LEN);
+        for (int e = tid; e < cnt * (LEN / 4); e += BT) reinterpret_cast<float4*>(tile)[e] = srcv[e];
+        __syncthreads();
         for (int jj = 0; jj < cnt; ++jj) {
-            const float4 s0 = tile[3 * jj], s1 = tile[3 * jj + 1], s2 = tile[3 * jj + 2];
-            const float dxv = (t0.x - s0.x) + (t0.z - s0.z), dyv = (t0.y - s0.y) + (t0.w - s0.w);
-            w.cx = s1.y; w.cy = s1.z; w.cz = s1.w;
-            w.ex = s2.x; w.ey = s2.y; w.ez = s2.z;
-            w.S1 = fmaf(w.ay, w.cy, w.ax * w.cx) + fmaf(w.by, w.ey, w.bx * w.ex);
-            w.S3 = fmaf(w.bz, w.ez, w.az * w.cz);
+            const float* sj = tile + jj * LEN;
+            const float dxv = (t0.x - sj[0]) + (t0.z - sj[2]), dyv = (t0.y - sj[1]) + (t0.w - sj[3]);
+            const float zj = sj[4];
             if (!PER) {
-                contract<WALL>(dxv, dyv, t1.x - s1.x, t1.x, s1.x, pc, w, psi, g);
+                contract<WALL, KCT>(dxv, dyv, zi - zj, zi, zj, pc, A, B, sj, psi, g);
             } else {
                 const float dxm = dxv - pc.Lx * rintf(dxv * pc.iLx), dym = dyv - pc.Ly * rintf(dyv * pc.iLy);
 #pragma unroll
                 for (int ia = -1; ia <= 1; ++ia)
 #pragma unroll
                     for (int ib = -1; ib <= 1; ++ib)
-                        contract<WALL>(dxm + (float)ia * pc.Lx, dym + (float)ib * pc.Ly, t1.x - s1.x, t1.x, s1.x, pc, w,
-                                       psi, g);
+                        contract<WALL, KCT>(dxm + (float)ia * pc.Lx, dym + (float)ib * pc.Ly, zi - zj, zi, zj, pc, A, B,
+                                            sj, psi, g);
             }
         }
         __syncthreads();
@@ -216,20 +270,37 @@ __global__ void __launch_bounds__(BT) adjoint_f32_kernel(int64_t n, const float4
     }
 }
 
-// g_k from the chunk partials, FP64, chunks in order
-__global__ void reduce_kernel(int64_t n, int nch, const float* __restrict__ part, const double* __restrict__ r,
+// g_k from the partials of every (pass, chunk), FP64, in a fixed order
+__global__ void reduce_kernel(int64_t n, int nparts, const float* __restrict__ part, const double* __restrict__ r,
                               double a, int wall, double s_min, double inv8pieta, double* __restrict__ grad)
 {
     const int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (k >= n) return;
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    for (int c = 0; c < nch; ++c)
+    for (int c = 0; c < nparts; ++c)
 #pragma unroll
         for (int q = 0; q < 4; ++q) acc[q] += (double)part[((int64_t)c * 4 + q) * n + k];
     const RegBlob b = reg_blob(r, n, k, a, wall, s_min);
     grad[k] = inv8pieta * b.s * acc[1];
     grad[n + k] = inv8pieta * b.s * acc[2];
     grad[2 * n + k] = inv8pieta * (b.s * acc[3] * b.dzt + b.ds * acc[0]);
+}
+
+template <int KCT>
+static void launch_pass(int64_t n, int kc, const double* r, const double* u, const double* F, const rpbd_params& p,
+                        float* rec, float* part, cudaStream_t st)
+{
+    const unsigned grid = (unsigned)((n + BT - 1) / BT);
+    const int nch = (int)((n + CH - 1) / CH);
+    const int wall = p.wall ? 1 : 0;
+    pack_kernel<KCT><<<grid, BT, 0, st>>>(n, kc, r, u, F, p.a, wall, p.s_min, rec);
+    count_launch();
+    const PairConst<float> pc = PairConst<float>::make(p.a, p.Lx, p.Ly);
+    const dim3 g2(grid, (unsigned)nch);
+    if (p.Lx > 0.0) adjoint_f32_kernel<true, true, KCT><<<g2, BT, 0, st>>>(n, kc, rec, u, F, pc, part);
+    else if (wall) adjoint_f32_kernel<true, false, KCT><<<g2, BT, 0, st>>>(n, kc, rec, u, F, pc, part);
+    else adjoint_f32_kernel<false, false, KCT><<<g2, BT, 0, st>>>(n, kc, rec, u, F, pc, part);
+    count_launch();
 }
 
 }  // namespace adjf32
@@ -282,11 +353,12 @@ using namespace rpbd;
 
 extern "C" {
 
-static int adjoint_entry(rpbd_handle* h, int64_t n, const double* r, const double* u, const double* F, double* grad,
-                         void* stream, bool f32)
+static int adjoint_entry(rpbd_handle* h, int64_t n, const double* r, const double* u, const double* F, int nr,
+                         double* grad, void* stream, bool f32)
 {
     if (!h) return RPBD_BAD_ARG;
-    if (n < 0 || (n > 0 && (!r || !u || !F || !grad))) return set_error(h, RPBD_BAD_ARG, "adjoint: bad arguments");
+    if (n < 0 || nr < 1 || nr > 16 || (n > 0 && (!r || !u || !F || !grad)))
+        return set_error(h, RPBD_BAD_ARG, "adjoint: bad arguments (need n >= 0, 1 <= k <= 16, non-null pointers)");
     if (n == 0) return RPBD_OK;
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
@@ -295,25 +367,26 @@ static int adjoint_entry(rpbd_handle* h, int64_t n, const double* r, const doubl
     const bool per = Lx > 0.0;
     if (f32) {
         using namespace adjf32;
-        float4* rec;
-        float* part;
         const int nch = (int)((n + CH - 1) / CH);
-        RPBD_TRY(ensure_t(h, BUF_PACK, (size_t)3 * n, &rec));
-        RPBD_TRY(ensure_t(h, BUF_PARTIAL, (size_t)nch * 4 * n, &part));
-        const int wall = h->p.wall ? 1 : 0;
-        pack_kernel<<<grid, 128, 0, st>>>(n, r, u, F, a, wall, sm, rec);
-        count_launch();
-        const PairConst<float> pc = PairConst<float>::make(a, Lx, Ly);
-        const dim3 g2(grid, (unsigned)nch);
-        if (per) adjoint_f32_kernel<true, true><<<g2, BT, 0, st>>>(n, rec, u, F, pc, part);
-        else if (wall) adjoint_f32_kernel<true, false><<<g2, BT, 0, st>>>(n, rec, u, F, pc, part);
-        else adjoint_f32_kernel<false, false><<<g2, BT, 0, st>>>(n, rec, u, F, pc, part);
-        count_launch();
-        reduce_kernel<<<grid, 128, 0, st>>>(n, nch, part, r, a, wall, sm, inv8pieta, grad);
+        const int npass = (nr + KCMAX - 1) / KCMAX;
+        float* rec;
+        float* part;
+        RPBD_TRY(ensure_t(h, BUF_PACK, (size_t)n * ARec<KCMAX>::LEN, &rec));
+        RPBD_TRY(ensure_t(h, BUF_PARTIAL, (size_t)npass * nch * 4 * n, &part));
+        for (int ps = 0; ps < npass; ++ps) {
+            const int m0 = ps * KCMAX, kc = nr - m0 < KCMAX ? nr - m0 : KCMAX;
+            const double* up = u + (int64_t)m0 * 3 * n;
+            const double* Fp = F + (int64_t)m0 * 3 * n;
+            float* pp = part + (size_t)ps * nch * 4 * n;
+            if (kc == 1) launch_pass<1>(n, kc, r, up, Fp, h->p, rec, pp, st);
+            else if (kc == 2) launch_pass<2>(n, kc, r, up, Fp, h->p, rec, pp, st);
+            else launch_pass<4>(n, kc, r, up, Fp, h->p, rec, pp, st);
+        }
+        reduce_kernel<<<grid, 128, 0, st>>>(n, npass * nch, part, r, a, h->p.wall ? 1 : 0, sm, inv8pieta, grad);
     } else {
-        if (per) adjoint_kernel<true, true, double><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
-        else if (h->p.wall) adjoint_kernel<true, false, double><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
-        else adjoint_kernel<false, false, double><<<grid, 128, 0, st>>>(n, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
+        if (per) adjoint_kernel<true, true, double><<<grid, 128, 0, st>>>(n, nr, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
+        else if (h->p.wall) adjoint_kernel<true, false, double><<<grid, 128, 0, st>>>(n, nr, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
+        else adjoint_kernel<false, false, double><<<grid, 128, 0, st>>>(n, nr, r, u, F, a, sm, Lx, Ly, inv8pieta, grad);
     }
     count_launch();
     RPBD_LAUNCH_CHECK(h);
@@ -323,13 +396,20 @@ static int adjoint_entry(rpbd_handle* h, int64_t n, const double* r, const doubl
 int rpbd_mobility_adjoint(rpbd_handle* h, int64_t n, const double* r, const double* u, const double* F, double* grad,
                           void* stream)
 {
-    return adjoint_entry(h, n, r, u, F, grad, stream, false);
+    return adjoint_entry(h, n, r, u, F, 1, grad, stream, false);
 }
 
 int rpbd_mobility_adjoint_f32(rpbd_handle* h, int64_t n, const double* r, const double* u, const double* F,
                               double* grad, void* stream)
 {
-    return adjoint_entry(h, n, r, u, F, grad, stream, true);
+    return adjoint_entry(h, n, r, u, F, 1, grad, stream, true);
+}
+
+int rpbd_mobility_adjoint_multi(rpbd_handle* h, int64_t n, const double* r, const double* u, const double* F, int k,
+                                double* grad, int dtype, void* stream)
+{
+    if (h && dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "adjoint: bad dtype");
+    return adjoint_entry(h, n, r, u, F, k, grad, stream, dtype == RPBD_F32);
 }
 
 int rpbd_mobility_divergence(rpbd_handle* h, int64_t n, const double* r, double* div, void* stream)

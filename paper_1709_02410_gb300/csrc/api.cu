@@ -4,7 +4,10 @@
 #include <cstdio>
 #include <cstring>
 #include <atomic>
+#include <mutex>
 #include <new>
+#include <set>
+#include <utility>
 
 #include "rpbd_internal.cuh"
 
@@ -46,6 +49,14 @@ int set_error(rpbd_handle* h, int code, const std::string& msg)
 {
     if (h) h->err = msg;
     return code;
+}
+
+bool once_per_device(rpbd_handle* h, const void* key)
+{
+    static std::mutex mu;
+    static std::set<std::pair<int, const void*>> seen;
+    std::lock_guard<std::mutex> lock(mu);
+    return seen.insert(std::make_pair(h->device, key)).second;
 }
 
 int ensure(rpbd_handle* h, Buf b, size_t bytes, void** out)
@@ -257,6 +268,7 @@ int rpbd_set_option(rpbd_handle* h, int option, int value)
         if (value < -1 || value > 3) return set_error(h, RPBD_BAD_ARG, "symmetric variant must be -1..3");
         for (int c = 0; c < 3; ++c) h->sym_variant[c] = value;
         return RPBD_OK;
+    case RPBD_OPT_TEST_STALL: h->test_stall = value != 0; return RPBD_OK;
     default: return set_error(h, RPBD_BAD_ARG, "unknown option");
     }
 }

@@ -180,6 +180,7 @@ struct BatchGraph {
     int use_precond = 0;
     bool with_apply = false;
     int variant = -1;
+    int test_stall = 0;  // the failure-path test option the kernels were captured with
     // every workspace buffer the captured kernels address: a buffer that has
     // grown (moved) since the capture invalidates the graph
     static constexpr int NSIG = 8;
@@ -320,12 +321,9 @@ int rpbd_lanczos_sqrt_apply_batched(rpbd_handle* h, int n_sys, const int64_t* of
     if (use_precond && (!h->prec_valid || h->prec_nb * h->prec_nper != n))
         return set_error(h, RPBD_BAD_ARG, "batched lanczos: preconditioner not built for these blobs");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
-    static bool attr = false;
-    if (!attr) {
+    if (once_per_device(h, reinterpret_cast<const void*>(blz_sqrt_kernel)))
         RPBD_CU(h, cudaFuncSetAttribute(blz_sqrt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         tridiag_sqrt_smem_doubles(BLZ_MAX) * (int)sizeof(double)));
-        attr = true;
-    }
     BlzBufs B;
     RPBD_TRY(blz_bufs(h, n_sys, offsets, n, max_iter, &B));
     const bool with_apply = F != nullptr;
@@ -346,7 +344,8 @@ int rpbd_lanczos_sqrt_apply_batched(rpbd_handle* h, int n_sys, const int64_t* of
         signature(sig);
         for (BatchGraph* c : h->bgraphs)
             if (c->max_iter == max_iter && c->tol == tol && c->use_precond == use_precond &&
-                c->with_apply == with_apply && c->variant == h->batch_variant && (int)c->off.size() == n_sys + 1 &&
+                c->with_apply == with_apply && c->variant == h->batch_variant && c->test_stall == h->test_stall &&
+                (int)c->off.size() == n_sys + 1 &&
                 std::equal(c->off.begin(), c->off.end(), offsets) && std::equal(sig, sig + BatchGraph::NSIG, c->sig))
                 G = c;
         if (!G) {
@@ -363,6 +362,7 @@ int rpbd_lanczos_sqrt_apply_batched(rpbd_handle* h, int n_sys, const int64_t* of
             G->use_precond = use_precond;
             G->with_apply = with_apply;
             G->variant = h->batch_variant;
+            G->test_stall = h->test_stall;
             std::copy(sig2, sig2 + BatchGraph::NSIG, G->sig);
             h->bgraphs.push_back(G);
             RPBD_CU(h, cudaStreamCreateWithFlags(&G->cap, cudaStreamNonBlocking));

@@ -306,12 +306,9 @@ int lanczos_multi_impl(rpbd_handle* h, int64_t n, const double* r, int nsys, con
     RPBD_TRY(ensure_t(h, BUF_VEC, (size_t)nsys * 3 * len, &vall));
     RPBD_TRY(ensure_t(h, BUF_SMALL, (size_t)nsys * small_count, &small));
     if (nsys > 1) RPBD_TRY(ensure_t(h, BUF_GMRES_MV, (size_t)2 * nsys * len, &mv));
-    static bool attr = false;
-    if (!attr) {
+    if (once_per_device(h, reinterpret_cast<const void*>(lanczos_sqrt_kernel)))
         RPBD_CU(h, cudaFuncSetAttribute(lanczos_sqrt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                         tridiag_sqrt_smem_doubles(LANCZOS_MAX + 1) * (int)sizeof(double)));
-        attr = true;
-    }
     RPBD_CU(h, cudaMemsetAsync(h->dev_flag, 0, sizeof(int), st));
     const unsigned g = vgrid(len);
     LanczosProc P[4];

@@ -93,13 +93,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
         : "memory");
     return ok != 0;
 }
-// bounded wait: ~2 s of SM clock at most; false on timeout
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+// bounded wait: `limit` SM clock cycles at most (default ~2 s); false on timeout
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = 4000000000LL)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity)) {
-        if (clock64() - t0 > 4000000000LL) return false;
+        if (clock64() - t0 > limit) return false;
     }
     return true;
 }
@@ -173,7 +173,7 @@ __global__ void pack_kernel(int64_t n, int64_t n_pad, int k, const double* __res
 template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
 __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, int64_t n_pad, int tiles_per_chunk,
                                           int n_tiles, PairConst<R> pc, typename PartialT<R>::type* __restrict__ partial,
-                                          int* __restrict__ err_flag)
+                                          int* __restrict__ err_flag, RingTest rt)
 {
     constexpr int LEN = Rec<R, K>::LEN;
     constexpr uint32_t TILE_BYTES = TS * LEN * sizeof(R);
@@ -195,7 +195,8 @@ __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, 
     }
     __syncthreads();
     if (tid == 0) {
-        for (int s = 0; s < NST && s < ntile; ++s) {
+        // (failure-path test: stage 0 gets no copy, so its wait runs out)
+        for (int s = rt.skip_first ? 1 : 0; s < NST && s < ntile; ++s) {
             mbar_expect_tx(&bar[s], TILE_BYTES);
             tma_load_1d(stage + (size_t)s * TS * LEN, rec + (size_t)(tile0 + s) * TS * LEN, TILE_BYTES, &bar[s]);
         }
@@ -229,7 +230,7 @@ __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, 
     for (; t < ntile; ++t) {
         const int s = t % NST;
         const uint32_t par = (t / NST) & 1;
-        const bool ok = mbar_wait_bounded(&bar[s], par);
+        const bool ok = mbar_wait_bounded(&bar[s], par, rt.limit);
         if (ok) {
             const R* st = stage + (size_t)s * TS * LEN;
 #pragma unroll(K <= 4 ? 2 : 1)
@@ -328,9 +329,9 @@ template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
 __global__ void __launch_bounds__(BT) pair_kernel(const R* __restrict__ rec, int64_t n, int64_t n_pad,
                                                   int tiles_per_chunk, int n_tiles, PairConst<R> pc,
                                                   typename PartialT<R>::type* __restrict__ partial,
-                                                  int* __restrict__ err_flag)
+                                                  int* __restrict__ err_flag, RingTest rt)
 {
-    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag);
+    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag, rt);
 }
 
 // FP32, 16 right-hand sides: registers capped so five CTAs share an SM
@@ -338,9 +339,9 @@ template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
 __global__ void __launch_bounds__(BT, 5) pair_kernel_k16(const R* __restrict__ rec, int64_t n, int64_t n_pad,
                                                          int tiles_per_chunk, int n_tiles, PairConst<R> pc,
                                                          typename PartialT<R>::type* __restrict__ partial,
-                                                         int* __restrict__ err_flag)
+                                                         int* __restrict__ err_flag, RingTest rt)
 {
-    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag);
+    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag, rt);
 }
 
 template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
@@ -432,14 +433,12 @@ static int apply_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out*
     RPBD_LAUNCH_CHECK(h);
     const size_t smem = (size_t)NST * TS * LEN * sizeof(R) + NST * sizeof(uint64_t);
     auto kern = pick_pair_kernel<R, K, BT, TS, NST, WALL, PER>();
-    static bool attr_set = false;
-    if (!attr_set) {
+    if (once_per_device(h, reinterpret_cast<const void*>(kern)))
         RPBD_CU(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        attr_set = true;
-    }
     dim3 grid((unsigned)tgt_tiles, (unsigned)n_chunks);
     if (h->profile) prof_begin(h, st);
-    kern<<<grid, BT, smem, st>>>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, h->dev_flag); count_launch();
+    kern<<<grid, BT, smem, st>>>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, h->dev_flag, ring_test(h));
+    count_launch();
     if (h->profile) prof_end(h, st, sizeof(R) == 4 ? RPBD_F32 : RPBD_F64, K, (double)n * (double)n);
     RPBD_LAUNCH_CHECK(h);
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
@@ -548,6 +547,16 @@ static int scratch_address(unsigned char** out)
     return RPBD_OK;
 }
 
+// A pair kernel whose bounded wait ran out skips its partial sums, so the
+// reduction has summed stale values from an earlier call: the whole result
+// is overwritten with NaN so that it cannot pass for a valid one.
+__global__ void poison_on_timeout_kernel(int64_t count, const int* __restrict__ flag, float* __restrict__ U)
+{
+    if (*flag == 0) return;
+    const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (e < count) U[e] = __int_as_float(0x7fc00000);
+}
+
 template <int K, bool WALL>
 static int apply(int sm_count, const rpbd_params& p, int64_t n, const double* r, const float* F, float* U, int k,
                  cudaStream_t st)
@@ -592,11 +601,14 @@ static int apply(int sm_count, const rpbd_params& p, int64_t n, const double* r,
     static_assert((size_t)NST * TS * Rec<float, 16>::LEN * sizeof(float) + NST * sizeof(uint64_t) <= 48 * 1024,
                   "the no-alloc kernels must fit the default dynamic shared memory limit");
     pair_kernel<float, K, BT, TS, NST, WALL, false><<<dim3((unsigned)tgt_tiles, (unsigned)n_chunks), BT, smem, st>>>(
-        rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, flag);
+        rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, flag, RingTest{4000000000LL, 0});
     count_launch();
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * p.eta);
     reduce_kernel<float, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(
         n, n_pad, k, K, n_chunks, partial, scale, inv8pieta, U);
+    count_launch();
+    const int64_t count = (int64_t)3 * k * n;
+    poison_on_timeout_kernel<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(count, flag, U);
     count_launch();
     return cudaGetLastError() == cudaSuccess ? RPBD_OK : RPBD_CUDA;
 }

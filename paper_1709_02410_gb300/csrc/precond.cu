@@ -328,8 +328,7 @@ int precond_build_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, co
     RPBD_TRY(ensure_t(h, BUF_PREC_N, (size_t)nb * 36, &N));
     const size_t smem = (size_t)(2 * m * m + 6 * m + 5 * nper) * sizeof(double);
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
-    static bool attr = false;
-    if (!attr) {
+    if (once_per_device(h, reinterpret_cast<const void*>(prec_apply_kernel))) {
         const int mx = (2 * PREC_MAX_M * PREC_MAX_M + 6 * PREC_MAX_M + 5 * 32) * (int)sizeof(double);
         RPBD_CU(h, cudaFuncSetAttribute(prec_build_kernel<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
         RPBD_CU(h, cudaFuncSetAttribute(prec_build_kernel<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx));
@@ -337,7 +336,6 @@ int precond_build_impl(rpbd_handle* h, int64_t nb, int nper, const double* r, co
         const int mx2 = (PREC_MAX_M * PREC_MAX_M + 7 * PREC_MAX_M) * (int)sizeof(double);
         RPBD_CU(h, cudaFuncSetAttribute(prec_apply_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx2));
         RPBD_CU(h, cudaFuncSetAttribute(prec_saddle_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, mx2));
-        attr = true;
     }
     RPBD_CU(h, cudaMemsetAsync(h->dev_flag, 0, sizeof(int), st));
     const double Lx = h->p.Lx, Ly = h->p.Ly;

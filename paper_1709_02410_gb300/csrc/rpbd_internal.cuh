@@ -126,11 +126,29 @@ struct rpbd_handle {
     int sym_variant[3] = {-1, -1, -1};
     rpbd::SymPlan sym_plan;     // work list of the one-home symmetric kernel (128-blob home tiles)
     int use_packed = 1;         // k <= 4 with the wall: the packed two-homes-per-thread symmetric kernel
+    // failure-path test (RPBD_OPT_TEST_STALL): the pair kernels leave their
+    // first source stage's barrier without a copy, so its bounded wait runs
+    // out after a short limit and the kernel reports RPBD_TIMEOUT
+    int test_stall = 0;
 };
 
 namespace rpbd {
 
 int set_error(rpbd_handle* h, int code, const std::string& msg);
+// true the first time it is called for (h's device, key), false afterwards;
+// guards per-device one-time settings such as a kernel's shared-memory limit
+bool once_per_device(rpbd_handle* h, const void* key);
+// wait limit (SM clock cycles) and first-stage skip of the pair kernels'
+// source ring: ~2 s normally; a short limit with the skip under the
+// failure-path test option
+struct RingTest {
+    long long limit;
+    int skip_first;
+};
+inline RingTest ring_test(const rpbd_handle* h)
+{
+    return h->test_stall ? RingTest{200000LL, 1} : RingTest{4000000000LL, 0};
+}
 // library-wide count of kernel launches (read by rpbd_launch_count)
 void count_launch();
 // pair-kernel timing records (rpbd_profile_*)

@@ -120,12 +120,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity)
                  : "memory");
     return ok != 0;
 }
-__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity)
+// bounded wait: `limit` SM clock cycles at most (default ~2 s); false on timeout
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long limit = 4000000000LL)
 {
     if (mbar_try_wait(bar, parity)) return true;
     const long long t0 = clock64();
     while (!mbar_try_wait(bar, parity))
-        if (clock64() - t0 > 4000000000LL) return false;
+        if (clock64() - t0 > limit) return false;
     return true;
 }
 
@@ -186,7 +187,7 @@ __device__ __forceinline__ void load_rec(const float* rj, float& xh, float& yh, 
 template <int K, bool WALL, bool PER, int UNR, int MINB>
 __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__ rec, int64_t n, int64_t n_pad,
                                                  const SymItem* __restrict__ items, int n_home_tiles, PairConst<float> pc,
-                                                 float* __restrict__ partial, int* __restrict__ err_flag)
+                                                 float* __restrict__ partial, int* __restrict__ err_flag, RingTest rt)
 {
     constexpr int LEN = Rec<K>::LEN;
     constexpr uint32_t TILE_BYTES = VT * LEN * sizeof(float);
@@ -207,8 +208,8 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0)
-        for (int s = 0; s < NST && s < it.ntile; ++s) {
+    if (tid == 0)  // (failure-path test: stage 0 gets no copy, so its wait runs out)
+        for (int s = rt.skip_first ? 1 : 0; s < NST && s < it.ntile; ++s) {
             mbar_expect_tx(&bar[s], TILE_BYTES);
             tma_load_1d(stage + (size_t)s * VT * LEN, rec + ((size_t)it.v0 + (size_t)s * VT) * LEN, TILE_BYTES, &bar[s]);
         }
@@ -222,7 +223,7 @@ __global__ void __launch_bounds__(HT, MINB) sym_kernel(const float* __restrict__
     bool bad = false;
     for (; t < it.ntile; ++t) {
         const int s = t % NST;
-        const bool ok = mbar_wait_bounded(&bar[s], (t / NST) & 1);
+        const bool ok = mbar_wait_bounded(&bar[s], (t / NST) & 1, rt.limit);
         const float* st = stage + (size_t)s * VT * LEN;
         if (ok && diag) {
             // one direction, all lanes on the same source (broadcast reads)
@@ -480,11 +481,12 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     // variant -1: the measured default per K (k <= 2: unroll 4; otherwise unroll 2)
     const int sv = h->sym_variant[sym_class(K)];
     const int var = sv >= 0 ? sv : (K <= 2 ? 3 : 0);
+    const RingTest rt = ring_test(h);
     switch (var) {  // tuning variants: (visitor-loop unroll, min CTAs per SM), see SymVar
-    case 1: sym_kernel<K, WALL, PER, SymVar<K, 1>::UNR, SymVar<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
-    case 2: sym_kernel<K, WALL, PER, SymVar<K, 2>::UNR, SymVar<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
-    case 3: sym_kernel<K, WALL, PER, SymVar<K, 3>::UNR, SymVar<K, 3>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
-    default: sym_kernel<K, WALL, PER, SymVar<K, 0>::UNR, SymVar<K, 0>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag); break;
+    case 1: sym_kernel<K, WALL, PER, SymVar<K, 1>::UNR, SymVar<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
+    case 2: sym_kernel<K, WALL, PER, SymVar<K, 2>::UNR, SymVar<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
+    case 3: sym_kernel<K, WALL, PER, SymVar<K, 3>::UNR, SymVar<K, 3>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
+    default: sym_kernel<K, WALL, PER, SymVar<K, 0>::UNR, SymVar<K, 0>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
     }
     count_launch();
     if (h->profile) prof_end(h, st, (K <= 2 && !PER) ? 4 /* symmetric, factored */ : 3 /* symmetric */, K,
@@ -674,7 +676,7 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
                                                   int64_t n, int64_t n_pad, int n_home_tiles,
                                                   const SymSys* __restrict__ sys, const int* __restrict__ active,
                                                   float Lx, float Ly, float* __restrict__ partial,
-                                                  int* __restrict__ err_flag)
+                                                  int* __restrict__ err_flag, RingTest rt)
 {
     constexpr int LEN = Rec2<K>::LEN;
     constexpr uint32_t TILE_BYTES = VT * LEN * sizeof(float);
@@ -700,8 +702,8 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
         fence_mbar_init();
     }
     __syncthreads();
-    if (tid == 0)
-        for (int s = 0; s < NST && s < it.ntile; ++s) {
+    if (tid == 0)  // (failure-path test: stage 0 gets no copy, so its wait runs out)
+        for (int s = rt.skip_first ? 1 : 0; s < NST && s < it.ntile; ++s) {
             mbar_expect_tx(&bar[s], TILE_BYTES);
             tma_load_1d(stage + (size_t)s * VT * LEN, rec + ((size_t)it.v0 + (size_t)s * VT) * LEN, TILE_BYTES, &bar[s]);
         }
@@ -732,7 +734,7 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
     bool bad = false;
     for (; t < it.ntile; ++t) {
         const int s = t % NST;
-        const bool ok = mbar_wait_bounded(&bar[s], (t / NST) & 1);
+        const bool ok = mbar_wait_bounded(&bar[s], (t / NST) & 1, rt.limit);
         const float* st = stage + (size_t)s * VT * LEN;
         if (ok && diag) {
             // one direction, every lane on the same source (broadcast reads)
@@ -995,7 +997,7 @@ static int get_plan2(rpbd_handle* h, int n_sys, const int64_t* off, Sym2Plan** o
 // pseudo-periodic cell (single systems only)
 template <int K, bool PER, class In, class Out>
 static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, const In* F, Out* U, int k,
-                const int* active, Buf b_rec, Buf b_part, Buf b_seg, cudaStream_t st)
+                const int* active, Buf b_rec, Buf b_scale, Buf b_part, Buf b_seg, cudaStream_t st)
 {
     constexpr int LEN = Rec2<K>::LEN;
     const int64_t n_tot = off[n_sys];
@@ -1007,7 +1009,7 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     float* partial;
     double* segsum;
     RPBD_TRY(ensure_t(h, b_rec, (size_t)pl->rec_end * LEN, &rec));
-    RPBD_TRY(ensure_t(h, n_sys == 1 ? BUF_SCALE : BUF_BSCALE, (size_t)n_tot, &scale));
+    RPBD_TRY(ensure_t(h, b_scale, (size_t)n_tot, &scale));
     RPBD_TRY(ensure_t(h, b_part, (size_t)pl->part_rows * 3 * K, &partial));
     RPBD_TRY(ensure_t(h, b_seg, (size_t)std::max<int64_t>(1, pl->seg_rows) * 3 * K, &segsum));
     pack2_kernel<K, In><<<(unsigned)((pl->rec_end + 255) / 256), 256, 0, st>>>(
@@ -1022,20 +1024,21 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     const int ni = pl->n_items;
     const int64_t n1 = pl->sys[0].n, np1 = pl->sys[0].n_pad;
     const int T1 = pl->sys[0].T;
+    const RingTest rt = ring_test(h);
     const int var = sv >= 0 ? sv : 2;  // tuning variants (unroll, min CTAs per SM), see Sym2Var; -1: variant 2,
                                        // the one the autotuner picks for k = 1 and 2 at 65,535 blobs
     if (n_sys > 1) {  // batches: the default variant
         if constexpr (!PER)
             sym2_kernel<K, false, Sym2Var<K, 2>::UNR, Sym2Var<K, 2>::MINB, true>
-                <<<ni, HT, smem, st>>>(rec, items, 0, 0, 0, sys, active, Lxa, Lya, partial, h->dev_flag);
+                <<<ni, HT, smem, st>>>(rec, items, 0, 0, 0, sys, active, Lxa, Lya, partial, h->dev_flag, rt);
         else
             return set_error(h, RPBD_BAD_ARG, "packed symmetric kernel: batches are open in x, y");
     } else {
         switch (var) {
-        case 1: sym2_kernel<K, PER, Sym2Var<K, 1, PER>::UNR, Sym2Var<K, 1, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag); break;
-        case 2: sym2_kernel<K, PER, Sym2Var<K, 2, PER>::UNR, Sym2Var<K, 2, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag); break;
-        case 3: sym2_kernel<K, PER, Sym2Var<K, 3, PER>::UNR, Sym2Var<K, 3, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag); break;
-        default: sym2_kernel<K, PER, Sym2Var<K, 0, PER>::UNR, Sym2Var<K, 0, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag); break;
+        case 1: sym2_kernel<K, PER, Sym2Var<K, 1, PER>::UNR, Sym2Var<K, 1, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag, rt); break;
+        case 2: sym2_kernel<K, PER, Sym2Var<K, 2, PER>::UNR, Sym2Var<K, 2, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag, rt); break;
+        case 3: sym2_kernel<K, PER, Sym2Var<K, 3, PER>::UNR, Sym2Var<K, 3, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag, rt); break;
+        default: sym2_kernel<K, PER, Sym2Var<K, 0, PER>::UNR, Sym2Var<K, 0, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag, rt); break;
         }
     }
     count_launch();
@@ -1060,7 +1063,7 @@ template <int K, bool PER, class In, class Out>
 static int run2(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, int k, cudaStream_t st)
 {
     const int64_t off[2] = {0, n};
-    return run2<K, PER>(h, 1, off, r, F, U, k, nullptr, BUF_PACK, BUF_PARTIAL, BUF_SYM_SEG, st);
+    return run2<K, PER>(h, 1, off, r, F, U, k, nullptr, BUF_PACK, BUF_SCALE, BUF_PARTIAL, BUF_SYM_SEG, st);
 }
 
 }  // namespace sym
@@ -1093,9 +1096,9 @@ template <class In, class Out>
 static int sym_batched_dispatch(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, const In* F, Out* U,
                                 int k, const int* active, cudaStream_t st)
 {
-    if (k <= 1) return sym::run2<1, false>(h, n_sys, off, r, F, U, k, active, BUF_BPACK, BUF_BPARTIAL, BUF_BSEG, st);
-    if (k <= 2) return sym::run2<2, false>(h, n_sys, off, r, F, U, k, active, BUF_BPACK, BUF_BPARTIAL, BUF_BSEG, st);
-    return sym::run2<4, false>(h, n_sys, off, r, F, U, k, active, BUF_BPACK, BUF_BPARTIAL, BUF_BSEG, st);
+    if (k <= 1) return sym::run2<1, false>(h, n_sys, off, r, F, U, k, active, BUF_BPACK, BUF_BSCALE, BUF_BPARTIAL, BUF_BSEG, st);
+    if (k <= 2) return sym::run2<2, false>(h, n_sys, off, r, F, U, k, active, BUF_BPACK, BUF_BSCALE, BUF_BPARTIAL, BUF_BSEG, st);
+    return sym::run2<4, false>(h, n_sys, off, r, F, U, k, active, BUF_BPACK, BUF_BSCALE, BUF_BPARTIAL, BUF_BSEG, st);
 }
 
 int sym_batched_apply_impl(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, const void* F, void* U,

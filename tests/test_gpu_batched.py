@@ -89,3 +89,28 @@ def test_batched_lanczos_matches_oracle(use_graph, variant):
         assert abs(iters[s] - it) <= 1
         assert rel2(out[:, sl], ref) <= 1e-4
         assert rel2(U[:, sl], om.apply(rr, F[:, sl], prm)) <= 1e-5
+
+
+def test_graph_replay_after_the_single_system_workspace_grows():
+    """A captured one-system batched Lanczos keeps working after an ordinary
+    matvec on a larger suspension has regrown the handle's single-system
+    buffers: the batched path owns its own buffers (and the graph cache checks
+    them), so the replay reads no freed memory and matches the eager run."""
+    systems, rs, off, r = batch([20], seed=3)
+    h = handle_for(systems[0])
+    h.set_batch_variant(4)
+    rd = to_dev(r)
+    h.precond_build(15, rd, to_dev(systems[0].q))
+    W = to_dev(synth.gaussian(14, (3, r.shape[1])))
+    F = to_dev(synth.gaussian(15, (3, r.shape[1])))
+    ref, Uref, it_ref = h.lanczos_sqrt_apply_batched(off, rd, W, tol=1e-5, max_iter=60, use_graph=False, F=F)
+    ref, Uref = ref.clone(), Uref.clone()
+    h.lanczos_sqrt_apply_batched(off, rd, W, tol=1e-5, max_iter=60, use_graph=True, F=F)  # capture
+    big = synth.boomerang_suspension(400, 60.0, 9)
+    rb = to_dev(rigid.blob_positions(big.q, big.theta, big.shape))
+    for k in (1, 2, 16):  # every single-system buffer grows past the batch's size
+        h.mobility_apply(rb, to_dev(synth.gaussian(16 + k, (k, 3, big.n), np.float32), torch.float32))
+    out, U, it = h.lanczos_sqrt_apply_batched(off, rd, W, tol=1e-5, max_iter=60, use_graph=True, F=F)
+    assert it == it_ref
+    assert rel2(out.cpu().numpy(), ref.cpu().numpy()) <= 1e-13
+    assert rel2(U.cpu().numpy(), Uref.cpu().numpy()) <= 1e-13

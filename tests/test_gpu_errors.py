@@ -2,6 +2,8 @@
 non-finite positions in the synchronising calls return RPBD_BAD_INPUT, an
 unconverged Lanczos run returns RPBD_NOT_CONVERGED with its last iterate, and
 the handle stays usable after every error."""
+import ctypes as C
+
 import numpy as np
 import pytest
 import torch
@@ -29,9 +31,12 @@ def _still_works(h, s, r):
 def test_matvec_argument_checks():
     s, h, r = _setup()
     F = torch.zeros((17, 3, s.n), dtype=torch.float32, device=DEV)
-    with pytest.raises(RpbdError, match="bad argument"):
-        h.mobility_apply(to_dev(r), F)  # k = 17 > 16
-    # null pointers through the raw C entry point
+    with pytest.raises(RpbdError, match="F: expected shape"):
+        h.mobility_apply(to_dev(r), F)  # k = 17 > 16, caught by the binding
+    # the library's own checks: k out of range, null pointers
+    st = h.lib.rpbd_mobility_apply(h.h, s.n, C.c_void_p(to_dev(r).data_ptr()), C.c_void_p(F.data_ptr()),
+                                   C.c_void_p(F.data_ptr()), 17, F32, None)
+    assert st == -1 and b"k must be" in h.lib.rpbd_last_error(h.h)
     st = h.lib.rpbd_mobility_apply(h.h, s.n, None, None, None, 1, F64, None)
     assert st == -1 and b"null" in h.lib.rpbd_last_error(h.h)
     _still_works(h, s, r)
@@ -40,9 +45,16 @@ def test_matvec_argument_checks():
 def test_batched_argument_checks():
     s, h, r = _setup()
     F = torch.zeros((1, 3, s.n), dtype=torch.float32, device=DEV)
+    rd = to_dev(r)
     for off in ([0, 1000, 900, s.n], [5, s.n]):  # decreasing; not starting at 0
-        with pytest.raises(RpbdError, match="bad argument"):
-            h.mobility_apply_batched(np.array(off, dtype=np.int64), to_dev(r), F)
+        with pytest.raises(RpbdError, match="offsets"):
+            h.mobility_apply_batched(np.array(off, dtype=np.int64), rd, F)
+        # the library rejects them too
+        o = np.array(off, dtype=np.int64)
+        st = h.lib.rpbd_mobility_apply_batched(h.h, o.size - 1, o.ctypes.data_as(C.c_void_p),
+                                               C.c_void_p(rd.data_ptr()), C.c_void_p(F.data_ptr()),
+                                               C.c_void_p(F.data_ptr()), 1, None)
+        assert st == -1
     _still_works(h, s, r)
 
 

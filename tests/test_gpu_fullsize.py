@@ -57,6 +57,15 @@ def test_uneven_batch_471495_matvec_sampled(variant):
 
 
 def test_uneven_batch_471495_lanczos_graph():
+    """The graph-captured batched Lanczos over the whole 64-system batch.
+    Checked on ten systems: the six smallest and the four nearest 4,000
+    blobs.  Each system's answer is compared with the oracle's Lanczos run for
+    exactly the same number of iterations (a tolerance it cannot reach), so
+    both build the same Krylov space and differ only by the FP32 pair
+    arithmetic of the GPU matvec (~1e-6 per apply, the FP32 parity level,
+    propagated through a well-conditioned preconditioned operator): bound
+    1e-4.  The stopping rule itself is checked on the three smallest systems:
+    the oracle stops at tol = 1e-4 within one iteration of the GPU."""
     systems, rs, off, r = _batch()
     h = handle_for(systems[0])
     rd = to_dev(r)
@@ -69,13 +78,19 @@ def test_uneven_batch_471495_lanczos_graph():
     out, U = out.cpu().numpy(), U.cpu().numpy()
     h.close()
     assert all(1 <= it <= 60 for it in iters)
-    for s in np.argsort([rr.shape[1] for rr in rs])[:3]:  # the three smallest systems
+    sizes = np.array([rr.shape[1] for rr in rs])
+    order = np.argsort(sizes)
+    near4k = [s for s in np.argsort(np.abs(sizes - 4000)) if s not in order[:6]][:4]
+    for rank, s in enumerate(list(order[:6]) + near4k):
         sy, rr = systems[s], rs[s]
         sl = slice(off[s], off[s + 1])
         prm = oracle_params(sy)
         pc = precond.BlockPrecond(rr, sy.q, sy.nper, prm)
         G = lambda v: pc.Linv_apply(om.apply(rr, pc.LinvT_apply(v), prm))
-        y, it, _ = krylov.lanczos_sqrt(G, W[:, sl], 1e-4, 60)
-        assert abs(iters[s] - it) <= 1
-        assert rel2(out[:, sl], pc.L_apply(y)) <= 1e-3
-        assert rel2(U[:, sl], om.apply(rr, F[:, sl], prm)) <= 1e-5
+        y, it, _ = krylov.lanczos_sqrt(G, W[:, sl], 0.0, iters[s])
+        assert it == iters[s]
+        assert rel2(out[:, sl], pc.L_apply(y)) <= 1e-4, s
+        assert rel2(U[:, sl], om.apply(rr, F[:, sl], prm)) <= 1e-5, s
+        if rank < 3:
+            _, it_tol, _ = krylov.lanczos_sqrt(G, W[:, sl], 1e-4, 60)
+            assert abs(iters[s] - it_tol) <= 1, s

@@ -7,13 +7,17 @@ keeps its scratch in a fixed device array compiled into the library.  This
 test calls it through the C ABI twice in a row, with different inputs and
 right-hand-side counts, and checks each result against the ordinary
 workspace-based rpbd_mobility_apply within the FP32 parity tolerance
-(relative 2-norm error <= 1e-5).  It also checks the size limit."""
+(relative 2-norm error <= 1e-5) and, on sampled rows, against the FP64
+oracle.  A third call with the same sizes must leave the device's free memory
+exactly as it was (nothing allocated, nothing freed).  It also checks the
+size limit."""
 import ctypes as C
 
 import numpy as np
 import pytest
 import torch
 
+from oracle import mobility as om
 from paper_1709_02410_gb300 import Handle, _native, synth
 
 from gpu_util import DEV, positions, rel2, to_dev
@@ -31,11 +35,14 @@ def _call(lib, prm, r, F, U, k, n=None):
 def test_noalloc_matches_workspace_path_twice():
     lib = _native.load()
     s = synth.c2_blobs_16384()           # 16,380 blobs, just under the 16,384 limit
-    r = to_dev(positions(s))
+    rh = positions(s)
+    r = to_dev(rh)
     prm = _native.Params(synth.ETA, s.a, synth.KT, 1, 1e-3)
     h = Handle(synth.ETA, s.a, synth.KT)
+    rows = np.random.default_rng(7).choice(s.n, 16, replace=False)
     for k, seed in ((16, 101), (3, 202)):
-        F = to_dev(synth.gaussian(seed, (k, 3, s.n), np.float32), torch.float32)
+        Fh = synth.gaussian(seed, (k, 3, s.n), np.float32)
+        F = to_dev(Fh, torch.float32)
         U = torch.full_like(F, float("nan"))
         assert _call(lib, prm, r, F, U, k) == 0
         ref = h.mobility_apply(r, F)
@@ -44,6 +51,26 @@ def test_noalloc_matches_workspace_path_twice():
         assert np.isfinite(U).all()
         for m in range(k):
             assert rel2(U[m], ref[m]) <= 1e-5
+        orc = om.apply(rh, Fh[:2].astype(np.float64), om.Params(synth.ETA, s.a), rows=rows)
+        assert rel2(U[:2][:, :, rows], orc) <= 1e-5
+
+
+def test_noalloc_allocates_nothing():
+    lib = _native.load()
+    s = synth.boomerang_suspension(300, 40.0, 8)
+    r = to_dev(positions(s))
+    prm = _native.Params(synth.ETA, s.a, synth.KT, 1, 1e-3)
+    F = to_dev(synth.gaussian(303, (4, 3, s.n), np.float32), torch.float32)
+    U = torch.empty_like(F)
+    assert _call(lib, prm, r, F, U, 4) == 0   # the first call may load the kernels' code
+    torch.cuda.synchronize()
+    U1 = U.clone()
+    free0, _ = torch.cuda.mem_get_info()
+    assert _call(lib, prm, r, F, U, 4) == 0
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert torch.equal(U, U1)  # deterministic: the same inputs give the same bits
 
 
 def test_noalloc_rejects_oversize():
