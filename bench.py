@@ -33,15 +33,16 @@ UNIT = "pairs/s"
 NB, NPER = 4369, 15
 N = NB * NPER
 K_RHS = 16
-F_GEOM = 76                  # algorithmic flops of one pair block (FMA = 2, rsqrt = 1)
+# algorithmic flops of one pair block (FMA = 2, rsqrt = 1): 3 for the separation r_i - r_j, 14 for
+# the free-space coefficients, 50 for the wall part, 12 to assemble the nine entries
+F_GEOM = 79
 FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x max SM clock
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/pair_kernel_f32_k16_boomerangs_65535.md, profiles/sym_kernel_f32_k*_boomerangs_65535.md);
 # None when not captured
-NCU_TRAFFIC = {"f32_k16": 22067968 + 343998464, "f32symf_k1": 4396544 + 55015168,
-               "f32symf_k2": 8545280 + 168197888}
+NCU_TRAFFIC = {}
 # FMA-pipe activity (sm__pipe_fma_cycles_active) from the same captures
-NCU_FMA_PIPE = {"f32_k16": 0.781, "f32symf_k1": 0.761, "f32symf_k2": 0.739}
+NCU_FMA_PIPE = {}
 
 
 F_ASSEMBLY = 12             # flops of forming the 9 entries from the block's 5 scalars
@@ -606,13 +607,24 @@ def measure_rollers(dev, T, steps=5):
     it3 = checked(*h.step_ts(shape, q, th, forces, sp3), 100)
     e1.record()
     torch.cuda.synchronize()
-    return {"workload": "rollers_196608: 16384 x 12-blob rollers, phi = 0.4", "n_blobs": s.n, "steps": steps,
+    # the same suspension placed purely at random (rollers interpenetrating), for comparison
+    so = synth.c3_rollers_196608(overlap=True)
+    qo, tho = T(so.q), T(so.theta)
+    e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e2.record()
+    ito = checked(*h.step_ts(shape, qo, tho, forces, sp(200)), 200)
+    e3.record()
+    torch.cuda.synchronize()
+    return {"workload": "rollers_196608: 16384 x 12-blob rollers, phi = 0.4, hard-sphere placement (centres >= 2 R_h)",
+            "n_blobs": s.n, "steps": steps,
             "s_per_step": t, "s_per_step_each": ts, "steps_per_s": 1.0 / t,
             "iterations_rfd_lanczos_pred_corr": its, "matvecs_per_step": mv,
             "gmres_tol": 1e-6, "lanczos_tol": 1e-4, "dt": 0.008, "dtype": "f32 pairs, f64 Krylov",
             "status": "every timed step converged (status 0)",
             "paper_tolerances_1e-3": {"iterations_rfd_lanczos_pred_corr": it3,
-                                      "matvecs_per_step": sum(it3) + 2, "s_per_step": e0.elapsed_time(e1) / 1e3}}
+                                      "matvecs_per_step": sum(it3) + 2, "s_per_step": e0.elapsed_time(e1) / 1e3},
+            "random_overlapping_placement": {"iterations_rfd_lanczos_pred_corr": ito, "matvecs_per_step": sum(ito) + 2,
+                                             "s_per_step": e2.elapsed_time(e3) / 1e3}}
 
 
 # ---------------------------------------------------------------------------

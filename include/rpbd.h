@@ -362,8 +362,10 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
  * (M_ji = M_ij^T, Sec. 2.1); 0: the one-direction kernel for every k.  Sets
  * every right-hand-side class (see rpbd_autotune). */
 #define RPBD_OPT_SYMMETRIC 1
-/* -1 (default): per-k default; 0..3: loop-unroll / occupancy variant of the
- * symmetric kernel, for every right-hand-side class. */
+/* -1 (default): per-k default; 0..5: loop-unroll / occupancy variant of the
+ * symmetric kernel, for every right-hand-side class (4, 5: the packed kernel
+ * with four home blobs per thread; the one-home kernel has 0..3 and runs 4, 5
+ * as 0). */
 #define RPBD_OPT_SYM_VARIANT 2
 /* value != 0 (default): with the wall (open or periodic cell), symmetric
  * matvecs (k <= 4) use the packed kernel (two home blobs per thread, both
@@ -386,6 +388,18 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
  * return RPBD_TIMEOUT.  The kernel-only calls then return garbage without a
  * status.  For tests of the error path only; set it back to 0 afterwards. */
 #define RPBD_OPT_TEST_STALL 5
+/* value != 0 (default 0): FP32 matvecs of one system with the wall form each
+ * pair block with the direct-minus-image differences written without
+ * cancellation (1/r - 1/|R| = 4 zi zj / (r |R| (r + |R|)) and the matching
+ * cubic), so every block keeps FP32 relative accuracy (~1e-7) at any
+ * separation; the default form loses digits in proportion to
+ * |R|^2 / (zi zj) (~1e-3 relative for a block 700 a away), which the matvec's
+ * rows do not show because such blocks are tiny.  Runs the packed symmetric
+ * kernel for every k (groups of up to four right-hand sides), about 9%
+ * slower per launch; RPBD_BAD_ARG when packing is off or n is past the
+ * symmetric kernel's memory limit.  Batched and adjoint calls keep the
+ * default form. */
+#define RPBD_OPT_FARFIELD 6
 int rpbd_set_option(rpbd_handle* h, int option, int value);
 
 /* Times the FP32 matvec kernels on n blobs at r (k right-hand sides, zero

@@ -265,10 +265,11 @@ int rpbd_set_option(rpbd_handle* h, int option, int value)
         h->batch_variant = value;
         return RPBD_OK;
     case RPBD_OPT_SYM_VARIANT:
-        if (value < -1 || value > 3) return set_error(h, RPBD_BAD_ARG, "symmetric variant must be -1..3");
+        if (value < -1 || value > 5) return set_error(h, RPBD_BAD_ARG, "symmetric variant must be -1..5");
         for (int c = 0; c < 3; ++c) h->sym_variant[c] = value;
         return RPBD_OK;
     case RPBD_OPT_TEST_STALL: h->test_stall = value != 0; return RPBD_OK;
+    case RPBD_OPT_FARFIELD: h->far_field = value != 0; return RPBD_OK;
     default: return set_error(h, RPBD_BAD_ARG, "unknown option");
     }
 }
@@ -319,8 +320,10 @@ int rpbd_autotune(rpbd_handle* h, int64_t n, const double* r, int k, double* bes
     cudaEvent_t e0, e1;
     RPBD_CU(h, cudaEventCreate(&e0));
     RPBD_CU(h, cudaEventCreate(&e1));
-    // candidates: one-direction kernel (-1) and, for k <= 4, the symmetric variants 0..3
-    const int ncand = k <= 4 ? 5 : 1;
+    // candidates: one-direction kernel (-1) and, for k <= 4, the symmetric variants (0..5 of the
+    // packed kernel with the wall, 0..3 of the one-home kernel otherwise)
+    const int nsym = (h->use_packed && h->p.wall) ? 6 : 4;
+    const int ncand = k <= 4 ? 1 + nsym : 1;
     double best = 1e300;
     int best_c = -1;
     const bool prof = h->profile;

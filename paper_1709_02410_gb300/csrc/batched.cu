@@ -376,7 +376,7 @@ __global__ void __launch_bounds__(BT) bpair2_kernel(const float* __restrict__ re
                     const float2 zj = make_float2(p2.x, p2.y);
                     const float2 dz = fma2(m1, zj, zi);
                     float2 al, be, gx, gz, mzz;
-                    pair_factors_x2(dx, dy, dz, zi, zj, pc, al, be, gx, gz, mzz);
+                    pair_factors_x2<false>(dx, dy, dz, zi, zj, pc, al, be, gx, gz, mzz);
                     // forces F(m, c) at float index 10 + 2 (3m + c) of the record
 #pragma unroll
                     for (int m = 0; m < K; ++m) {

@@ -487,6 +487,21 @@ int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* 
     const double np_ = (double)(n + 255);
     const double sym_bytes =
         (np_ / 256.0 + np_ / 2048.0 + 2.0 * np_ / 4096.0 + 4.0) * 3.0 * (k <= 2 ? k : 4) * np_ * 4.0;
+    if (dtype == RPBD_F32 && h->p.wall && h->far_field) {
+        // cancellation-free far field: the packed symmetric kernel, up to four
+        // right-hand sides per launch
+        if (!h->use_packed || sym_bytes > 16.0 * (1ull << 30))
+            return set_error(h, RPBD_BAD_ARG,
+                             "far-field mode needs the packed symmetric kernel (packing on, n within its memory limit)");
+        const size_t esz = io_double ? sizeof(double) : sizeof(float);
+        for (int m0 = 0; m0 < k; m0 += 4) {
+            const int kc = k - m0 < 4 ? k - m0 : 4;
+            const size_t off = (size_t)m0 * 3 * (size_t)n * esz;
+            RPBD_TRY(sym_apply_impl(h, n, r, static_cast<const char*>(F) + off, static_cast<char*>(U) + off, kc,
+                                    io_double, st));
+        }
+        return RPBD_OK;
+    }
     if (dtype == RPBD_F32 && k <= 4 && h->use_sym[sym_class(k)] && sym_bytes <= 16.0 * (1ull << 30))
         return sym_apply_impl(h, n, r, F, U, k, io_double, st);
     // one direction with the wall in the open cell: the packed tile (two

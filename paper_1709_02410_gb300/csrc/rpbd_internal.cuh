@@ -130,6 +130,9 @@ struct rpbd_handle {
     // first source stage's barrier without a copy, so its bounded wait runs
     // out after a short limit and the kernel reports RPBD_TIMEOUT
     int test_stall = 0;
+    // RPBD_OPT_FARFIELD: single-system FP32 matvecs with the wall form every
+    // block with the cancellation-free direct-minus-image differences
+    int far_field = 0;
 };
 
 namespace rpbd {

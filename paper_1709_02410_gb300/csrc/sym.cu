@@ -610,13 +610,13 @@ __device__ __forceinline__ void load_rec2(const float* st, int j, float2& xh, fl
 
 // Both directions (BOTH) or the home direction only, for one pair separation
 // in packed form: acc += M f (visitor forces f), vacc += M^T hf (home forces).
-template <int K, bool BOTH>
+template <int K, bool BOTH, bool FAR>
 __device__ __forceinline__ void pair_apply2(float2 dx, float2 dy, float2 dz, float2 hz, float2 zj,
                                             const PairConstX2& pc, const float2* f, const float2* hf, float2* acc,
                                             float2* vacc)
 {
     float2 al, be, gx, gz, mzz;
-    pair_factors_x2(dx, dy, dz, hz, zj, pc, al, be, gx, gz, mzz);
+    pair_factors_x2<FAR>(dx, dy, dz, hz, zj, pc, al, be, gx, gz, mzz);
 #pragma unroll
     for (int m = 0; m < K; ++m) {
         const float2 fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
@@ -638,13 +638,13 @@ __device__ __forceinline__ void pair_apply2(float2 dx, float2 dy, float2 dz, flo
 
 // pair_apply2 summed over the minimum image and its 8 nearest periodic images
 // in x, y (Sec. 4.2); Lx, Ly in units of a
-template <int K, bool BOTH, bool PER>
+template <int K, bool BOTH, bool PER, bool FAR>
 __device__ __forceinline__ void pair_apply2_images(float2 dx, float2 dy, float2 dz, float2 hz, float2 zj,
                                                    const PairConstX2& pc, float Lx, float Ly, const float2* f,
                                                    const float2* hf, float2* acc, float2* vacc)
 {
     if constexpr (!PER) {
-        pair_apply2<K, BOTH>(dx, dy, dz, hz, zj, pc, f, hf, acc, vacc);
+        pair_apply2<K, BOTH, FAR>(dx, dy, dz, hz, zj, pc, f, hf, acc, vacc);
     } else {
         const float iLx = 1.0f / Lx, iLy = 1.0f / Ly;
         dx = make_float2(dx.x - Lx * rintf(dx.x * iLx), dx.y - Lx * rintf(dx.y * iLx));
@@ -653,37 +653,57 @@ __device__ __forceinline__ void pair_apply2_images(float2 dx, float2 dy, float2 
         for (int ia = -1; ia <= 1; ++ia)
 #pragma unroll
             for (int ib = -1; ib <= 1; ++ib)
-                pair_apply2<K, BOTH>(add2(dx, bc2((float)ia * Lx)), add2(dy, bc2((float)ib * Ly)), dz, hz, zj, pc,
+                pair_apply2<K, BOTH, FAR>(add2(dx, bc2((float)ia * Lx)), add2(dy, bc2((float)ib * Ly)), dz, hz, zj, pc,
                                      f, hf, acc, vacc);
     }
 }
 
-// tuning variants (visitor-loop unroll, min CTAs per SM); chosen per K so no variant spills
+// tuning variants (visitor-loop unroll, min CTAs per SM, packed home pairs
+// per thread); chosen per K so no variant spills.  Variants 0-3: two home
+// blobs per thread (128 threads); 4-5: four (64 threads).
 template <int K, int V, bool PER = false>
 struct Sym2Var {
-    static constexpr int UNR = V == 0 ? 2 : (V == 1 ? 1 : (V == 2 ? 2 : 4));
-    static constexpr int MINB0 = K == 1 ? (V == 1 ? 6 : (V == 2 ? 5 : 4))
-                                        : (K == 2 ? (V == 2 ? 3 : 4) : (V == 1 ? 3 : 2));
+    static constexpr int HP = V >= 4 ? 2 : 1;
+    static constexpr int UNR = V == 0 ? 2 : (V == 1 ? 1 : (V == 2 ? 2 : (V == 3 ? 4 : (V == 4 ? 1 : 2))));
+    static constexpr int MINB0 = V >= 4 ? (K == 1 ? 8 : (K == 2 ? 6 : 4))
+                                        : (K == 1 ? (V == 1 ? 6 : (V == 2 ? 5 : 4))
+                                                  : (K == 2 ? (V == 2 ? 3 : 4) : (V == 1 ? 3 : 2)));
     // the image loop of the periodic cell needs more registers
-    static constexpr int MINB = PER ? (MINB0 > (K == 1 ? 4 : 2) ? (K == 1 ? 4 : 2) : MINB0) : MINB0;
+    static constexpr int PCAP = HP == 1 ? (K == 1 ? 4 : 2) : (K == 1 ? 6 : 4);
+    static constexpr int MINB = PER ? (MINB0 > PCAP ? PCAP : MINB0) : MINB0;
+    static constexpr int NT = HT2 / (2 * HP);  // threads per CTA
+    static size_t smem(int len)
+    {
+        return (size_t)NST * VT * len * sizeof(float) + 2 * (NT / 32) * VT * 3 * K * sizeof(float) +
+               NST * sizeof(uint64_t);
+    }
 };
 
 // BATCH: items of several systems (layout per item from sys[], converged
 // systems skipped); otherwise one system of n blobs, n_pad records and
-// n_home_tiles home tiles, given as arguments.
-template <int K, bool PER, int UNR, int MINB, bool BATCH>
-__global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict__ rec, const SymItem* __restrict__ items,
-                                                  int64_t n, int64_t n_pad, int n_home_tiles,
-                                                  const SymSys* __restrict__ sys, const int* __restrict__ active,
-                                                  float Lx, float Ly, float* __restrict__ partial,
-                                                  int* __restrict__ err_flag, RingTest rt)
+// n_home_tiles home tiles, given as arguments.  HP: packed home pairs per
+// thread (1: two home blobs per thread, 128 threads; 2: four home blobs per
+// thread, 64 threads, so each visitor record loaded and each visitor sum
+// handed on serves twice the pairs).  Warp w owns homes [64 HP w, 64 HP (w+1))
+// of the tile; pair p of a thread holds homes 64 HP w + 64 p + lane (.x) and
+// that + 32 (.y).
+template <int K, bool PER, int UNR, int MINB, bool BATCH, int HP = 1, bool FAR = false>
+__global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float* __restrict__ rec,
+                                                              const SymItem* __restrict__ items, int64_t n,
+                                                              int64_t n_pad, int n_home_tiles,
+                                                              const SymSys* __restrict__ sys,
+                                                              const int* __restrict__ active, float Lx, float Ly,
+                                                              float* __restrict__ partial, int* __restrict__ err_flag,
+                                                              RingTest rt)
 {
+    constexpr int NT = HT2 / (2 * HP);  // threads
+    constexpr int NW = NT / 32;          // warps
     constexpr int LEN = Rec2<K>::LEN;
     constexpr uint32_t TILE_BYTES = VT * LEN * sizeof(float);
     extern __shared__ __align__(128) unsigned char smem_raw[];
     float* stage = reinterpret_cast<float*>(smem_raw);
-    float* red = reinterpret_cast<float*>(smem_raw + NST * TILE_BYTES);  // [2 buffers][4 warps][VT][3K]
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + NST * TILE_BYTES + 2 * 4 * VT * 3 * K * sizeof(float));
+    float* red = reinterpret_cast<float*>(smem_raw + NST * TILE_BYTES);  // [2 buffers][NW warps][VT][3K]
+    uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + NST * TILE_BYTES + 2 * NW * VT * 3 * K * sizeof(float));
     const SymItem it = items[blockIdx.x];
     if constexpr (BATCH)
         if (active && !active[it.sys]) return;  // a converged system: nothing in flight yet
@@ -692,7 +712,7 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
     const SymSys* const sd = sys + it.sys;
     const bool diag = it.slot == 0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t i0 = (int64_t)it.home * HT2 + warp * 64 + lane, i1 = i0 + 32;  // home records
+    const int64_t ib = (int64_t)it.home * HT2 + warp * 64 * HP + lane;  // home record of pair 0, lane .x
     const PairConstX2 pc = PairConstX2::make_unit();
     const float2 m1 = pc.m1;
 
@@ -707,28 +727,31 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
             mbar_expect_tx(&bar[s], TILE_BYTES);
             tma_load_1d(stage + (size_t)s * VT * LEN, rec + ((size_t)it.v0 + (size_t)s * VT) * LEN, TILE_BYTES, &bar[s]);
         }
-    float2 hxh, hyh, hxl, hyl, hz, hf[3 * K];
-    {
-        // value m of home blob i0 in .x, of i1 in .y
+    float2 hxh[HP], hyh[HP], hxl[HP], hyl[HP], hz[HP], hf[HP][3 * K];
+#pragma unroll
+    for (int p = 0; p < HP; ++p) {
+        // value m of home blob ib + 64 p in .x, of ib + 64 p + 32 in .y
         float2 hv[2 * Rec2<K>::NCH];
 #pragma unroll
         for (int c = 0; c < Rec2<K>::NCH; ++c) {
-            const float4 a = *reinterpret_cast<const float4*>(rec + rec2_off(i0, c, LEN));
-            const float4 b = *reinterpret_cast<const float4*>(rec + rec2_off(i1, c, LEN));
+            const float4 a = *reinterpret_cast<const float4*>(rec + rec2_off(ib + 64 * p, c, LEN));
+            const float4 b = *reinterpret_cast<const float4*>(rec + rec2_off(ib + 64 * p + 32, c, LEN));
             hv[2 * c] = make_float2(a.x, b.x);
             hv[2 * c + 1] = make_float2(a.z, b.z);
         }
-        hxh = hv[0];
-        hyh = hv[1];
-        hxl = hv[2];
-        hyl = hv[3];
-        hz = hv[4];
+        hxh[p] = hv[0];
+        hyh[p] = hv[1];
+        hxl[p] = hv[2];
+        hyl[p] = hv[3];
+        hz[p] = hv[4];
 #pragma unroll
-        for (int q = 0; q < 3 * K; ++q) hf[q] = hv[5 + q];
+        for (int q = 0; q < 3 * K; ++q) hf[p][q] = hv[5 + q];
     }
-    float2 acc[3 * K];
+    float2 acc[HP][3 * K];
 #pragma unroll
-    for (int q = 0; q < 3 * K; ++q) acc[q] = make_float2(0.0f, 0.0f);
+    for (int p = 0; p < HP; ++p)
+#pragma unroll
+        for (int q = 0; q < 3 * K; ++q) acc[p][q] = make_float2(0.0f, 0.0f);
 
     int t = 0;
     bool bad = false;
@@ -742,10 +765,14 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
             for (int jj = 0; jj < VT; ++jj) {
                 float2 xh, yh, xl, yl, zj, f[3 * K];
                 load_rec2<K>(st, jj, xh, yh, xl, yl, zj, f);
-                const float2 dx = add2(fma2(m1, xh, hxh), fma2(m1, xl, hxl));
-                const float2 dy = add2(fma2(m1, yh, hyh), fma2(m1, yl, hyl));
-                const float2 dz = fma2(m1, zj, hz);
-                pair_apply2_images<K, false, PER>(dx, dy, dz, hz, zj, pc, Lx, Ly, f, hf, acc, nullptr);
+#pragma unroll
+                for (int p = 0; p < HP; ++p) {
+                    const float2 dx = add2(fma2(m1, xh, hxh[p]), fma2(m1, xl, hxl[p]));
+                    const float2 dy = add2(fma2(m1, yh, hyh[p]), fma2(m1, yl, hyl[p]));
+                    const float2 dz = fma2(m1, zj, hz[p]);
+                    pair_apply2_images<K, false, PER, FAR>(dx, dy, dz, hz[p], zj, pc, Lx, Ly, f, hf[p], acc[p],
+                                                           nullptr);
+                }
             }
         } else if (ok) {
             // both directions; lane l takes visitor (step + l) mod 32
@@ -757,10 +784,13 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
                 const int v = (step + lane) & (VT - 1);
                 float2 xh, yh, xl, yl, zj, f[3 * K];
                 load_rec2<K>(st, v, xh, yh, xl, yl, zj, f);
-                const float2 dx = add2(fma2(m1, xh, hxh), fma2(m1, xl, hxl));
-                const float2 dy = add2(fma2(m1, yh, hyh), fma2(m1, yl, hyl));
-                const float2 dz = fma2(m1, zj, hz);
-                pair_apply2_images<K, true, PER>(dx, dy, dz, hz, zj, pc, Lx, Ly, f, hf, acc, vacc);
+#pragma unroll
+                for (int p = 0; p < HP; ++p) {
+                    const float2 dx = add2(fma2(m1, xh, hxh[p]), fma2(m1, xl, hxl[p]));
+                    const float2 dy = add2(fma2(m1, yh, hyh[p]), fma2(m1, yl, hyl[p]));
+                    const float2 dz = fma2(m1, zj, hz[p]);
+                    pair_apply2_images<K, true, PER, FAR>(dx, dy, dz, hz[p], zj, pc, Lx, Ly, f, hf[p], acc[p], vacc);
+                }
                 // hand the visitor sums to the lane that takes that visitor next
 #pragma unroll
                 for (int q = 0; q < 3 * K; ++q) {
@@ -768,8 +798,8 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
                     vacc[q].y = __shfl_sync(0xffffffffu, vacc[q].y, (lane + 1) & 31);
                 }
             }
-            // lane l now holds visitor l's sums over this warp's 64 homes
-            float* rb = red + (t & 1) * (4 * VT * 3 * K);  // double-buffered: one barrier per tile
+            // lane l now holds visitor l's sums over this warp's 64 HP homes
+            float* rb = red + (t & 1) * (NW * VT * 3 * K);  // double-buffered: one barrier per tile
 #pragma unroll
             for (int q = 0; q < 3 * K; ++q) rb[(warp * VT + lane) * 3 * K + q] = vacc[q].x + vacc[q].y;
         }
@@ -778,18 +808,19 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
             break;
         }
         if (!diag) {
-            const float* rb = red + (t & 1) * (4 * VT * 3 * K);
+            const float* rb = red + (t & 1) * (NW * VT * 3 * K);
             const int64_t sB = BATCH ? __ldg(&sd->B) : 0, sn = BATCH ? __ldg(&sd->n) : n;
             const int64_t sn_pad = BATCH ? __ldg(&sd->n_pad) : n_pad;
             float* const part = BATCH ? partial + (int64_t)3 * K * __ldg(&sd->P1) : partial;  // the system's partials
             const int64_t hloc = (int64_t)it.home - sB / HT2;  // home tile within the system
             const int64_t vbase = (int64_t)it.v0 + (int64_t)t * VT - sB;
-            for (int e = tid; e < VT * 3 * K; e += HT) {
+            for (int e = tid; e < VT * 3 * K; e += NT) {
                 const int vl = e / (3 * K), q = e % (3 * K);
                 const int64_t vg = vbase + vl;
                 if (vg < sn) {
-                    const float sum = rb[(0 * VT + vl) * 3 * K + q] + rb[(1 * VT + vl) * 3 * K + q] +
-                                      rb[(2 * VT + vl) * 3 * K + q] + rb[(3 * VT + vl) * 3 * K + q];
+                    float sum = rb[vl * 3 * K + q];
+#pragma unroll
+                    for (int w = 1; w < NW; ++w) sum += rb[(w * VT + vl) * 3 * K + q];
                     part[(hloc * 3 * K + q) * sn_pad + vg] = sum;
                 }
             }
@@ -812,11 +843,14 @@ __global__ void __launch_bounds__(HT, MINB) sym2_kernel(const float* __restrict_
     const int64_t sn_pad = BATCH ? __ldg(&sd->n_pad) : n_pad;
     float* const part = BATCH ? partial + (int64_t)3 * K * __ldg(&sd->P1) : partial;
     const int slot = (BATCH ? __ldg(&sd->T) : n_home_tiles) + it.slot;
-    const int64_t l0 = i0 - sB, l1 = i1 - sB;  // the home blobs within the system
 #pragma unroll
-    for (int q = 0; q < 3 * K; ++q) {
-        if (l0 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l0] = acc[q].x;
-        if (l1 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l1] = acc[q].y;
+    for (int p = 0; p < HP; ++p) {
+        const int64_t l0 = ib + 64 * p - sB, l1 = l0 + 32;  // the home blobs within the system
+#pragma unroll
+        for (int q = 0; q < 3 * K; ++q) {
+            if (l0 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l0] = acc[p][q].x;
+            if (l1 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l1] = acc[p][q].y;
+        }
     }
 }
 
@@ -1015,7 +1049,6 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     pack2_kernel<K, In><<<(unsigned)((pl->rec_end + 255) / 256), 256, 0, st>>>(
         n_sys, pl->d_sys, pl->rec_end, n_tot, k, r, F, h->p.a, h->p.wall, h->p.s_min, active, rec, scale);
     count_launch();
-    const size_t smem = (size_t)NST * VT * LEN * sizeof(float) + 2 * 4 * VT * 3 * K * sizeof(float) + NST * sizeof(uint64_t);
     const float Lxa = (float)(h->p.Lx / h->p.a), Lya = (float)(h->p.Ly / h->p.a);  // periodic cell in units of a
     if (h->profile) prof_begin(h, st);
     const int sv = h->sym_variant[sym_class(K)];
@@ -1025,22 +1058,34 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     const int64_t n1 = pl->sys[0].n, np1 = pl->sys[0].n_pad;
     const int T1 = pl->sys[0].T;
     const RingTest rt = ring_test(h);
-    const int var = sv >= 0 ? sv : 2;  // tuning variants (unroll, min CTAs per SM), see Sym2Var; -1: variant 2,
-                                       // the one the autotuner picks for k = 1 and 2 at 65,535 blobs
+    const int var = sv >= 0 ? sv : 2;  // tuning variants, see Sym2Var; -1: variant 2, the one the
+                                       // autotuner picks for k = 1 and 2 at 65,535 blobs
+#define RPBD_SYM2_LAUNCH(V)                                                                                    \
+    sym2_kernel<K, PER, Sym2Var<K, V, PER>::UNR, Sym2Var<K, V, PER>::MINB, false, Sym2Var<K, V, PER>::HP>     \
+        <<<ni, Sym2Var<K, V, PER>::NT, Sym2Var<K, V, PER>::smem(LEN), st>>>(rec, items, n1, np1, T1, sys, nullptr, \
+                                                                            Lxa, Lya, partial, h->dev_flag, rt)
     if (n_sys > 1) {  // batches: the default variant
         if constexpr (!PER)
             sym2_kernel<K, false, Sym2Var<K, 2>::UNR, Sym2Var<K, 2>::MINB, true>
-                <<<ni, HT, smem, st>>>(rec, items, 0, 0, 0, sys, active, Lxa, Lya, partial, h->dev_flag, rt);
+                <<<ni, Sym2Var<K, 2>::NT, Sym2Var<K, 2>::smem(LEN), st>>>(rec, items, 0, 0, 0, sys, active, Lxa,
+                                                                          Lya, partial, h->dev_flag, rt);
         else
             return set_error(h, RPBD_BAD_ARG, "packed symmetric kernel: batches are open in x, y");
+    } else if (h->far_field) {  // the cancellation-free block: one compiled variant
+        sym2_kernel<K, PER, Sym2Var<K, 2, PER>::UNR, Sym2Var<K, 2, PER>::MINB, false, 1, true>
+            <<<ni, Sym2Var<K, 2, PER>::NT, Sym2Var<K, 2, PER>::smem(LEN), st>>>(rec, items, n1, np1, T1, sys, nullptr,
+                                                                                Lxa, Lya, partial, h->dev_flag, rt);
     } else {
         switch (var) {
-        case 1: sym2_kernel<K, PER, Sym2Var<K, 1, PER>::UNR, Sym2Var<K, 1, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag, rt); break;
-        case 2: sym2_kernel<K, PER, Sym2Var<K, 2, PER>::UNR, Sym2Var<K, 2, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag, rt); break;
-        case 3: sym2_kernel<K, PER, Sym2Var<K, 3, PER>::UNR, Sym2Var<K, 3, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag, rt); break;
-        default: sym2_kernel<K, PER, Sym2Var<K, 0, PER>::UNR, Sym2Var<K, 0, PER>::MINB, false><<<ni, HT, smem, st>>>(rec, items, n1, np1, T1, sys, nullptr, Lxa, Lya, partial, h->dev_flag, rt); break;
+        case 1: RPBD_SYM2_LAUNCH(1); break;
+        case 2: RPBD_SYM2_LAUNCH(2); break;
+        case 3: RPBD_SYM2_LAUNCH(3); break;
+        case 4: RPBD_SYM2_LAUNCH(4); break;
+        case 5: RPBD_SYM2_LAUNCH(5); break;
+        default: RPBD_SYM2_LAUNCH(0); break;
         }
     }
+#undef RPBD_SYM2_LAUNCH
     count_launch();
     if (h->profile) {
         double pairs = 0.0;

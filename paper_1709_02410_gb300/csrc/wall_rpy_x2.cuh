@@ -57,6 +57,13 @@ __device__ __forceinline__ void overlap_fix(float r2, float rinv, const PairCons
     }
 }
 
+__device__ __forceinline__ float rcp_approx(float x)
+{
+    float y;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
 // alpha, beta, gx, gz, Mzz of two pairs (see pair_factors for the formulas).
 // With a = 1 the wall scalars are polynomials in w = 1/|R|^2, y = e_z^2 and
 // u = zi zj, regrouped in Horner form around shared factors:
@@ -66,6 +73,20 @@ __device__ __forceinline__ void overlap_fix(float r2, float rinv, const PairCons
 //   Z     = w (y (20w - 4 - h1) - 8/3 w)
 // so Rinv A and Rinv Z become v (...) with v = Rinv w, and no term is formed
 // twice.  zi6 = 6 zi and m2zi = -2 zi depend on the target only.
+//
+// FAR = true: the direct and image terms are combined without cancellation.
+// Far from the target (|d| >> z) the free-space coefficients c1 ~ 1/r and
+// c2 ~ 1/r^3 and their image counterparts 1/|R|, 1/|R|^3 agree in their
+// leading digits while the block itself is only O(zi zj / |R|^3), so the
+// default form loses FP32 digits in proportion to |R|^2 / (zi zj) (a block at
+// 700 a carries a relative error of ~1e-3; the matvec's rows barely notice,
+// since such blocks are tiny).  With |R|^2 - r^2 = 4 zi zj exactly,
+//   1/r - 1/R     = 4 zi zj / (r R (r + R)),
+//   1/r^3 - 1/R^3 = (1/r - 1/R) (1/r^2 + 1/(r R) + 1/R^2),
+// so c1 - 1/R and c2 - 1/R^3 are formed from these differences and every
+// block keeps FP32 relative accuracy at any distance, for ~8 more packed
+// operations and one reciprocal per pair.
+template <bool FAR = false>
 __device__ __forceinline__ void pair_factors_x2(float2 dx, float2 dy, float2 dz, float2 zi, float2 zj,
                                                 const PairConstX2& c, float2& alpha, float2& beta, float2& gx,
                                                 float2& gz, float2& Mzz)
@@ -75,12 +96,6 @@ __device__ __forceinline__ void pair_factors_x2(float2 dx, float2 dy, float2 dz,
     const float2 rinv = make_float2(rsqrtf(r2.x), rsqrtf(r2.y));
     const float2 rinv2 = mul2(rinv, rinv);
     const float2 rinv3 = mul2(rinv, rinv2);
-    float2 c1 = fma2(c.a23, rinv3, rinv);
-    float2 c2 = mul2(rinv3, fma2(c.m2a2, rinv2, c.one));
-    if (r2.x < c.four_a2 || r2.y < c.four_a2) {
-        overlap_fix(r2.x, rinv.x, c, c1.x, c2.x);
-        overlap_fix(r2.y, rinv.y, c, c1.y, c2.y);
-    }
     const float2 zi6 = mul2(bc2(6.0f), zi);
     const float2 m2zi = mul2(bc2(-2.0f), zi);
     // wall part
@@ -90,16 +105,49 @@ __device__ __forceinline__ void pair_factors_x2(float2 dx, float2 dy, float2 dz,
     const float2 Rinv = make_float2(rsqrtf(R2.x), rsqrtf(R2.y));
     const float2 w = mul2(Rinv, Rinv);
     const float2 v = mul2(Rinv, w);
+    float2 X1, c2v;  // c1 - 1/R and c2 - 1/R^3
+    if constexpr (FAR) {
+        const float2 rR = mul2(rinv, Rinv);
+        const float2 sR = fma2(r2, rinv, mul2(R2, Rinv));  // r + R
+        const float2 isR = make_float2(rcp_approx(sR.x), rcp_approx(sR.y));
+        const float2 D1 = mul2(mul2(mul2(mul2(bc2(4.0f), zi), zj), rR), isR);
+        const float2 D3 = mul2(D1, add2(add2(rinv2, w), rR));
+        X1 = fma2(c.a23, rinv3, D1);
+        c2v = fma2(c.m2a2, mul2(rinv3, rinv2), D3);
+        if (r2.x < c.four_a2 || r2.y < c.four_a2) {
+            // overlapping or self pairs: the plain coefficients (no cancellation here)
+            if (r2.x < c.four_a2) {
+                float c1x = 0.0f, c2x = 0.0f;
+                overlap_fix(r2.x, rinv.x, c, c1x, c2x);
+                X1.x = c1x - Rinv.x;
+                c2v.x = c2x - v.x;
+            }
+            if (r2.y < c.four_a2) {
+                float c1y = 0.0f, c2y = 0.0f;
+                overlap_fix(r2.y, rinv.y, c, c1y, c2y);
+                X1.y = c1y - Rinv.y;
+                c2v.y = c2y - v.y;
+            }
+        }
+    } else {
+        float2 c1 = fma2(c.a23, rinv3, rinv);
+        float2 c2 = mul2(rinv3, fma2(c.m2a2, rinv2, c.one));
+        if (r2.x < c.four_a2 || r2.y < c.four_a2) {
+            overlap_fix(r2.x, rinv.x, c, c1.x, c2.x);
+            overlap_fix(r2.y, rinv.y, c, c1.y, c2.y);
+        }
+        X1 = fma2(c.m1, Rinv, c1);
+        c2v = fma2(c.m1, v, c2);
+    }
     const float2 y = mul2(q, w);  // e_z^2
     const float2 a1 = fma2(bc2(-10.0f), y, fma2(zi6, zj, bc2(2.0f)));
     const float2 b1 = fma2(bc2(70.0f / 3.0f), y, bc2(-10.0f / 3.0f));
     const float2 h1 = fma2(w, b1, a1);
     const float2 Bp = mul2(w, h1);  // B + 1
-    const float2 c2v = fma2(c.m1, v, c2);
     beta = fma2(v, Bp, c2v);
     const float2 eA = fma2(m2zi, zj, fma2(bc2(2.0f), y, bc2(-2.0f / 3.0f)));
     const float2 iA = fma2(w, fma2(bc2(-10.0f / 3.0f), y, c.a23), eA);
-    alpha = fma2(v, iA, fma2(c.m1, Rinv, c1));
+    alpha = fma2(v, iA, X1);
     const float2 Pn = fma2(mul2(bc2(-20.0f / 3.0f), w), w, Bp);  // -P
     const float2 base = mul2(dz, c2v);
     const float2 vRPn = mul2(mul2(v, Rz), Pn);

@@ -109,11 +109,43 @@ def boomerang_suspension(nb: int, box: float, seed: int, a: float = A_BOOMERANG,
     return Suspension(q, th, shape, a, box, "boomerang", dict(lift=lift))
 
 
+def _separate(q: np.ndarray, box: float, dmin: float, rng: np.random.Generator, tries: int = 10000) -> np.ndarray:
+    """Placement only: random sequential addition -- each body in turn keeps
+    its height and re-draws x, y until its centre is at least dmin (3-D
+    distance) from every body already placed (a cell list of side >= dmin)."""
+    q = q.copy()
+    nc = max(1, int(box // dmin))
+    cell = box / nc
+    grid = {}
+    for i in range(q.shape[0]):
+        for _ in range(tries):
+            cx, cy = min(int(q[i, 0] // cell), nc - 1), min(int(q[i, 1] // cell), nc - 1)
+            clash = False
+            for dx in (-1, 0, 1):
+                for dy in (-1, 0, 1):
+                    for j in grid.get((cx + dx, cy + dy), ()):
+                        if np.sum((q[i] - q[j]) ** 2) < dmin * dmin:
+                            clash = True
+                            break
+                    if clash:
+                        break
+                if clash:
+                    break
+            if not clash:
+                grid.setdefault((cx, cy), []).append(i)
+                break
+            q[i, :2] = rng.uniform(0.0, box, size=2)
+        else:
+            raise RuntimeError("could not place the bodies without overlap")
+    return q
+
+
 def roller_suspension(nb: int, phi: float, seed: int, a: float = A_ROLLER,
-                      rh: float = RH_ROLLER, lift: bool = True) -> Suspension:
+                      rh: float = RH_ROLLER, lift: bool = True, overlap: bool = True) -> Suspension:
     """nb 12-blob rollers at in-plane packing fraction phi = n pi rh^2;
     height a + Exp(1.5 a) (lowest blob), or rh + Exp(1.5 a) for the centre
-    when lift=False."""
+    when lift=False.  overlap=False re-draws x, y until no two roller centres
+    are closer than 2 rh (hard spheres of the hydrodynamic radius)."""
     box = float(np.sqrt(nb * np.pi * rh * rh / phi))
     rng = np.random.default_rng(seed)
     q = np.empty((nb, 3))
@@ -122,7 +154,9 @@ def roller_suspension(nb: int, phi: float, seed: int, a: float = A_ROLLER,
     th = random_quaternions(rng, nb)
     shape = icosahedron_shape(a)
     q[:, 2] = (a + e - _lowest_offset(th, shape)) if lift else (rh + e)
-    return Suspension(q, th, shape, a, box, "roller", dict(lift=lift))
+    if not overlap:
+        q = _separate(q, box, 2.0 * rh, rng)
+    return Suspension(q, th, shape, a, box, "roller", dict(lift=lift, overlap=overlap))
 
 
 def gaussian(seed: int, shape, dtype=np.float64) -> np.ndarray:
@@ -146,9 +180,11 @@ def c2_blobs_16384(seed: int = 2) -> Suspension:
     return boomerang_suspension(1092, 40.0 * np.sqrt(1092 / 128), seed)
 
 
-def c3_rollers_196608(seed: int = 3, nb: int = 16384) -> Suspension:
-    """16,384 rollers x 12 = 196,608 blobs at phi = 0.4."""
-    return roller_suspension(nb, 0.4, seed)
+def c3_rollers_196608(seed: int = 3, nb: int = 16384, overlap: bool = False) -> Suspension:
+    """16,384 rollers x 12 = 196,608 blobs at phi = 0.4, placed as hard
+    spheres of the hydrodynamic radius (no two centres closer than 2 R_h);
+    overlap=True keeps the purely random placement."""
+    return roller_suspension(nb, 0.4, seed, overlap=overlap)
 
 
 def c4_uneven_batch(seed: int = 4, n_sys: int = 64):

@@ -138,10 +138,10 @@ def test_autotune_picks_a_correct_kernel():
     F = synth.gaussian(60, (1, 3, s.n), np.float32)
     h = handle_for(s)
     choice, ms = h.autotune(to_dev(r), 1)
-    assert 0 <= choice <= 4 and ms > 0
+    assert 0 <= choice <= 6 and ms > 0
     U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
     assert rel2(U, om.apply(r, F.astype(np.float64), oracle_params(s))) <= 1e-5
-    for v in range(4):
+    for v in range(6):
         h.set_symmetric(True)
         h.set_sym_variant(v)
         U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
@@ -155,7 +155,7 @@ def test_autotune_classes_are_independent():
     h = handle_for(s)
     c1, _ = h.autotune(to_dev(r), 1)
     c2, _ = h.autotune(to_dev(r), 2)
-    assert 0 <= c1 <= 4 and 0 <= c2 <= 4
+    assert 0 <= c1 <= 6 and 0 <= c2 <= 6
     for k in (1, 2, 3):
         F = synth.gaussian(61 + k, (k, 3, s.n), np.float32)
         U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
@@ -173,19 +173,22 @@ def test_fma_peak_probe():
     assert 0.0 < f64 < f32
 
 
+@pytest.mark.parametrize("variant", [-1, 4, 5])
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
 @pytest.mark.parametrize("n", [1, 31, 255, 256, 257, 700, 2049, 4500])
-def test_f32_packed_symmetric_kernel(k, n):
-    """The packed symmetric kernel (two homes per thread, 256-blob home tiles,
-    two-wide FP32 arithmetic) against the oracle and against the one-home
-    symmetric kernel: sizes below, at and across the 256-blob tile and the
-    2048-visitor chunk, blobs overlapping each other and the wall."""
+def test_f32_packed_symmetric_kernel(k, n, variant):
+    """The packed symmetric kernel (256-blob home tiles, two-wide FP32
+    arithmetic; two home blobs per thread by default, four in variants 4 and
+    5) against the oracle and against the one-home symmetric kernel: sizes
+    below, at and across the 256-blob tile and the 2048-visitor chunk, blobs
+    overlapping each other and the wall."""
     rng = np.random.default_rng(11 * n + k)
     box = max(2.0, np.sqrt(n))
     r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
     F = rng.standard_normal((k, 3, n)).astype(np.float32)
     s = synth.c0_boomerangs_1920()
     h = handle_for(s)
+    h.set_sym_variant(variant)
     Up = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
     h.set_packed(False)
     Us = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
@@ -195,7 +198,7 @@ def test_f32_packed_symmetric_kernel(k, n):
 
 
 @pytest.mark.parametrize("k", [1, 2, 4])
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_f32_packed_variants(variant, k):
     s = synth.c0_boomerangs_1920()
     r = positions(s)

@@ -32,15 +32,18 @@ def test_periodic_f64(nb):
 
 
 @pytest.mark.parametrize("k", [1, 2, 4, 16])
-@pytest.mark.parametrize("sym,packed", [(True, True), (True, False), (False, False)])
-def test_periodic_f32(k, sym, packed):
-    """FP32 in the periodic cell: packed symmetric kernel (default for k <= 4),
-    one-home symmetric kernel, one-direction kernel"""
+@pytest.mark.parametrize("sym,packed,variant", [(True, True, -1), (True, True, 4), (True, True, 5), (True, False, -1),
+                                                (False, False, -1)])
+def test_periodic_f32(k, sym, packed, variant):
+    """FP32 in the periodic cell: packed symmetric kernel (default for k <= 4;
+    variants 4, 5: four home blobs per thread), one-home symmetric kernel,
+    one-direction kernel"""
     s, r, prm = cell(40, 52)
     F = synth.gaussian(53 + k, (k, 3, s.n), np.float32)
     h = handle(s)
     h.set_symmetric(sym)
     h.set_packed(packed)
+    h.set_sym_variant(variant)
     U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
     assert rel2(U, om.apply(r, F.astype(np.float64), prm)) <= 1e-5
 
