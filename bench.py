@@ -422,6 +422,16 @@ def measure_matvecs(h, r, F16, U16, T, time_launch):
         extra[f"f32_k{kk}"] = dict(s_per_launch=tk, pairs_per_s=N * N / tk, matvecs_per_s=kk / tk,
                                    kernel="symmetric" if sym else "one-direction",
                                    tflops=N * N * f_pair(kk, sym, sym and kk <= 2) / tk / 1e12)
+    # the packed symmetric kernel with FP64 atomic accumulation per blob (memory O(n)) and
+    # with the cancellation-free far field, k = 1 and 2
+    for mode, setter in (("atomic", h.set_sym_atomic), ("far_field", h.set_far_field)):
+        setter(True)
+        for kk in (1, 2):
+            Fk = F1f if kk == 1 else T(synth.gaussian(212, (2, 3, N)), torch.float32)
+            Uk = torch.empty_like(Fk)
+            tk = time_launch(lambda: h.mobility_apply(r, Fk, out=Uk), 3)
+            extra[f"f32_k{kk}_symmetric_{mode}"] = dict(s_per_launch=tk, pairs_per_s=N * N / tk)
+        setter(False)
     extra["f64_k1"] = dict(s_per_launch=t64, pairs_per_s=N * N / t64)
     extra["speedup_f32_k16_vs_f64_k1_per_rhs"] = (t64 * K_RHS) / t16
     extra["speedup_f32_k1_vs_f64_k1"] = t64 / t32k1

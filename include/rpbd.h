@@ -400,6 +400,15 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
  * symmetric kernel's memory limit.  Batched and adjoint calls keep the
  * default form. */
 #define RPBD_OPT_FARFIELD 6
+/* value != 0 (default 0): the packed symmetric kernel of a single system adds
+ * every visitor and home contribution into one FP64 accumulator per blob with
+ * atomic adds (device memory 3k n doubles) instead of writing one FP32 partial
+ * per (256-blob home tile, blob) and reducing them in a fixed order (memory
+ * about n^2 / 256 * 3k floats).  The sum order then varies from run to run
+ * (results agree to FP64 rounding, not bit for bit).  Past 16 GiB of partials
+ * the library uses this mode whatever the option says (for example k = 2 at
+ * 500,000 blobs).  Not combined with RPBD_OPT_FARFIELD. */
+#define RPBD_OPT_SYM_ATOMIC 7
 int rpbd_set_option(rpbd_handle* h, int option, int value);
 
 /* Times the FP32 matvec kernels on n blobs at r (k right-hand sides, zero

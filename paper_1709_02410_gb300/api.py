@@ -112,6 +112,11 @@ class Handle:
         direct-minus-image differences (FP32 accuracy at any separation, ~9% slower)."""
         self._check(self.lib.rpbd_set_option(self.h, 6, int(bool(on))), "set_option")
 
+    def set_sym_atomic(self, on: bool):
+        """Packed symmetric kernel: FP64 atomic accumulation per blob (memory O(n), sum order not
+        fixed) instead of per-home-tile partials (memory O(n^2), deterministic)."""
+        self._check(self.lib.rpbd_set_option(self.h, 7, int(bool(on))), "set_option")
+
     def measure_fma_peak(self, dtype=F32):
         """FMA throughput of this GPU in TFLOP/s (FMA = 2), measured by the library."""
         v = C.c_double()

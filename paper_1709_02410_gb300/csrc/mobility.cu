@@ -482,8 +482,9 @@ int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* 
     if (!r || !F || !U) return set_error(h, RPBD_BAD_ARG, "null pointer");
     // the symmetric kernels keep one visitor partial per (home tile, blob): about
     // n^2 / 256 * 3k floats, plus FP64 segment sums (one per 16 home tiles);
-    // beyond 16 GiB (n of order a million) the one-direction kernel, whose
-    // partials grow as n^2 / 2048, takes over
+    // beyond 16 GiB the packed kernel accumulates in FP64 atomics per blob
+    // instead, and the one-home kernel gives way to the one-direction kernel,
+    // whose partials grow as n^2 / 2048
     const double np_ = (double)(n + 255);
     const double sym_bytes =
         (np_ / 256.0 + np_ / 2048.0 + 2.0 * np_ / 4096.0 + 4.0) * 3.0 * (k <= 2 ? k : 4) * np_ * 4.0;
@@ -502,7 +503,10 @@ int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* 
         }
         return RPBD_OK;
     }
-    if (dtype == RPBD_F32 && k <= 4 && h->use_sym[sym_class(k)] && sym_bytes <= 16.0 * (1ull << 30))
+    // the packed symmetric kernel takes any n (past the partials' limit it sums in FP64
+    // atomics); the one-home kernel only while its partials fit
+    const bool packed_sym = h->use_packed && h->p.wall;
+    if (dtype == RPBD_F32 && k <= 4 && h->use_sym[sym_class(k)] && (packed_sym || sym_bytes <= 16.0 * (1ull << 30)))
         return sym_apply_impl(h, n, r, F, U, k, io_double, st);
     // one direction with the wall in the open cell: the packed tile (two
     // targets per thread) for k = 1, 3, 4; k = 2 keeps its own K = 2 tile

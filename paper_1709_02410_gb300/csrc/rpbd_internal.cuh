@@ -133,6 +133,9 @@ struct rpbd_handle {
     // RPBD_OPT_FARFIELD: single-system FP32 matvecs with the wall form every
     // block with the cancellation-free direct-minus-image differences
     int far_field = 0;
+    // RPBD_OPT_SYM_ATOMIC: the packed symmetric kernel of one system sums into FP64
+    // atomics per blob (memory O(n)) even when its visitor partials would fit
+    int sym_atomic = 0;
 };
 
 namespace rpbd {

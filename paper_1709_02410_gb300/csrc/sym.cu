@@ -51,10 +51,13 @@ struct Rec {
 
 // tuning variants per K: visitor-loop unroll and minimum resident CTAs per SM
 // (the latter caps registers: 65536 / (MINB * 128)); chosen so no variant spills
-template <int K, int V>
+template <int K, int V, bool PER = false>
 struct SymVar {
     static constexpr int UNR = V == 1 ? 1 : (V == 3 ? 4 : 2);
-    static constexpr int MINB = K == 1 ? (V == 2 ? 9 : 8) : (K == 2 ? (V == 2 ? 8 : 7) : (V == 2 ? 5 : 4));
+    static constexpr int MINB0 = K == 1 ? (V == 2 ? 9 : 8) : (K == 2 ? (V == 2 ? 8 : 7) : (V == 2 ? 5 : 4));
+    // the image loop of the periodic cell needs more registers
+    static constexpr int PCAP = K == 1 ? 6 : (K == 2 ? 5 : 4);
+    static constexpr int MINB = PER && MINB0 > PCAP ? PCAP : MINB0;
 };
 
 struct SymItem {
@@ -483,10 +486,10 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
     const int var = sv >= 0 ? sv : (K <= 2 ? 3 : 0);
     const RingTest rt = ring_test(h);
     switch (var) {  // tuning variants: (visitor-loop unroll, min CTAs per SM), see SymVar
-    case 1: sym_kernel<K, WALL, PER, SymVar<K, 1>::UNR, SymVar<K, 1>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
-    case 2: sym_kernel<K, WALL, PER, SymVar<K, 2>::UNR, SymVar<K, 2>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
-    case 3: sym_kernel<K, WALL, PER, SymVar<K, 3>::UNR, SymVar<K, 3>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
-    default: sym_kernel<K, WALL, PER, SymVar<K, 0>::UNR, SymVar<K, 0>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
+    case 1: sym_kernel<K, WALL, PER, SymVar<K, 1, PER>::UNR, SymVar<K, 1, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
+    case 2: sym_kernel<K, WALL, PER, SymVar<K, 2, PER>::UNR, SymVar<K, 2, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
+    case 3: sym_kernel<K, WALL, PER, SymVar<K, 3, PER>::UNR, SymVar<K, 3, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
+    default: sym_kernel<K, WALL, PER, SymVar<K, 0, PER>::UNR, SymVar<K, 0, PER>::MINB><<<n_items, HT, smem, st>>>(rec, n, n_pad, items, n_home, pc, partial, h->dev_flag, rt); break;
     }
     count_launch();
     if (h->profile) prof_end(h, st, (K <= 2 && !PER) ? 4 /* symmetric, factored */ : 3 /* symmetric */, K,
@@ -519,6 +522,8 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
 // floats) so the 32 lanes' loads of different records hit distinct banks.
 
 constexpr int HT2 = 256;  // home blobs per CTA, two per thread
+// beyond this many bytes of visitor partials a single system accumulates in FP64 atomics
+constexpr double SYM_PARTIAL_LIMIT = 16.0 * (1ull << 30);
 
 template <int K>
 struct Rec2 {
@@ -687,7 +692,7 @@ struct Sym2Var {
 // handed on serves twice the pairs).  Warp w owns homes [64 HP w, 64 HP (w+1))
 // of the tile; pair p of a thread holds homes 64 HP w + 64 p + lane (.x) and
 // that + 32 (.y).
-template <int K, bool PER, int UNR, int MINB, bool BATCH, int HP = 1, bool FAR = false>
+template <int K, bool PER, int UNR, int MINB, bool BATCH, int HP = 1, bool FAR = false, bool ATOM = false>
 __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float* __restrict__ rec,
                                                               const SymItem* __restrict__ items, int64_t n,
                                                               int64_t n_pad, int n_home_tiles,
@@ -821,7 +826,10 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
                     float sum = rb[vl * 3 * K + q];
 #pragma unroll
                     for (int w = 1; w < NW; ++w) sum += rb[(w * VT + vl) * 3 * K + q];
-                    part[(hloc * 3 * K + q) * sn_pad + vg] = sum;
+                    if constexpr (ATOM)  // one FP64 accumulator per blob and component
+                        atomicAdd(reinterpret_cast<double*>(partial) + (int64_t)q * sn_pad + vg, (double)sum);
+                    else
+                        part[(hloc * 3 * K + q) * sn_pad + vg] = sum;
                 }
             }
         }
@@ -848,8 +856,14 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
         const int64_t l0 = ib + 64 * p - sB, l1 = l0 + 32;  // the home blobs within the system
 #pragma unroll
         for (int q = 0; q < 3 * K; ++q) {
-            if (l0 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l0] = acc[p][q].x;
-            if (l1 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l1] = acc[p][q].y;
+            if constexpr (ATOM) {
+                double* a64 = reinterpret_cast<double*>(partial) + (int64_t)q * sn_pad;
+                if (l0 < sn) atomicAdd(a64 + l0, (double)acc[p][q].x);
+                if (l1 < sn) atomicAdd(a64 + l1, (double)acc[p][q].y);
+            } else {
+                if (l0 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l0] = acc[p][q].x;
+                if (l1 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l1] = acc[p][q].y;
+            }
         }
     }
 }
@@ -925,6 +939,17 @@ __global__ void reduce2_kernel(int n_sys, const SymSys* __restrict__ sys, int64_
     for (int c = 0; c < home_slots; ++c) two_sum_acc(hs, hc, pt[((int64_t)(d.T + c) * 3 * kt + q) * d.n_pad]);
     sum += two_sum_value(hs, hc);
     U[(int64_t)q * n_tot + g] = (Out)(scale[g] * inv8pieta * sum);
+}
+
+// U of one system from the FP64 accumulators of the atomic mode: scale and write
+template <class Out>
+__global__ void finish_atomic_kernel(int64_t n, int64_t n_pad, int k, const double* __restrict__ acc,
+                                     const double* __restrict__ scale, double inv8pieta, Out* __restrict__ U)
+{
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (i >= n || q >= 3 * k) return;
+    U[(int64_t)q * n + i] = (Out)(scale[i] * inv8pieta * acc[(int64_t)q * n_pad + i]);
 }
 
 }  // namespace sym
@@ -1041,11 +1066,23 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     float* rec;
     double* scale;
     float* partial;
-    double* segsum;
+    double* segsum = nullptr;
+    // one system whose visitor partials would pass SYM_PARTIAL_LIMIT bytes (or the
+    // handle asks for it): FP64 atomic accumulation per blob instead (memory O(n))
+    const bool atom = n_sys == 1 && !h->far_field &&
+                      (h->sym_atomic || (double)pl->part_rows * 3 * K * sizeof(float) > SYM_PARTIAL_LIMIT);
+    const int64_t np1a = pl->sys[0].n_pad;
     RPBD_TRY(ensure_t(h, b_rec, (size_t)pl->rec_end * LEN, &rec));
     RPBD_TRY(ensure_t(h, b_scale, (size_t)n_tot, &scale));
-    RPBD_TRY(ensure_t(h, b_part, (size_t)pl->part_rows * 3 * K, &partial));
-    RPBD_TRY(ensure_t(h, b_seg, (size_t)std::max<int64_t>(1, pl->seg_rows) * 3 * K, &segsum));
+    if (atom) {
+        double* acc64;
+        RPBD_TRY(ensure_t(h, b_part, (size_t)3 * K * np1a, &acc64));
+        RPBD_CU(h, cudaMemsetAsync(acc64, 0, sizeof(double) * 3 * K * np1a, st));
+        partial = reinterpret_cast<float*>(acc64);
+    } else {
+        RPBD_TRY(ensure_t(h, b_part, (size_t)pl->part_rows * 3 * K, &partial));
+        RPBD_TRY(ensure_t(h, b_seg, (size_t)std::max<int64_t>(1, pl->seg_rows) * 3 * K, &segsum));
+    }
     pack2_kernel<K, In><<<(unsigned)((pl->rec_end + 255) / 256), 256, 0, st>>>(
         n_sys, pl->d_sys, pl->rec_end, n_tot, k, r, F, h->p.a, h->p.wall, h->p.s_min, active, rec, scale);
     count_launch();
@@ -1071,6 +1108,10 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
                                                                           Lya, partial, h->dev_flag, rt);
         else
             return set_error(h, RPBD_BAD_ARG, "packed symmetric kernel: batches are open in x, y");
+    } else if (atom) {  // FP64 atomic accumulation: one compiled variant
+        sym2_kernel<K, PER, Sym2Var<K, 2, PER>::UNR, Sym2Var<K, 2, PER>::MINB, false, 1, false, true>
+            <<<ni, Sym2Var<K, 2, PER>::NT, Sym2Var<K, 2, PER>::smem(LEN), st>>>(rec, items, n1, np1, T1, sys, nullptr,
+                                                                                Lxa, Lya, partial, h->dev_flag, rt);
     } else if (h->far_field) {  // the cancellation-free block: one compiled variant
         sym2_kernel<K, PER, Sym2Var<K, 2, PER>::UNR, Sym2Var<K, 2, PER>::MINB, false, 1, true>
             <<<ni, Sym2Var<K, 2, PER>::NT, Sym2Var<K, 2, PER>::smem(LEN), st>>>(rec, items, n1, np1, T1, sys, nullptr,
@@ -1094,6 +1135,13 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     }
     // blocks were formed in units of a: M = M(a = 1) / a
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta * h->p.a);
+    if (atom) {
+        finish_atomic_kernel<Out><<<dim3((unsigned)((n_tot + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(
+            n_tot, np1a, k, reinterpret_cast<const double*>(partial), scale, inv8pieta, U);
+        count_launch();
+        RPBD_LAUNCH_CHECK(h);
+        return RPBD_OK;
+    }
     reduce2_visitors_kernel<K><<<dim3((unsigned)((n_tot + 255) / 256), (unsigned)pl->max_nseg), 256, 0, st>>>(
         n_sys, sys, n_tot, k, active, partial, segsum);
     count_launch();

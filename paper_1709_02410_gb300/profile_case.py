@@ -25,6 +25,9 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="the uneven batch of 64 boomerang suspensions (one batched launch; --variant: tile variant)")
     ap.add_argument("--adjoint", action="store_true", help="the FP32 adjoint instead of the matvec")
+    ap.add_argument("--atomic", action="store_true",
+                    help="packed symmetric kernel with FP64 atomic accumulation per blob")
+    ap.add_argument("--far", action="store_true", help="cancellation-free far field")
     a = ap.parse_args()
     import torch
     from . import F32, F64, Handle, synth
@@ -38,6 +41,8 @@ def main():
     h = Handle(synth.ETA, s.a, synth.KT, wall=bool(a.wall))
     h.set_symmetric(bool(a.sym))
     h.set_sym_variant(a.variant)
+    h.set_sym_atomic(a.atomic)
+    h.set_far_field(a.far)
     T = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
     r = h.blobs_from_bodies(T(s.shape), T(s.q), T(s.theta))
     dt = torch.float32 if a.dtype == "f32" else torch.float64
@@ -52,7 +57,8 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / a.reps
-    print(json.dumps({"n": s.n, "k": a.k, "dtype": a.dtype, "sym": a.sym, "variant": a.variant,
+    print(json.dumps({"n": s.n, "k": a.k, "dtype": a.dtype, "sym": a.sym, "variant": a.variant, "atomic": a.atomic,
+                      "far": a.far,
                       "s_per_launch": t, "pairs_per_s": s.n * s.n / t,
                       "matvecs_per_s": a.k / t}))
 

@@ -210,6 +210,28 @@ def test_f32_packed_variants(variant, k):
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
+@pytest.mark.parametrize("n", [1, 257, 2049, 9000])
+def test_f32_packed_symmetric_atomic_mode(k, n):
+    """The packed symmetric kernel summing into one FP64 accumulator per blob
+    (atomic adds) instead of per-home-tile partials: against the oracle, and
+    against the fixed-order reduction (both sum the same FP32 tile partials in
+    FP64 or better, so they differ by FP32 output rounding only)."""
+    rng = np.random.default_rng(13 * n + k)
+    box = max(2.0, np.sqrt(n))
+    r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
+    F = rng.standard_normal((k, 3, n)).astype(np.float32)
+    s = synth.c0_boomerangs_1920()
+    h = handle_for(s)
+    Ud = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    h.set_sym_atomic(True)
+    Ua = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    Ua64 = h.mobility_apply(to_dev(r), to_dev(F.astype(np.float64)), dtype=1).cpu().numpy()
+    Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
+    assert rel2(Ua, Uo) <= 1e-5 and rel2(Ua64, Uo) <= 1e-5
+    assert rel2(Ua, Ud) <= 1e-6
+
+
+@pytest.mark.parametrize("k", [1, 2, 3, 4])
 def test_f32_one_direction_packed_tile(k):
     """With the symmetric kernel off, k = 1, 3, 4 run on the packed tile (two
     targets per thread; one system of the batched kernel) and k = 2 on its
@@ -233,18 +255,20 @@ def test_f32_one_direction_packed_tile(k):
         assert rel2(Up, Uo) <= 1e-5 and rel2(Ud, Uo) <= 1e-5 and rel2(Uu, Uo) <= 1e-5, n
 
 
+@pytest.mark.parametrize("sym", [True, False])
 @pytest.mark.parametrize("k", [1, 2, 3])
-def test_f32_half_million_blobs_row_sampled(k):
-    """500,010 blobs (33,334 boomerangs at the same density): k = 1 keeps the
-    packed symmetric kernel (13 GB of visitor partials), k = 2 and k = 3 pass
-    the 16 GiB limit of those partials and take the one-direction kernels
-    (k = 2 its own tile, k = 3 the packed tile with K = 4); 32 sampled rows
-    against the oracle."""
+def test_f32_half_million_blobs_row_sampled(k, sym):
+    """500,010 blobs (33,334 boomerangs at the same density): the packed
+    symmetric kernel keeps its per-home-tile partials for k = 1 (13 GB) and
+    sums into FP64 atomics per blob for k = 2 and 3, whose partials would pass
+    16 GiB; with the symmetric kernel off, the one-direction kernels (k = 2 its
+    own tile, k = 1, 3 the packed tile); 32 sampled rows against the oracle."""
     nb = 33334
     s = synth.boomerang_suspension(nb, 40.0 * np.sqrt(nb / 128), 44)
     r = positions(s)
     F = synth.gaussian(45 + k, (k, 3, s.n), np.float32)
     h = handle_for(s)
+    h.set_symmetric(sym)
     U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
     rows = np.random.default_rng(46).choice(s.n, 32, replace=False)
     rows[0], rows[1] = 0, s.n - 1
