@@ -2,7 +2,8 @@
 
 Workload: 4,369 L-shaped boomerangs x 15 blobs = 65,535 blobs above a no-slip
 wall (box scaled to the 128-boomerang / 40 x 40 um density), synthetic and
-seeded.  One bench step is one pass of the whole hot path over it:
+seeded.  One bench step is one pass of the whole hot path over it (every
+step starts from the generated configuration, with its own random draws):
   * one Trapezoidal-Slip time step (Algorithm 2): blob geometry, body-block
     preconditioner, GMRES RFD solve, RFD drift D^F / D^S, preconditioned
     Lanczos M^{1/2} W, predictor and corrector GMRES solves -- FP32 pair
@@ -40,9 +41,9 @@ FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.070e9 / 1e12   # SMs x FP32 lanes x FMA x m
 # DRAM bytes (read + write) per launch from one ncu capture of the current
 # kernels (profiles/pair_kernel_f32_k16_boomerangs_65535.md, profiles/sym_kernel_f32_k*_boomerangs_65535.md);
 # None when not captured
-NCU_TRAFFIC = {}
+NCU_TRAFFIC = {"f32symf_k1": 4433920 + 55049984, "f32symf_k2": 7635968 + 166915840, "f32_k16": 21113856 + 343361792}
 # FMA-pipe activity (sm__pipe_fma_cycles_active) from the same captures
-NCU_FMA_PIPE = {}
+NCU_FMA_PIPE = {"f32symf_k1": 0.756, "f32symf_k2": 0.756, "f32_k16": 0.795}
 
 
 F_ASSEMBLY = 12             # flops of forming the 9 entries from the block's 5 scalars
@@ -168,13 +169,20 @@ def run_ours(args, rank, world, local):
     tuned2 = h.autotune(r0, 2) if not args.no_autotune else (None, None)   # the lockstep RFD + predictor solves
     fma32 = h.measure_fma_peak(P.F32)
     fma64 = h.measure_fma_peak(P.F64)
+    fma32v = h.measure_fma_peak(3)   # packed FMAs with three distinct varying register operands
 
     def sp(i):
         return StepParams(0.01, 1e-3, Lp, 1e-6, 1e-4, 300, 100, 80, P.F32, 2024 + rank, i)
 
     stats_log = []
 
-    def step(i):
+    def step(i, from_initial=True):
+        # every step advances the generated suspension (new normals per step): a trajectory
+        # without steric forces drifts toward interpenetrating bodies, which raises the solver
+        # iterations from step to step (33 -> 45 GMRES iterations over 25 steps)
+        if from_initial:
+            q.copy_(q0)
+            th.copy_(th0)
         r = h.blobs_from_bodies(shape, q, th)
         st, status = h.step_ts(shape, q, th, forces, sp(i))
         if status != 0:   # a step whose solves did not converge is not a step
@@ -234,6 +242,8 @@ def run_ours(args, rank, world, local):
     # ---- end-to-end through the public API with host buffers (same steps)
     qh = torch.empty_like(q0, device="cpu").pin_memory()
     thh = torch.empty_like(th0, device="cpu").pin_memory()
+    qo = torch.empty_like(qh).pin_memory()
+    tho = torch.empty_like(thh).pin_memory()
     Fh = F16.cpu().pin_memory()
     Uh = torch.empty_like(Fh).pin_memory()
     qh.copy_(q0.cpu())
@@ -246,9 +256,9 @@ def run_ours(args, rank, world, local):
         q.copy_(qh, non_blocking=True)
         th.copy_(thh, non_blocking=True)
         F16.copy_(Fh, non_blocking=True)
-        step(1000 + i)
-        qh.copy_(q, non_blocking=True)
-        thh.copy_(th, non_blocking=True)
+        step(1000 + i, from_initial=False)
+        qo.copy_(q, non_blocking=True)
+        tho.copy_(th, non_blocking=True)
         Uh.copy_(U16, non_blocking=True)
         torch.cuda.synchronize()
     barrier()
@@ -314,8 +324,11 @@ def run_ours(args, rank, world, local):
                     "share_of_step": d["ms"] / (t_local * 1e3),
                     "measured_fma_peak": fma32, "frac_of_measured_fma_peak": ach / fma32,
                     "ncu_fma_pipe_active": NCU_FMA_PIPE.get(name),
+                    "three_varying_operand_fma_rate": fma32v,
                     "peak_note": "peak = 152 SMs x 128 FP32 lanes x 2 x 2.070 GHz (derived); "
-                                 "measured_fma_peak = the library's FMA-chain probe on this GPU"}
+                                 "measured_fma_peak = the library's FMA-chain probe on this GPU; "
+                                 "three_varying_operand_fma_rate = the same probe when every packed FMA reads "
+                                 "three distinct varying registers (the register file's ceiling for such code)"}
         # accuracy vs the FP64 oracle on sampled rows (outside the timed region)
         acc = {}
         if extras and not args.no_oracle:
@@ -376,7 +389,7 @@ def run_ours(args, rank, world, local):
             "autotune_k1": {"choice": tuned[0], "ms_per_launch": tuned[1],
                             "legend": "0: one-direction kernel; 1 + v: symmetric kernel variant v"},
             "autotune_k2": {"choice": tuned2[0], "ms_per_launch": tuned2[1]},
-            "measured_fma_peak_tflops": {"f32": fma32, "f64": fma64},
+            "measured_fma_peak_tflops": {"f32": fma32, "f64": fma64, "f32_packed_three_varying_operands": fma32v},
             "matvec": extra,
             "rows": row_times,
             "batched_c4": batched,

@@ -423,8 +423,10 @@ int rpbd_autotune(rpbd_handle* h, int64_t n, const double* r, int k, double* bes
 
 /* Number of kernels this library has launched since it was loaded. */
 long long rpbd_launch_count(void);
-/* Measures the FMA throughput of this GPU in dtype (RPBD_F32, RPBD_F64, or 2:
- * FP32 with packed two-wide FMA instructions):
+/* Measures the FMA throughput of this GPU in dtype (RPBD_F32, RPBD_F64, 2:
+ * FP32 with packed two-wide FMA instructions, or 3: packed FMAs whose three
+ * operands are distinct varying registers -- the form the pair kernels'
+ * accumulations take, which the register file feeds more slowly):
  * one launch of independent FMA chains filling every SM, timed with CUDA
  * events on the stream; *tflops (host) receives FLOP/s / 1e12 (FMA = 2).
  * The denominator for roofline fractions of ALU-bound kernels.  Synchronises

@@ -1095,8 +1095,9 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     const int64_t n1 = pl->sys[0].n, np1 = pl->sys[0].n_pad;
     const int T1 = pl->sys[0].T;
     const RingTest rt = ring_test(h);
-    const int var = sv >= 0 ? sv : 2;  // tuning variants, see Sym2Var; -1: variant 2, the one the
-                                       // autotuner picks for k = 1 and 2 at 65,535 blobs
+    // tuning variants, see Sym2Var; -1: the autotuner's usual pick at 65,535 blobs (k = 1: variant 3,
+    // k = 2: variant 5, k = 3..4: variant 4)
+    const int var = sv >= 0 ? sv : (K == 1 ? 3 : (K == 2 ? 5 : 4));
 #define RPBD_SYM2_LAUNCH(V)                                                                                    \
     sym2_kernel<K, PER, Sym2Var<K, V, PER>::UNR, Sym2Var<K, V, PER>::MINB, false, Sym2Var<K, V, PER>::HP>     \
         <<<ni, Sym2Var<K, V, PER>::NT, Sym2Var<K, V, PER>::smem(LEN), st>>>(rec, items, n1, np1, T1, sys, nullptr, \

@@ -169,8 +169,10 @@ def test_fma_peak_probe():
     h = handle_for(synth.c0_boomerangs_1920())
     f32 = h.measure_fma_peak(F32)
     f64 = h.measure_fma_peak(F64)
+    f32v = h.measure_fma_peak(3)   # packed FMAs reading three distinct varying registers
     assert 1.0 < f32 < 1.2 * 80.55
     assert 0.0 < f64 < f32
+    assert 0.0 < f32v < f32
 
 
 @pytest.mark.parametrize("variant", [-1, 4, 5])
