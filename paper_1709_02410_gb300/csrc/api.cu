@@ -209,8 +209,8 @@ __global__ void __launch_bounds__(256) fma2_peak_kernel(int iters, float a, floa
 
 // packed FMAs whose three operands are all distinct, varying registers (no
 // immediate, no loop-invariant or repeated operand): a twelve-value tangle
-// where every step reads three different pairs, 8 FMAs per unrolled step as in
-// fma2_peak_kernel.  The register file supplies such an instruction more
+// where every step reads three different pairs, 8 packed FMAs (16 FMAs) per
+// unrolled step.  The register file supplies such an instruction more
 // slowly than one with a constant operand, which bounds kernels made of them.
 __global__ void __launch_bounds__(256) fma2_varying_kernel(int iters, float a, float b, float* __restrict__ sink)
 {
@@ -254,7 +254,10 @@ static int measure_peak(rpbd_handle* h, int iters, double* tflops, cudaStream_t 
     RPBD_CU(h, cudaEventElapsedTime(&ms, e0, e1));
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
-    const double flops = 2.0 * 8 * 16 * (double)iters * grid * 256;
+    // FMAs per unrolled step of one thread: 8 chains (scalar), 4 packed pairs, or 8 packed
+    // pairs in the varying-operand form
+    const double fmas = VARYING ? 16.0 : 8.0;
+    const double flops = 2.0 * fmas * 16 * (double)iters * grid * 256;
     *tflops = ms > 0.0f ? flops / (ms * 1e-3) / 1e12 : 0.0;
     return RPBD_OK;
 }
