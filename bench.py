@@ -434,7 +434,7 @@ def measure_matvecs(h, r, F16, U16, T, time_launch):
         sym = kk <= 4
         extra[f"f32_k{kk}"] = dict(s_per_launch=tk, pairs_per_s=N * N / tk, matvecs_per_s=kk / tk,
                                    kernel="symmetric" if sym else "one-direction",
-                                   tflops=N * N * f_pair(kk, sym, sym and kk <= 2) / tk / 1e12)
+                                   tflops=N * N * f_pair(kk, sym, sym) / tk / 1e12)  # packed: factored form
     # the packed symmetric kernel with FP64 atomic accumulation per blob (memory O(n)) and
     # with the cancellation-free far field, k = 1 and 2
     for mode, setter in (("atomic", h.set_sym_atomic), ("far_field", h.set_far_field)):
