@@ -435,9 +435,9 @@ def measure_matvecs(h, r, F16, U16, T, time_launch):
         extra[f"f32_k{kk}"] = dict(s_per_launch=tk, pairs_per_s=N * N / tk, matvecs_per_s=kk / tk,
                                    kernel="symmetric" if sym else "one-direction",
                                    tflops=N * N * f_pair(kk, sym, sym) / tk / 1e12)  # packed: factored form
-    # the packed symmetric kernel with FP64 atomic accumulation per blob (memory O(n)) and
-    # with the cancellation-free far field, k = 1 and 2
-    for mode, setter in (("atomic", h.set_sym_atomic), ("far_field", h.set_far_field)):
+    # the packed symmetric kernel with per-home-tile partials and the fixed-order reduction
+    # (instead of the fixed-point accumulation), and with the cancellation-free far field
+    for mode, setter in (("partials", h.set_sym_partials), ("far_field", h.set_far_field)):
         setter(True)
         for kk in (1, 2):
             Fk = F1f if kk == 1 else T(synth.gaussian(212, (2, 3, N)), torch.float32)

@@ -396,19 +396,20 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
  * |R|^2 / (zi zj) (~1e-3 relative for a block 700 a away), which the matvec's
  * rows do not show because such blocks are tiny.  Runs the packed symmetric
  * kernel for every k (groups of up to four right-hand sides), about 9%
- * slower per launch; RPBD_BAD_ARG when packing is off or n is past the
- * symmetric kernel's memory limit.  Batched and adjoint calls keep the
- * default form. */
+ * slower per launch; RPBD_BAD_ARG when packing is off.  Batched and adjoint
+ * calls keep the default form. */
 #define RPBD_OPT_FARFIELD 6
-/* value != 0 (default 0): the packed symmetric kernel of a single system adds
- * every visitor and home contribution into one FP64 accumulator per blob with
- * atomic adds (device memory 3k n doubles) instead of writing one FP32 partial
- * per (256-blob home tile, blob) and reducing them in a fixed order (memory
- * about n^2 / 256 * 3k floats).  The sum order then varies from run to run
- * (results agree to FP64 rounding, not bit for bit).  Past 16 GiB of partials
- * the library uses this mode whatever the option says (for example k = 2 at
- * 500,000 blobs).  Not combined with RPBD_OPT_FARFIELD. */
-#define RPBD_OPT_SYM_ATOMIC 7
+/* value != 0 (default 0): the packed symmetric kernel of a single system
+ * writes one FP32 visitor partial per (256-blob home tile, blob) and reduces
+ * them in a fixed order (memory about n^2 / 256 * 3k floats; past 16 GiB the
+ * option is ignored).  By default it accumulates in fixed point instead: every
+ * contribution to a blob's velocity is scaled by 2^S, rounded to a 64-bit
+ * integer and added atomically, one accumulator per blob and component
+ * (memory 3k n integers; S from the largest |force|, so that no sum can
+ * overflow; the rounding step is ~1e-12 of the largest possible sum).  Integer
+ * addition does not depend on its order, so both are deterministic; they
+ * differ by FP32 output rounding. */
+#define RPBD_OPT_SYM_PARTIALS 7
 int rpbd_set_option(rpbd_handle* h, int option, int value);
 
 /* Times the FP32 matvec kernels on n blobs at r (k right-hand sides, zero

@@ -112,9 +112,9 @@ class Handle:
         direct-minus-image differences (FP32 accuracy at any separation, ~9% slower)."""
         self._check(self.lib.rpbd_set_option(self.h, 6, int(bool(on))), "set_option")
 
-    def set_sym_atomic(self, on: bool):
-        """Packed symmetric kernel: FP64 atomic accumulation per blob (memory O(n), sum order not
-        fixed) instead of per-home-tile partials (memory O(n^2), deterministic)."""
+    def set_sym_partials(self, on: bool):
+        """Packed symmetric kernel of one system: per-home-tile partials with the fixed-order
+        reduction (memory O(n^2)) instead of the default fixed-point accumulation (memory O(n))."""
         self._check(self.lib.rpbd_set_option(self.h, 7, int(bool(on))), "set_option")
 
     def measure_fma_peak(self, dtype=F32):

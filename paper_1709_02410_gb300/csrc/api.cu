@@ -296,7 +296,7 @@ int rpbd_set_option(rpbd_handle* h, int option, int value)
         return RPBD_OK;
     case RPBD_OPT_TEST_STALL: h->test_stall = value != 0; return RPBD_OK;
     case RPBD_OPT_FARFIELD: h->far_field = value != 0; return RPBD_OK;
-    case RPBD_OPT_SYM_ATOMIC: h->sym_atomic = value != 0; return RPBD_OK;
+    case RPBD_OPT_SYM_PARTIALS: h->sym_partials = value != 0; return RPBD_OK;
     default: return set_error(h, RPBD_BAD_ARG, "unknown option");
     }
 }

@@ -480,20 +480,18 @@ int mobility_apply_impl(rpbd_handle* h, int64_t n, const double* r, const void* 
     if (k < 1 || k > 16) return set_error(h, RPBD_BAD_ARG, "k must be in 1..16");
     if (dtype != RPBD_F32 && dtype != RPBD_F64) return set_error(h, RPBD_BAD_ARG, "bad dtype");
     if (!r || !F || !U) return set_error(h, RPBD_BAD_ARG, "null pointer");
-    // the symmetric kernels keep one visitor partial per (home tile, blob): about
-    // n^2 / 256 * 3k floats, plus FP64 segment sums (one per 16 home tiles);
-    // beyond 16 GiB the packed kernel accumulates in FP64 atomics per blob
-    // instead, and the one-home kernel gives way to the one-direction kernel,
-    // whose partials grow as n^2 / 2048
+    // the one-home symmetric kernel keeps one visitor partial per (home tile,
+    // blob): about n^2 / 256 * 3k floats, plus FP64 segment sums (one per 16
+    // home tiles); beyond 16 GiB it gives way to the one-direction kernel, whose
+    // partials grow as n^2 / 2048.  The packed kernel accumulates in fixed
+    // point per blob (memory O(n)) and takes any n.
     const double np_ = (double)(n + 255);
     const double sym_bytes =
         (np_ / 256.0 + np_ / 2048.0 + 2.0 * np_ / 4096.0 + 4.0) * 3.0 * (k <= 2 ? k : 4) * np_ * 4.0;
     if (dtype == RPBD_F32 && h->p.wall && h->far_field) {
         // cancellation-free far field: the packed symmetric kernel, up to four
         // right-hand sides per launch
-        if (!h->use_packed || sym_bytes > 16.0 * (1ull << 30))
-            return set_error(h, RPBD_BAD_ARG,
-                             "far-field mode needs the packed symmetric kernel (packing on, n within its memory limit)");
+        if (!h->use_packed) return set_error(h, RPBD_BAD_ARG, "far-field mode needs the packed symmetric kernel");
         const size_t esz = io_double ? sizeof(double) : sizeof(float);
         for (int m0 = 0; m0 < k; m0 += 4) {
             const int kc = k - m0 < 4 ? k - m0 : 4;

@@ -133,9 +133,10 @@ struct rpbd_handle {
     // RPBD_OPT_FARFIELD: single-system FP32 matvecs with the wall form every
     // block with the cancellation-free direct-minus-image differences
     int far_field = 0;
-    // RPBD_OPT_SYM_ATOMIC: the packed symmetric kernel of one system sums into FP64
-    // atomics per blob (memory O(n)) even when its visitor partials would fit
-    int sym_atomic = 0;
+    // RPBD_OPT_SYM_PARTIALS: the packed symmetric kernel of one system writes
+    // per-home-tile partials reduced in a fixed order (memory O(n^2)) instead of
+    // its fixed-point accumulation (memory O(n))
+    int sym_partials = 0;
 };
 
 namespace rpbd {

@@ -522,8 +522,39 @@ static int run(rpbd_handle* h, int64_t n, const double* r, const In* F, Out* U, 
 // floats) so the 32 lanes' loads of different records hit distinct banks.
 
 constexpr int HT2 = 256;  // home blobs per CTA, two per thread
-// beyond this many bytes of visitor partials a single system accumulates in FP64 atomics
+// beyond this many bytes of per-home-tile visitor partials a single system
+// always takes the fixed-point accumulation below
 constexpr double SYM_PARTIAL_LIMIT = 16.0 * (1ull << 30);
+
+// Fixed-point accumulation of one system's matvec.  Every contribution to a
+// blob's velocity (a visitor tile's sum, an item's home sum) is an FP32 number;
+// it is scaled by 2^S, rounded to a 64-bit integer and added with an integer
+// atomic, so the result does not depend on the order of the additions
+// (integer addition is associative): deterministic with one accumulator per
+// blob and component.  S is the largest exponent for which no sum can leave
+// 2^61: every block entry is at most the self term 4/3 (in units of a; nine
+// images in the periodic cell), so a component is bounded by 4 n max|F|
+// (x 9), and 2^S = 2^61 / (that bound rounded up to a power of two).  The
+// rounding step 2^-S is ~1e-12 of the largest possible sum.
+__device__ __forceinline__ int fixed_exponent(float fmax, int64_t n, bool per)
+{
+    const float bound = 4.0f * (float)n * fmax * (per ? 9.0f : 1.0f);
+    if (!(bound > 0.0f)) return 0;
+    int e;
+    frexpf(bound, &e);  // bound < 2^e
+    const int S = 61 - e;
+    return S < -100 ? -100 : (S > 120 ? 120 : S);
+}
+// adds v 2^S; a non-finite v (non-finite positions) raises flag, and the
+// finishing kernel then writes NaN, as the fixed-order reduction would
+__device__ __forceinline__ void fixed_add(unsigned long long* a, float v, float scale, unsigned* flag)
+{
+    if (!isfinite(v)) {
+        atomicExch(flag, 1u);
+        return;
+    }
+    atomicAdd(a, (unsigned long long)__float2ll_rn(v * scale));
+}
 
 template <int K>
 struct Rec2 {
@@ -542,7 +573,8 @@ __host__ __device__ __forceinline__ int64_t rec2_off(int64_t i, int c, int len)
 template <int K, class In>
 __global__ void pack2_kernel(int n_sys, const SymSys* __restrict__ sys, int64_t rec_end, int64_t n_tot, int k,
                              const double* __restrict__ r, const In* __restrict__ F, double a, int wall, double s_min,
-                             const int* __restrict__ active, float* __restrict__ rec, double* __restrict__ scale)
+                             const int* __restrict__ active, float* __restrict__ rec, double* __restrict__ scale,
+                             unsigned* __restrict__ fmax_bits = nullptr)
 {
     const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (j >= rec_end) return;
@@ -581,13 +613,28 @@ __global__ void pack2_kernel(int n_sys, const SymSys* __restrict__ sys, int64_t 
     v[2] = (float)(x - (double)xh);
     v[3] = (float)(y - (double)yh);
     v[4] = (float)zt;
+    float fm = 0.0f;
     if (real)
         for (int m = 0; m < k; ++m)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) v[5 + 3 * m + c] = (float)(s * (double)F[((int64_t)m * 3 + c) * n_tot + i]);
+            for (int c = 0; c < 3; ++c) {
+                v[5 + 3 * m + c] = (float)(s * (double)F[((int64_t)m * 3 + c) * n_tot + i]);
+                fm = isfinite(v[5 + 3 * m + c]) ? fmaxf(fm, fabsf(v[5 + 3 * m + c])) : INFINITY;
+            }
 #pragma unroll
     for (int c = 0; c < NCH; ++c)
         *reinterpret_cast<float4*>(rec + rec2_off(j, c, LEN)) = make_float4(v[2 * c], v[2 * c], v[2 * c + 1], v[2 * c + 1]);
+    if (fmax_bits) {
+        // fmax_bits[0]: largest finite |force| of the launch (non-negative floats
+        // order like their bits); fmax_bits[1] != 0: some force is not finite
+        const bool bad = isinf(fm);
+        const unsigned b = __reduce_max_sync(__activemask(), bad ? 0u : __float_as_uint(fm));
+        const unsigned anybad = __any_sync(__activemask(), bad);
+        if ((threadIdx.x & 31) == __ffs(__activemask()) - 1) {
+            atomicMax(fmax_bits, b);
+            if (anybad) atomicExch(fmax_bits + 1, 1u);
+        }
+    }
 }
 
 // record j of a staged tile -> packed operands (both lanes equal); value m
@@ -699,7 +746,7 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
                                                               const SymSys* __restrict__ sys,
                                                               const int* __restrict__ active, float Lx, float Ly,
                                                               float* __restrict__ partial, int* __restrict__ err_flag,
-                                                              RingTest rt)
+                                                              RingTest rt, const unsigned* __restrict__ fmax_bits = nullptr)
 {
     constexpr int NT = HT2 / (2 * HP);  // threads
     constexpr int NW = NT / 32;          // warps
@@ -720,6 +767,8 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
     const int64_t ib = (int64_t)it.home * HT2 + warp * 64 * HP + lane;  // home record of pair 0, lane .x
     const PairConstX2 pc = PairConstX2::make_unit();
     const float2 m1 = pc.m1;
+    // fixed-point scale 2^S of the accumulation (ATOM)
+    const float fscale = ATOM ? ldexpf(1.0f, fixed_exponent(__uint_as_float(__ldg(fmax_bits)), n, PER)) : 0.0f;
 
     if (tid == 0) {
 #pragma unroll
@@ -826,8 +875,9 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
                     float sum = rb[vl * 3 * K + q];
 #pragma unroll
                     for (int w = 1; w < NW; ++w) sum += rb[(w * VT + vl) * 3 * K + q];
-                    if constexpr (ATOM)  // one FP64 accumulator per blob and component
-                        atomicAdd(reinterpret_cast<double*>(partial) + (int64_t)q * sn_pad + vg, (double)sum);
+                    if constexpr (ATOM)  // one fixed-point accumulator per blob and component
+                        fixed_add(reinterpret_cast<unsigned long long*>(partial) + (int64_t)q * sn_pad + vg, sum,
+                                  fscale, const_cast<unsigned*>(fmax_bits) + 1);
                     else
                         part[(hloc * 3 * K + q) * sn_pad + vg] = sum;
                 }
@@ -857,9 +907,9 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
 #pragma unroll
         for (int q = 0; q < 3 * K; ++q) {
             if constexpr (ATOM) {
-                double* a64 = reinterpret_cast<double*>(partial) + (int64_t)q * sn_pad;
-                if (l0 < sn) atomicAdd(a64 + l0, (double)acc[p][q].x);
-                if (l1 < sn) atomicAdd(a64 + l1, (double)acc[p][q].y);
+                unsigned long long* a64 = reinterpret_cast<unsigned long long*>(partial) + (int64_t)q * sn_pad;
+                if (l0 < sn) fixed_add(a64 + l0, acc[p][q].x, fscale, const_cast<unsigned*>(fmax_bits) + 1);
+                if (l1 < sn) fixed_add(a64 + l1, acc[p][q].y, fscale, const_cast<unsigned*>(fmax_bits) + 1);
             } else {
                 if (l0 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l0] = acc[p][q].x;
                 if (l1 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l1] = acc[p][q].y;
@@ -941,15 +991,19 @@ __global__ void reduce2_kernel(int n_sys, const SymSys* __restrict__ sys, int64_
     U[(int64_t)q * n_tot + g] = (Out)(scale[g] * inv8pieta * sum);
 }
 
-// U of one system from the FP64 accumulators of the atomic mode: scale and write
+// U of one system from its fixed-point accumulators: undo 2^S, scale and write
 template <class Out>
-__global__ void finish_atomic_kernel(int64_t n, int64_t n_pad, int k, const double* __restrict__ acc,
-                                     const double* __restrict__ scale, double inv8pieta, Out* __restrict__ U)
+__global__ void finish_fixed_kernel(int64_t n, int64_t n_pad, int k, bool per, const unsigned long long* __restrict__ acc,
+                                    const unsigned* __restrict__ fmax_bits, const double* __restrict__ scale,
+                                    double inv8pieta, Out* __restrict__ U)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int q = blockIdx.y;
     if (i >= n || q >= 3 * k) return;
-    U[(int64_t)q * n + i] = (Out)(scale[i] * inv8pieta * acc[(int64_t)q * n_pad + i]);
+    const int S = fixed_exponent(__uint_as_float(fmax_bits[0]), n, per);
+    const double v = fmax_bits[1] ? __longlong_as_double(0x7ff8000000000000LL)
+                                   : ldexp((double)(long long)acc[(int64_t)q * n_pad + i], -S);
+    U[(int64_t)q * n + i] = (Out)(scale[i] * inv8pieta * v);
 }
 
 }  // namespace sym
@@ -1067,24 +1121,28 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     double* scale;
     float* partial;
     double* segsum = nullptr;
-    // one system whose visitor partials would pass SYM_PARTIAL_LIMIT bytes (or the
-    // handle asks for it): FP64 atomic accumulation per blob instead (memory O(n))
-    const bool atom = n_sys == 1 && !h->far_field &&
-                      (h->sym_atomic || (double)pl->part_rows * 3 * K * sizeof(float) > SYM_PARTIAL_LIMIT);
+    // one system: fixed-point accumulation, one integer per blob and component
+    // (memory O(n), deterministic); per-home-tile partials with the fixed-order
+    // reduction on request while they stay under SYM_PARTIAL_LIMIT bytes; batches:
+    // per-system partials
+    const bool atom = n_sys == 1 && (!h->sym_partials || h->far_field ||
+                                     (double)pl->part_rows * 3 * K * sizeof(float) > SYM_PARTIAL_LIMIT);
     const int64_t np1a = pl->sys[0].n_pad;
+    unsigned* fmax_bits = nullptr;
     RPBD_TRY(ensure_t(h, b_rec, (size_t)pl->rec_end * LEN, &rec));
     RPBD_TRY(ensure_t(h, b_scale, (size_t)n_tot, &scale));
     if (atom) {
-        double* acc64;
-        RPBD_TRY(ensure_t(h, b_part, (size_t)3 * K * np1a, &acc64));
-        RPBD_CU(h, cudaMemsetAsync(acc64, 0, sizeof(double) * 3 * K * np1a, st));
-        partial = reinterpret_cast<float*>(acc64);
+        unsigned long long* acc;  // [3K][n_pad] accumulators, then the two words of fmax_bits
+        RPBD_TRY(ensure_t(h, b_part, (size_t)3 * K * np1a + 1, &acc));
+        RPBD_CU(h, cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (3 * K * np1a + 1), st));
+        partial = reinterpret_cast<float*>(acc);
+        fmax_bits = reinterpret_cast<unsigned*>(acc + 3 * K * np1a);
     } else {
         RPBD_TRY(ensure_t(h, b_part, (size_t)pl->part_rows * 3 * K, &partial));
         RPBD_TRY(ensure_t(h, b_seg, (size_t)std::max<int64_t>(1, pl->seg_rows) * 3 * K, &segsum));
     }
     pack2_kernel<K, In><<<(unsigned)((pl->rec_end + 255) / 256), 256, 0, st>>>(
-        n_sys, pl->d_sys, pl->rec_end, n_tot, k, r, F, h->p.a, h->p.wall, h->p.s_min, active, rec, scale);
+        n_sys, pl->d_sys, pl->rec_end, n_tot, k, r, F, h->p.a, h->p.wall, h->p.s_min, active, rec, scale, fmax_bits);
     count_launch();
     const float Lxa = (float)(h->p.Lx / h->p.a), Lya = (float)(h->p.Ly / h->p.a);  // periodic cell in units of a
     if (h->profile) prof_begin(h, st);
@@ -1098,10 +1156,11 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     // tuning variants, see Sym2Var; -1: the autotuner's usual pick at 65,535 blobs (k = 1: variant 3,
     // k = 2: variant 5, k = 3..4: variant 4)
     const int var = sv >= 0 ? sv : (K == 1 ? 3 : (K == 2 ? 5 : 4));
-#define RPBD_SYM2_LAUNCH(V)                                                                                    \
-    sym2_kernel<K, PER, Sym2Var<K, V, PER>::UNR, Sym2Var<K, V, PER>::MINB, false, Sym2Var<K, V, PER>::HP>     \
-        <<<ni, Sym2Var<K, V, PER>::NT, Sym2Var<K, V, PER>::smem(LEN), st>>>(rec, items, n1, np1, T1, sys, nullptr, \
-                                                                            Lxa, Lya, partial, h->dev_flag, rt)
+#define RPBD_SYM2_LAUNCH(V, FARV, ATOMV)                                                                          \
+    sym2_kernel<K, PER, Sym2Var<K, V, PER>::UNR, Sym2Var<K, V, PER>::MINB, false, Sym2Var<K, V, PER>::HP, FARV, ATOMV> \
+        <<<ni, Sym2Var<K, V, PER>::NT, Sym2Var<K, V, PER>::smem(LEN), st>>>(rec, items, n1, np1, T1, sys, nullptr,     \
+                                                                            Lxa, Lya, partial, h->dev_flag, rt,        \
+                                                                            fmax_bits)
     if (n_sys > 1) {  // batches: the default variant
         if constexpr (!PER)
             sym2_kernel<K, false, Sym2Var<K, 2>::UNR, Sym2Var<K, 2>::MINB, true>
@@ -1109,22 +1168,18 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
                                                                           Lya, partial, h->dev_flag, rt);
         else
             return set_error(h, RPBD_BAD_ARG, "packed symmetric kernel: batches are open in x, y");
-    } else if (atom) {  // FP64 atomic accumulation: one compiled variant
-        sym2_kernel<K, PER, Sym2Var<K, 2, PER>::UNR, Sym2Var<K, 2, PER>::MINB, false, 1, false, true>
-            <<<ni, Sym2Var<K, 2, PER>::NT, Sym2Var<K, 2, PER>::smem(LEN), st>>>(rec, items, n1, np1, T1, sys, nullptr,
-                                                                                Lxa, Lya, partial, h->dev_flag, rt);
     } else if (h->far_field) {  // the cancellation-free block: one compiled variant
-        sym2_kernel<K, PER, Sym2Var<K, 2, PER>::UNR, Sym2Var<K, 2, PER>::MINB, false, 1, true>
-            <<<ni, Sym2Var<K, 2, PER>::NT, Sym2Var<K, 2, PER>::smem(LEN), st>>>(rec, items, n1, np1, T1, sys, nullptr,
-                                                                                Lxa, Lya, partial, h->dev_flag, rt);
+        RPBD_SYM2_LAUNCH(2, true, true);
+    } else if (!atom) {  // per-home-tile partials and the fixed-order reduction: one compiled variant
+        RPBD_SYM2_LAUNCH(2, false, false);
     } else {
         switch (var) {
-        case 1: RPBD_SYM2_LAUNCH(1); break;
-        case 2: RPBD_SYM2_LAUNCH(2); break;
-        case 3: RPBD_SYM2_LAUNCH(3); break;
-        case 4: RPBD_SYM2_LAUNCH(4); break;
-        case 5: RPBD_SYM2_LAUNCH(5); break;
-        default: RPBD_SYM2_LAUNCH(0); break;
+        case 1: RPBD_SYM2_LAUNCH(1, false, true); break;
+        case 2: RPBD_SYM2_LAUNCH(2, false, true); break;
+        case 3: RPBD_SYM2_LAUNCH(3, false, true); break;
+        case 4: RPBD_SYM2_LAUNCH(4, false, true); break;
+        case 5: RPBD_SYM2_LAUNCH(5, false, true); break;
+        default: RPBD_SYM2_LAUNCH(0, false, true); break;
         }
     }
 #undef RPBD_SYM2_LAUNCH
@@ -1137,8 +1192,8 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     // blocks were formed in units of a: M = M(a = 1) / a
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta * h->p.a);
     if (atom) {
-        finish_atomic_kernel<Out><<<dim3((unsigned)((n_tot + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(
-            n_tot, np1a, k, reinterpret_cast<const double*>(partial), scale, inv8pieta, U);
+        finish_fixed_kernel<Out><<<dim3((unsigned)((n_tot + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(
+            n_tot, np1a, k, PER, reinterpret_cast<const unsigned long long*>(partial), fmax_bits, scale, inv8pieta, U);
         count_launch();
         RPBD_LAUNCH_CHECK(h);
         return RPBD_OK;

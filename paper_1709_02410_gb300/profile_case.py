@@ -2,7 +2,7 @@
 
     python -m paper_1709_02410_gb300.profile_case --n 65535 --k 16 --dtype f32 --reps 5
     python -m paper_1709_02410_gb300.profile_case --batched --k 1 --reps 5     # 64 uneven suspensions
-    python -m paper_1709_02410_gb300.profile_case --adjoint --n 65535 --reps 3 # FP32 adjoint
+    python -m paper_1709_02410_gb300.profile_case --adjoint --n 65535 --reps 3 # FP32 adjoint (--k: RHS pairs)
 
 Prints one JSON line: seconds per launch (pack + pair kernel + reduce),
 pairs/s and matvecs/s.  Useful on its own and as the target of profilers.
@@ -25,8 +25,8 @@ def main():
     ap.add_argument("--batched", action="store_true",
                     help="the uneven batch of 64 boomerang suspensions (one batched launch; --variant: tile variant)")
     ap.add_argument("--adjoint", action="store_true", help="the FP32 adjoint instead of the matvec")
-    ap.add_argument("--atomic", action="store_true",
-                    help="packed symmetric kernel with FP64 atomic accumulation per blob")
+    ap.add_argument("--partials", action="store_true",
+                    help="packed symmetric kernel with per-home-tile partials (not the fixed-point accumulation)")
     ap.add_argument("--far", action="store_true", help="cancellation-free far field")
     a = ap.parse_args()
     import torch
@@ -41,7 +41,7 @@ def main():
     h = Handle(synth.ETA, s.a, synth.KT, wall=bool(a.wall))
     h.set_symmetric(bool(a.sym))
     h.set_sym_variant(a.variant)
-    h.set_sym_atomic(a.atomic)
+    h.set_sym_partials(a.partials)
     h.set_far_field(a.far)
     T = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
     r = h.blobs_from_bodies(T(s.shape), T(s.q), T(s.theta))
@@ -57,7 +57,7 @@ def main():
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / a.reps
-    print(json.dumps({"n": s.n, "k": a.k, "dtype": a.dtype, "sym": a.sym, "variant": a.variant, "atomic": a.atomic,
+    print(json.dumps({"n": s.n, "k": a.k, "dtype": a.dtype, "sym": a.sym, "variant": a.variant, "partials": a.partials,
                       "far": a.far,
                       "s_per_launch": t, "pairs_per_s": s.n * s.n / t,
                       "matvecs_per_s": a.k / t}))
@@ -101,7 +101,8 @@ def adjoint(a):
     dev = "cuda:0"
     T = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
     r = h.blobs_from_bodies(T(s.shape), T(s.q), T(s.theta))
-    u, F = T(synth.gaussian(8, (3, s.n))), T(synth.gaussian(9, (3, s.n)))
+    shp = (3, s.n) if a.k == 1 else (a.k, 3, s.n)   # k right-hand-side pairs, summed
+    u, F = T(synth.gaussian(8, shp)), T(synth.gaussian(9, shp))
     g = h.mobility_adjoint(r, u, F, dtype=F32)
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
@@ -111,7 +112,7 @@ def adjoint(a):
     e1.record()
     torch.cuda.synchronize()
     t = e0.elapsed_time(e1) / 1e3 / a.reps
-    print(json.dumps({"adjoint_f32": True, "n": s.n, "s_per_launch": t, "pairs_per_s": s.n * s.n / t}))
+    print(json.dumps({"adjoint_f32": True, "n": s.n, "k": a.k, "s_per_launch": t, "pairs_per_s": s.n * s.n / t}))
 
 
 if __name__ == "__main__":

@@ -213,24 +213,45 @@ def test_f32_packed_variants(variant, k):
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
 @pytest.mark.parametrize("n", [1, 257, 2049, 9000])
-def test_f32_packed_symmetric_atomic_mode(k, n):
-    """The packed symmetric kernel summing into one FP64 accumulator per blob
-    (atomic adds) instead of per-home-tile partials: against the oracle, and
-    against the fixed-order reduction (both sum the same FP32 tile partials in
-    FP64 or better, so they differ by FP32 output rounding only)."""
+def test_f32_packed_symmetric_fixed_point_and_partials(k, n):
+    """The packed symmetric kernel's two accumulations: fixed point per blob
+    (the default; integer atomics) and per-home-tile partials with the
+    fixed-order reduction.  Both against the oracle, against each other (they
+    sum the same FP32 tile sums, to ~1e-12 and to ~48 bits, so they differ by
+    FP32 output rounding), and each bit for bit against a repeat of itself."""
     rng = np.random.default_rng(13 * n + k)
     box = max(2.0, np.sqrt(n))
     r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
     F = rng.standard_normal((k, 3, n)).astype(np.float32)
     s = synth.c0_boomerangs_1920()
     h = handle_for(s)
-    Ud = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
-    h.set_sym_atomic(True)
-    Ua = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
-    Ua64 = h.mobility_apply(to_dev(r), to_dev(F.astype(np.float64)), dtype=1).cpu().numpy()
+    rd, Fd = to_dev(r), to_dev(F, torch.float32)
+    Ufx = h.mobility_apply(rd, Fd).cpu().numpy()
+    assert np.array_equal(Ufx, h.mobility_apply(rd, Fd).cpu().numpy())
+    Ufx64 = h.mobility_apply(rd, to_dev(F.astype(np.float64)), dtype=1).cpu().numpy()
+    h.set_sym_partials(True)
+    Upt = h.mobility_apply(rd, Fd).cpu().numpy()
+    assert np.array_equal(Upt, h.mobility_apply(rd, Fd).cpu().numpy())
     Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
-    assert rel2(Ua, Uo) <= 1e-5 and rel2(Ua64, Uo) <= 1e-5
-    assert rel2(Ua, Ud) <= 1e-6
+    assert rel2(Ufx, Uo) <= 1e-5 and rel2(Ufx64, Uo) <= 1e-5 and rel2(Upt, Uo) <= 1e-5
+    assert rel2(Ufx, Upt) <= 1e-6
+
+
+def test_f32_fixed_point_non_finite_input_gives_nan():
+    """A NaN force or position makes the fixed-point sums NaN, as the
+    fixed-order reduction's sums would be."""
+    s = synth.c0_boomerangs_1920()
+    r = positions(s)
+    F = synth.gaussian(3, (1, 3, s.n), np.float32)
+    h = handle_for(s)
+    Fb = F.copy()
+    Fb[0, 1, 77] = np.nan
+    assert np.isnan(h.mobility_apply(to_dev(r), to_dev(Fb, torch.float32)).cpu().numpy()).any()
+    rb = r.copy()
+    rb[0, 5] = np.nan
+    assert np.isnan(h.mobility_apply(to_dev(rb), to_dev(F, torch.float32)).cpu().numpy()).any()
+    U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()   # and the handle is fine
+    assert rel2(U, om.apply(r, F.astype(np.float64), oracle_params(s))) <= 1e-5
 
 
 @pytest.mark.parametrize("k", [1, 2, 3, 4])
@@ -261,10 +282,9 @@ def test_f32_one_direction_packed_tile(k):
 @pytest.mark.parametrize("k", [1, 2, 3])
 def test_f32_half_million_blobs_row_sampled(k, sym):
     """500,010 blobs (33,334 boomerangs at the same density): the packed
-    symmetric kernel keeps its per-home-tile partials for k = 1 (13 GB) and
-    sums into FP64 atomics per blob for k = 2 and 3, whose partials would pass
-    16 GiB; with the symmetric kernel off, the one-direction kernels (k = 2 its
-    own tile, k = 1, 3 the packed tile); 32 sampled rows against the oracle."""
+    symmetric kernel with its fixed-point accumulation (memory O(n)); with the
+    symmetric kernel off, the one-direction kernels (k = 2 its own tile, k = 1,
+    3 the packed tile); 32 sampled rows against the oracle."""
     nb = 33334
     s = synth.boomerang_suspension(nb, 40.0 * np.sqrt(nb / 128), 44)
     r = positions(s)
