@@ -237,6 +237,36 @@ def test_f32_packed_symmetric_fixed_point_and_partials(k, n):
     assert rel2(Ufx, Upt) <= 1e-6
 
 
+def test_f32_fixed_point_wide_force_range():
+    """Forces over ten decades (log-uniform 1e-4..1e4, one blob at 1e6): the
+    fixed-point step 2^-S is set by the largest force, so small rows carry an
+    absolute error of at most (contributions per blob) x 2^-S / 2, in units of
+    1 / (8 pi eta a).  Checked element by element against the partials path
+    (the same FP32 tile sums, no fixed-point rounding), and both against the
+    oracle."""
+    n = 9000
+    rng = np.random.default_rng(4242)
+    box = np.sqrt(n)
+    r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
+    F = rng.standard_normal((1, 3, n)) * 10.0 ** rng.uniform(-4, 4, n)
+    F[0, :, 4321] = [1e6, -1e6, 5e5]
+    F = F.astype(np.float32)
+    s = synth.c0_boomerangs_1920()
+    h = handle_for(s)
+    rd, Fd = to_dev(r), to_dev(F, torch.float32)
+    Ufx = h.mobility_apply(rd, Fd).cpu().numpy().astype(np.float64)
+    h.set_sym_partials(True)
+    Upt = h.mobility_apply(rd, Fd).cpu().numpy().astype(np.float64)
+    Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
+    assert rel2(Ufx, Uo) <= 1e-5 and rel2(Upt, Uo) <= 1e-5
+    # S as the kernel takes it: 2^S = 2^61 / 2^e with 4 n max|F| < 2^e (FP32 product)
+    bound = np.float32(4.0) * np.float32(n) * np.float32(np.abs(F).max())
+    step = 2.0 ** -(61 - np.frexp(bound)[1])
+    contributions = n // 256 + n // 32 + 2      # visitor tiles before the blob + its home items
+    abs_tol = contributions * step / 2 / (8 * np.pi * synth.ETA * s.a)
+    assert np.all(np.abs(Ufx - Upt) <= 4 * np.finfo(np.float32).eps * np.abs(Upt) + abs_tol)
+
+
 def test_f32_fixed_point_non_finite_input_gives_nan():
     """A NaN force or position makes the fixed-point sums NaN, as the
     fixed-order reduction's sums would be."""
