@@ -406,7 +406,8 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
  * contribution to a blob's velocity is scaled by 2^S, rounded to a 64-bit
  * integer and added atomically, one accumulator per blob and component
  * (memory 3k n integers; S from the largest |force|, so that no sum can
- * overflow; the rounding step is ~1e-12 of the largest possible sum).  Integer
+ * overflow; the rounding step is at most 2^-60 of the largest possible sum,
+ * 4 n max|F| in units of 1 / (8 pi eta a); any finite FP32 forces).  Integer
  * addition does not depend on its order, so both are deterministic; they
  * differ by FP32 output rounding. */
 #define RPBD_OPT_SYM_PARTIALS 7

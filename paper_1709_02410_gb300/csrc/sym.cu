@@ -535,25 +535,30 @@ constexpr double SYM_PARTIAL_LIMIT = 16.0 * (1ull << 30);
 // 2^61: every block entry is at most the self term 4/3 (in units of a; nine
 // images in the periodic cell), so a component is bounded by 4 n max|F|
 // (x 9), and 2^S = 2^61 / (that bound rounded up to a power of two).  The
-// rounding step 2^-S is ~1e-12 of the largest possible sum.
+// rounding step 2^-S is at most 2^-60 of that bound.
 __device__ __forceinline__ int fixed_exponent(float fmax, int64_t n, bool per)
 {
-    const float bound = 4.0f * (float)n * fmax * (per ? 9.0f : 1.0f);
-    if (!(bound > 0.0f)) return 0;
+    // in FP64, where the bound stays finite for every finite FP32 force (S
+    // then lies within about [-120, 210])
+    const double bound = 4.0 * (double)n * (double)fmax * (per ? 9.0 : 1.0);
+    if (!(bound > 0.0)) return 0;
     int e;
-    frexpf(bound, &e);  // bound < 2^e
-    const int S = 61 - e;
-    return S < -100 ? -100 : (S > 120 ? 120 : S);
+    frexp(bound, &e);  // bound < 2^e
+    return 61 - e;
 }
-// adds v 2^S; a non-finite v (non-finite positions) raises flag, and the
-// finishing kernel then writes NaN, as the fixed-order reduction would
-__device__ __forceinline__ void fixed_add(unsigned long long* a, float v, float scale, unsigned* flag)
+// adds v 2^S, scaled in two exact FP32 steps 2^h 2^(S-h) so that each factor
+// is a normal FP32 number over the whole range of S; a non-finite v
+// (non-finite positions) raises flag, and the finishing kernel then writes
+// NaN, as the fixed-order reduction would
+__device__ __forceinline__ void fixed_add(unsigned long long* a, float v, int S, unsigned* flag)
 {
     if (!isfinite(v)) {
         atomicExch(flag, 1u);
         return;
     }
-    atomicAdd(a, (unsigned long long)__float2ll_rn(v * scale));
+    const int h = S >> 1;
+    const float s1 = __int_as_float((h + 127) << 23), s2 = __int_as_float((S - h + 127) << 23);
+    atomicAdd(a, (unsigned long long)__float2ll_rn((v * s1) * s2));
 }
 
 template <int K>
@@ -672,18 +677,38 @@ __device__ __forceinline__ void pair_apply2(float2 dx, float2 dy, float2 dz, flo
 #pragma unroll
     for (int m = 0; m < K; ++m) {
         const float2 fx = f[3 * m], fy = f[3 * m + 1], fz = f[3 * m + 2];
-        const float2 P = fma2(dy, fy, mul2(dx, fx));
-        const float2 Q = fma2(be, P, mul2(gx, fz));
-        acc[3 * m + 0] = fma2(dx, Q, fma2(al, fx, acc[3 * m + 0]));
-        acc[3 * m + 1] = fma2(dy, Q, fma2(al, fy, acc[3 * m + 1]));
-        acc[3 * m + 2] = fma2(mzz, fz, fma2(gz, P, acc[3 * m + 2]));
         if constexpr (BOTH) {
+            // both directions, written so that consecutive instructions share
+            // an operand in the same position (al, dx, dy, be, mzz): the
+            // register file feeds such packed FMAs faster than ones that read
+            // three fresh register pairs
             const float2 hx = hf[3 * m], hy = hf[3 * m + 1], hzf = hf[3 * m + 2];
-            const float2 Pt = fma2(dy, hy, mul2(dx, hx));
-            const float2 Qt = fma2(be, Pt, mul2(gz, hzf));
-            vacc[3 * m + 0] = fma2(dx, Qt, fma2(al, hx, vacc[3 * m + 0]));
-            vacc[3 * m + 1] = fma2(dy, Qt, fma2(al, hy, vacc[3 * m + 1]));
-            vacc[3 * m + 2] = fma2(mzz, hzf, fma2(gx, Pt, vacc[3 * m + 2]));
+            float2 a0 = fma2(al, fx, acc[3 * m + 0]);
+            float2 a1 = fma2(al, fy, acc[3 * m + 1]);
+            float2 v0 = fma2(al, hx, vacc[3 * m + 0]);
+            float2 v1 = fma2(al, hy, vacc[3 * m + 1]);
+            float2 P = mul2(dx, fx);
+            float2 Pt = mul2(dx, hx);
+            P = fma2(dy, fy, P);
+            Pt = fma2(dy, hy, Pt);
+            float2 Q = mul2(gx, fz);
+            float2 Qt = mul2(gz, hzf);
+            Q = fma2(be, P, Q);
+            Qt = fma2(be, Pt, Qt);
+            acc[3 * m + 0] = fma2(dx, Q, a0);
+            vacc[3 * m + 0] = fma2(dx, Qt, v0);
+            acc[3 * m + 1] = fma2(dy, Q, a1);
+            vacc[3 * m + 1] = fma2(dy, Qt, v1);
+            float2 a2 = fma2(mzz, fz, acc[3 * m + 2]);
+            float2 v2 = fma2(mzz, hzf, vacc[3 * m + 2]);
+            acc[3 * m + 2] = fma2(gz, P, a2);
+            vacc[3 * m + 2] = fma2(gx, Pt, v2);
+        } else {
+            const float2 P = fma2(dy, fy, mul2(dx, fx));
+            const float2 Q = fma2(be, P, mul2(gx, fz));
+            acc[3 * m + 0] = fma2(dx, Q, fma2(al, fx, acc[3 * m + 0]));
+            acc[3 * m + 1] = fma2(dy, Q, fma2(al, fy, acc[3 * m + 1]));
+            acc[3 * m + 2] = fma2(mzz, fz, fma2(gz, P, acc[3 * m + 2]));
         }
     }
 }
@@ -767,8 +792,8 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
     const int64_t ib = (int64_t)it.home * HT2 + warp * 64 * HP + lane;  // home record of pair 0, lane .x
     const PairConstX2 pc = PairConstX2::make_unit();
     const float2 m1 = pc.m1;
-    // fixed-point scale 2^S of the accumulation (ATOM)
-    const float fscale = ATOM ? ldexpf(1.0f, fixed_exponent(__uint_as_float(__ldg(fmax_bits)), n, PER)) : 0.0f;
+    // exponent S of the fixed-point scale 2^S (ATOM)
+    const int fexp = ATOM ? fixed_exponent(__uint_as_float(__ldg(fmax_bits)), n, PER) : 0;
 
     if (tid == 0) {
 #pragma unroll
@@ -877,7 +902,7 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
                     for (int w = 1; w < NW; ++w) sum += rb[(w * VT + vl) * 3 * K + q];
                     if constexpr (ATOM)  // one fixed-point accumulator per blob and component
                         fixed_add(reinterpret_cast<unsigned long long*>(partial) + (int64_t)q * sn_pad + vg, sum,
-                                  fscale, const_cast<unsigned*>(fmax_bits) + 1);
+                                  fexp, const_cast<unsigned*>(fmax_bits) + 1);
                     else
                         part[(hloc * 3 * K + q) * sn_pad + vg] = sum;
                 }
@@ -908,8 +933,8 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
         for (int q = 0; q < 3 * K; ++q) {
             if constexpr (ATOM) {
                 unsigned long long* a64 = reinterpret_cast<unsigned long long*>(partial) + (int64_t)q * sn_pad;
-                if (l0 < sn) fixed_add(a64 + l0, acc[p][q].x, fscale, const_cast<unsigned*>(fmax_bits) + 1);
-                if (l1 < sn) fixed_add(a64 + l1, acc[p][q].y, fscale, const_cast<unsigned*>(fmax_bits) + 1);
+                if (l0 < sn) fixed_add(a64 + l0, acc[p][q].x, fexp, const_cast<unsigned*>(fmax_bits) + 1);
+                if (l1 < sn) fixed_add(a64 + l1, acc[p][q].y, fexp, const_cast<unsigned*>(fmax_bits) + 1);
             } else {
                 if (l0 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l0] = acc[p][q].x;
                 if (l1 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l1] = acc[p][q].y;

@@ -142,19 +142,22 @@ __device__ __forceinline__ void pair_factors_x2(float2 dx, float2 dy, float2 dz,
     const float2 y = mul2(q, w);  // e_z^2
     const float2 a1 = fma2(bc2(-10.0f), y, fma2(zi6, zj, bc2(2.0f)));
     const float2 b1 = fma2(bc2(70.0f / 3.0f), y, bc2(-10.0f / 3.0f));
-    const float2 h1 = fma2(w, b1, a1);
-    const float2 Bp = mul2(w, h1);  // B + 1
-    beta = fma2(v, Bp, c2v);
     const float2 eA = fma2(m2zi, zj, fma2(bc2(2.0f), y, bc2(-2.0f / 3.0f)));
-    const float2 iA = fma2(w, fma2(bc2(-10.0f / 3.0f), y, c.a23), eA);
+    const float2 b2 = fma2(bc2(-10.0f / 3.0f), y, c.a23);
+    const float2 h1 = fma2(w, b1, a1);
+    const float2 iA = fma2(w, b2, eA);
+    const float2 Bp = mul2(w, h1);  // B + 1
+    const float2 w2 = mul2(w, bc2(-20.0f / 3.0f));
+    const float2 tz = fma2(bc2(20.0f), w, fma2(c.m1, h1, bc2(-4.0f)));
+    beta = fma2(v, Bp, c2v);
     alpha = fma2(v, iA, X1);
-    const float2 Pn = fma2(mul2(bc2(-20.0f / 3.0f), w), w, Bp);  // -P
+    const float2 vR = mul2(v, Rz);
+    const float2 Pn = fma2(w2, w, Bp);  // -P
     const float2 base = mul2(dz, c2v);
-    const float2 vRPn = mul2(mul2(v, Rz), Pn);
+    const float2 vRPn = mul2(vR, Pn);
+    const float2 iZ = fma2(y, tz, mul2(bc2(-8.0f / 3.0f), w));
     gx = fma2(c.m1, vRPn, base);
     gz = add2(base, vRPn);
-    const float2 tz = fma2(bc2(20.0f), w, fma2(c.m1, h1, bc2(-4.0f)));
-    const float2 iZ = fma2(y, tz, mul2(bc2(-8.0f / 3.0f), w));
     Mzz = fma2(v, iZ, fma2(dz, base, alpha));
 }
 

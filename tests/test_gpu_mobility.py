@@ -259,12 +259,31 @@ def test_f32_fixed_point_wide_force_range():
     Upt = h.mobility_apply(rd, Fd).cpu().numpy().astype(np.float64)
     Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
     assert rel2(Ufx, Uo) <= 1e-5 and rel2(Upt, Uo) <= 1e-5
-    # S as the kernel takes it: 2^S = 2^61 / 2^e with 4 n max|F| < 2^e (FP32 product)
-    bound = np.float32(4.0) * np.float32(n) * np.float32(np.abs(F).max())
+    # S as the kernel takes it: 2^S = 2^61 / 2^e with 4 n max|F| < 2^e
+    bound = 4.0 * n * float(np.abs(F).max())
     step = 2.0 ** -(61 - np.frexp(bound)[1])
     contributions = n // 256 + n // 32 + 2      # visitor tiles before the blob + its home items
     abs_tol = contributions * step / 2 / (8 * np.pi * synth.ETA * s.a)
     assert np.all(np.abs(Ufx - Upt) <= 4 * np.finfo(np.float32).eps * np.abs(Upt) + abs_tol)
+
+
+@pytest.mark.parametrize("n,scale", [(2049, 1e-30), (2049, 1e-20), (2049, 1e20), (9000, 4e33)])
+def test_f32_fixed_point_extreme_force_scales(n, scale):
+    """The fixed-point exponent follows the forces' scale over the FP32 range:
+    forces of 1e-30 (2^S = 2^145, beyond FP32's largest power of two) and of
+    4e33 at 9,000 blobs (4 n max|F| ~ 6e38, beyond FP32's largest value) give
+    the oracle's velocities to the FP32 tolerance, as N(0,1) forces do.  (Far
+    smaller forces meet FP32's flush of subnormal products, not the fixed
+    point.)"""
+    rng = np.random.default_rng(977)
+    box = np.sqrt(n)
+    r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
+    F = (rng.standard_normal((2, 3, n)) * scale).astype(np.float32)
+    s = synth.c0_boomerangs_1920()
+    h = handle_for(s)
+    U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(U))
+    assert rel2(U, om.apply(r, F.astype(np.float64), oracle_params(s))) <= 1e-5
 
 
 def test_f32_fixed_point_non_finite_input_gives_nan():
