@@ -21,7 +21,7 @@ def main():
     ap.add_argument("--reps", type=int, default=3)
     ap.add_argument("--wall", type=int, default=1)
     ap.add_argument("--sym", type=int, default=1, help="FP32 k <= 4: symmetric kernel (1) or one-direction (0)")
-    ap.add_argument("--variant", type=int, default=-1, help="symmetric kernel variant 0..3 (-1: default)")
+    ap.add_argument("--variant", type=int, default=-1, help="symmetric kernel variant 0..5 (-1: default)")
     ap.add_argument("--batched", action="store_true",
                     help="the uneven batch of 64 boomerang suspensions (one batched launch; --variant: tile variant)")
     ap.add_argument("--adjoint", action="store_true", help="the FP32 adjoint instead of the matvec")
