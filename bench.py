@@ -301,7 +301,7 @@ def run_ours(args, rank, world, local):
     batched = measure_batched(h.lib, dev, T) if (rank == 0 and extras) else None
     rollers = measure_rollers(dev, T) if (rank == 0 and extras and not args.no_rollers) else None
     next_rows = measure_next_rows(dev, T, s, shape, q0, th0, forces, Lp) if (rank == 0 and extras) else None
-    c2_div = measure_c2_divergence(T) if (rank == 0 and extras) else None
+    rfd_div = measure_rfd_vs_divergence(T) if (rank == 0 and extras) else None
 
     out = None
     if rank == 0:
@@ -392,10 +392,10 @@ def run_ours(args, rank, world, local):
             "measured_fma_peak_tflops": {"f32": fma32, "f64": fma64, "f32_packed_three_varying_operands": fma32v},
             "matvec": extra,
             "rows": row_times,
-            "batched_c4": batched,
-            "ts_step_rollers_c3": rollers,
+            "batched_uneven_64": batched,
+            "ts_step_rollers_196608": rollers,
             "next_rows": next_rows,
-            "c2_rfd_vs_divergence": c2_div,
+            "rfd_vs_divergence_16380": rfd_div,
             "accuracy": acc,
             "wall_s_timed": wall,
         }
@@ -549,14 +549,14 @@ def measure_next_rows(dev, T, s, shape, q0, th0, forces, Lp):
 
 
 # ---------------------------------------------------------------------------
-# config 2: the exact divergence of M (FP64 dual-number kernel) against the
+# The exact divergence of M (FP64 dual-number kernel) against the
 # mean of the blob RFD drift over 10^4 random W (Sec. 3), 16,380 blobs
 
-def measure_c2_divergence(T, samples=10000, chunk=250):
+def measure_rfd_vs_divergence(T, samples=10000, chunk=250):
     import torch
     import paper_1709_02410_gb300 as P
     from paper_1709_02410_gb300 import synth
-    s = synth.c2_blobs_16384()
+    s = synth.blobs_16384()
     h = P.Handle(synth.ETA, s.a, synth.KT)
     r = h.blobs_from_bodies(T(s.shape), T(s.q), T(s.theta))
     n = r.shape[1]
@@ -598,7 +598,7 @@ def measure_rollers(dev, T, steps=5):
     import paper_1709_02410_gb300 as P
     from paper_1709_02410_gb300 import synth
     from paper_1709_02410_gb300._native import Forces, StepParams
-    s = synth.c3_rollers_196608()
+    s = synth.rollers_196608()
     h = P.Handle(synth.ETA, s.a, synth.KT)
     shape, q, th = T(s.shape), T(s.q), T(s.theta)
     # buoyant weight m_e g = 1.24e-14 N = 1.24e-2 mg um/s^2 per roller, shared by its 12 blobs;
@@ -631,7 +631,7 @@ def measure_rollers(dev, T, steps=5):
     e1.record()
     torch.cuda.synchronize()
     # the same suspension placed purely at random (rollers interpenetrating), for comparison
-    so = synth.c3_rollers_196608(overlap=True)
+    so = synth.rollers_196608(overlap=True)
     qo, tho = T(so.q), T(so.theta)
     e2, e3 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e2.record()
@@ -657,7 +657,7 @@ def measure_batched(lib, dev, T, tol=1e-4, max_iter=60):
     import torch
     import paper_1709_02410_gb300 as P
     from paper_1709_02410_gb300 import synth
-    systems = synth.c4_uneven_batch()
+    systems = synth.uneven_batch_64()
     a = systems[0].a
     hb = P.Handle(synth.ETA, a, synth.KT)
     shape = T(systems[0].shape)

@@ -66,7 +66,7 @@ def main():
 def batched(a):
     import torch
     from . import Handle, synth
-    systems = synth.c4_uneven_batch()
+    systems = synth.uneven_batch_64()
     h = Handle(synth.ETA, systems[0].a, synth.KT)
     if a.variant >= 0:
         h.set_batch_variant(a.variant)

@@ -165,29 +165,29 @@ def gaussian(seed: int, shape, dtype=np.float64) -> np.ndarray:
 
 # ---- the five workloads -------------------------------------------------
 
-def c0_boomerangs_1920(seed: int = 0) -> Suspension:
+def boomerangs_1920(seed: int = 0) -> Suspension:
     """128 boomerangs x 15 = 1,920 blobs in a 40 x 40 um box (FP64 parity)."""
     return boomerang_suspension(128, 40.0, seed)
 
 
-def c1_boomerangs_65535(seed: int = 1) -> Suspension:
+def boomerangs_65535(seed: int = 1) -> Suspension:
     """4,369 boomerangs x 15 = 65,535 blobs, box scaled to c0's area density."""
     return boomerang_suspension(4369, 40.0 * np.sqrt(4369 / 128), seed)
 
 
-def c2_blobs_16384(seed: int = 2) -> Suspension:
+def blobs_16384(seed: int = 2) -> Suspension:
     """16,380 blobs as 1,092 boomerangs (adjoint workload), same density."""
     return boomerang_suspension(1092, 40.0 * np.sqrt(1092 / 128), seed)
 
 
-def c3_rollers_196608(seed: int = 3, nb: int = 16384, overlap: bool = False) -> Suspension:
+def rollers_196608(seed: int = 3, nb: int = 16384, overlap: bool = False) -> Suspension:
     """16,384 rollers x 12 = 196,608 blobs at phi = 0.4, placed as hard
     spheres of the hydrodynamic radius (no two centres closer than 2 R_h);
     overlap=True keeps the purely random placement."""
     return roller_suspension(nb, 0.4, seed, overlap=overlap)
 
 
-def c4_uneven_batch(seed: int = 4, n_sys: int = 64):
+def uneven_batch_64(seed: int = 4, n_sys: int = 64):
     """64 boomerang suspensions with body counts log-uniform in [32, 1500]."""
     rng = np.random.default_rng(seed)
     counts = np.floor(np.exp(rng.uniform(np.log(32), np.log(1500), size=n_sys))).astype(int)

@@ -17,7 +17,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_empty_suspension_launches_nothing():
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     r = torch.zeros((3, 0), dtype=torch.float64, device=DEV)
     torch.cuda.synchronize()
@@ -58,7 +58,7 @@ def test_lone_blob_is_its_self_mobility(dtype):
     """One blob at height h: U = mu(h) F with the near-wall self mobility
     mu_par = (1 - 9/16 x + 1/8 x^3 - 1/16 x^5) / (6 pi eta a),
     mu_perp = (1 - 9/8 x + 1/2 x^3 - 1/8 x^5) / (6 pi eta a), x = a / h."""
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     a, eta = s.a, synth.ETA
     h = handle_for(s)
     for height in (1.0 * a, 1.7 * a, 5.0 * a):

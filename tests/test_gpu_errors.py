@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _setup():
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     return s, handle_for(s), positions(s)
 
 

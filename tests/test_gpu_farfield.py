@@ -75,7 +75,7 @@ def test_far_field_mode_matvec_parity(k, n):
     box = max(2.0, np.sqrt(n))
     r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
     F = rng.standard_normal((k, 3, n)).astype(np.float32)
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     h.set_far_field(True)
     U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()

@@ -18,7 +18,7 @@ pytestmark = pytest.mark.gpu
 
 @pytest.mark.parametrize("k", [1, 2])
 def test_rollers_196608_row_sampled(k):
-    s = synth.c3_rollers_196608()
+    s = synth.rollers_196608()
     r = rigid.blob_positions(s.q, s.theta, s.shape)
     F = synth.gaussian(80 + k, (k, 3, s.n), np.float32)
     h = handle_for(s)
@@ -31,7 +31,7 @@ def test_rollers_196608_row_sampled(k):
 
 
 def _batch():
-    systems = synth.c4_uneven_batch()
+    systems = synth.uneven_batch_64()
     rs = [rigid.blob_positions(sy.q, sy.theta, sy.shape) for sy in systems]
     off = np.concatenate([[0], np.cumsum([x.shape[1] for x in rs])]).astype(np.int64)
     return systems, rs, off, np.concatenate(rs, axis=1)

@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_blob_geometry_matches_oracle():
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     r = h.blobs_from_bodies(to_dev(s.shape), to_dev(s.q), to_dev(s.theta)).cpu().numpy()
     np.testing.assert_allclose(r, positions(s), rtol=0, atol=1e-13)
@@ -21,7 +21,7 @@ def test_blob_geometry_matches_oracle():
 
 @pytest.mark.parametrize("wall", [True, False])
 def test_f64_matvec_c0(wall):
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     F = synth.gaussian(10, (3, s.n))
     h = handle_for(s, wall=wall)
@@ -38,7 +38,7 @@ def test_f64_matvec_ragged(n, k):
     box = max(2.0, np.sqrt(n) * 0.8)
     r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
     F = rng.standard_normal((k, 3, n))
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     U = h.mobility_apply(to_dev(r), to_dev(F)).cpu().numpy()
     Uo = om.apply(r, F, oracle_params(s))
@@ -47,7 +47,7 @@ def test_f64_matvec_ragged(n, k):
 
 @pytest.mark.parametrize("k", [1, 2, 4, 8, 16])
 def test_f32_matvec_c0(k):
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     F32in = synth.gaussian(20 + k, (k, 3, s.n), np.float32)
     h = handle_for(s)
@@ -63,7 +63,7 @@ def test_f32_matvec_ragged(n):
     box = max(2.0, np.sqrt(n))
     r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
     F = rng.standard_normal((5, 3, n)).astype(np.float32)
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
     Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
@@ -71,7 +71,7 @@ def test_f32_matvec_ragged(n):
 
 
 def test_mixed_mode_f32_pairs_f64_vectors():
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     F = synth.gaussian(30, (3, s.n))
     h = handle_for(s)
@@ -80,7 +80,7 @@ def test_mixed_mode_f32_pairs_f64_vectors():
 
 
 def test_empty_is_noop():
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     r = torch.zeros((3, 0), dtype=torch.float64, device=DEV)
     F = torch.zeros((3, 0), dtype=torch.float64, device=DEV)
@@ -93,7 +93,7 @@ def test_f32_full_size_row_sampled(k):
     """65,535 blobs in the bench's launch configurations (k = 1, 2: packed
     symmetric kernel; k = 16: one-direction kernel); 128 sampled target rows
     (the first and last blob included) against the oracle."""
-    s = synth.c1_boomerangs_65535()
+    s = synth.boomerangs_65535()
     r = positions(s)
     F = synth.gaussian(40 + k, (k, 3, s.n), np.float32)
     h = handle_for(s)
@@ -105,7 +105,7 @@ def test_f32_full_size_row_sampled(k):
 
 
 def test_f64_full_size_row_sampled():
-    s = synth.c1_boomerangs_65535()
+    s = synth.boomerangs_65535()
     r = positions(s)
     F = synth.gaussian(42, (3, s.n))
     h = handle_for(s)
@@ -123,7 +123,7 @@ def test_f32_symmetric_and_one_direction_agree(k, n):
     box = max(2.0, np.sqrt(n))
     r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
     F = rng.standard_normal((k, 3, n)).astype(np.float32)
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     U1 = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
     h.set_symmetric(False)
@@ -133,7 +133,7 @@ def test_f32_symmetric_and_one_direction_agree(k, n):
 
 
 def test_autotune_picks_a_correct_kernel():
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     F = synth.gaussian(60, (1, 3, s.n), np.float32)
     h = handle_for(s)
@@ -150,7 +150,7 @@ def test_autotune_picks_a_correct_kernel():
 
 def test_autotune_classes_are_independent():
     """Autotuning k = 2 keeps the k = 1 choice; both classes stay correct."""
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     h = handle_for(s)
     c1, _ = h.autotune(to_dev(r), 1)
@@ -166,7 +166,7 @@ def test_fma_peak_probe():
     """The FMA-throughput probe returns a plausible figure: below the nominal
     dense peaks (FP32: 152 SMs x 128 lanes x 2 x 2.07 GHz) with margin, and
     FP32 well above FP64."""
-    h = handle_for(synth.c0_boomerangs_1920())
+    h = handle_for(synth.boomerangs_1920())
     f32 = h.measure_fma_peak(F32)
     f64 = h.measure_fma_peak(F64)
     f32v = h.measure_fma_peak(3)   # packed FMAs reading three distinct varying registers
@@ -188,7 +188,7 @@ def test_f32_packed_symmetric_kernel(k, n, variant):
     box = max(2.0, np.sqrt(n))
     r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
     F = rng.standard_normal((k, 3, n)).astype(np.float32)
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     h.set_sym_variant(variant)
     Up = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
@@ -202,7 +202,7 @@ def test_f32_packed_symmetric_kernel(k, n, variant):
 @pytest.mark.parametrize("k", [1, 2, 4])
 @pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 def test_f32_packed_variants(variant, k):
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     F = synth.gaussian(70 + variant, (k, 3, s.n), np.float32)
     h = handle_for(s)
@@ -223,7 +223,7 @@ def test_f32_packed_symmetric_fixed_point_and_partials(k, n):
     box = max(2.0, np.sqrt(n))
     r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
     F = rng.standard_normal((k, 3, n)).astype(np.float32)
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     rd, Fd = to_dev(r), to_dev(F, torch.float32)
     Ufx = h.mobility_apply(rd, Fd).cpu().numpy()
@@ -251,7 +251,7 @@ def test_f32_fixed_point_wide_force_range():
     F = rng.standard_normal((1, 3, n)) * 10.0 ** rng.uniform(-4, 4, n)
     F[0, :, 4321] = [1e6, -1e6, 5e5]
     F = F.astype(np.float32)
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     rd, Fd = to_dev(r), to_dev(F, torch.float32)
     Ufx = h.mobility_apply(rd, Fd).cpu().numpy().astype(np.float64)
@@ -279,7 +279,7 @@ def test_f32_fixed_point_extreme_force_scales(n, scale):
     box = np.sqrt(n)
     r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
     F = (rng.standard_normal((2, 3, n)) * scale).astype(np.float32)
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy().astype(np.float64)
     assert np.all(np.isfinite(U))
@@ -289,7 +289,7 @@ def test_f32_fixed_point_extreme_force_scales(n, scale):
 def test_f32_fixed_point_non_finite_input_gives_nan():
     """A NaN force or position makes the fixed-point sums NaN, as the
     fixed-order reduction's sums would be."""
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     F = synth.gaussian(3, (1, 3, s.n), np.float32)
     h = handle_for(s)
@@ -310,7 +310,7 @@ def test_f32_one_direction_packed_tile(k):
     own tile; packed and unpacked one-direction kernels against the oracle at
     sizes across the 64-source tile and the 2048-source chunk, the work list
     rebuilt as n changes, FP32 and FP64 vectors."""
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     h.set_symmetric(False)
     for n in (1, 63, 129, 2049, 4500, 700):
@@ -354,7 +354,7 @@ def test_f32_packed_far_from_origin_and_wide(k):
     x, y as hi/lo float pairs, so a translation by 10^5 a leaves U unchanged
     (to FP32 rounding of the pair blocks), and a 4,000 a wide scatter of
     clusters still meets the oracle at 1e-5."""
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     F = synth.gaussian(47 + k, (k, 3, s.n), np.float32)
     h = handle_for(s)

@@ -12,7 +12,7 @@ pytestmark = pytest.mark.gpu
 
 
 def test_K_and_KT():
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     rng = np.random.default_rng(0)
     U = rng.standard_normal((s.nb, 6))
@@ -26,14 +26,14 @@ def test_K_and_KT():
 
 @pytest.mark.parametrize("n", [1, 3, 4, 5, 1001])
 def test_philox_normals(n):
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     z = h.philox_normals(n, seed=0x1234567890ABCDEF, step=9, sid=1).cpu().numpy()
     np.testing.assert_allclose(z, philox.normals(n, 0x1234567890ABCDEF, 9, 1), rtol=1e-13, atol=1e-13)
 
 
 def test_blob_forces():
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     fm = steps.ForceModel(weight=0.05, wall_gamma=0.096, wall_b=0.162, h_floor=0.1)
     f = Forces(fm.weight, fm.wall_gamma, fm.wall_b, fm.h_floor, (0.0, 0.0, 0.0))
@@ -47,7 +47,7 @@ def test_blob_forces():
 def test_blob_forces_steric(r_cut, dtype, tol):
     """Blob-blob Yukawa repulsion between blobs of different bodies (FP64
     separations, force arithmetic in dtype) against the FP64 oracle."""
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     fm = steps.ForceModel(weight=0.05, wall_gamma=0.096, wall_b=0.162, h_floor=0.1, steric_gamma=0.5,
                           steric_b=0.3, r_floor=0.1, r_cut=r_cut)
@@ -65,7 +65,7 @@ def test_blob_forces_steric(r_cut, dtype, tol):
 
 
 def test_blob_forces_steric_rejects_bad_args():
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     h = handle_for(s)
     r = to_dev(positions(s))
     f = Forces(0.0, 0.0, 1.0, 0.1, (0.0, 0.0, 0.0), 1.0, 0.3, 0.1, 0.0)

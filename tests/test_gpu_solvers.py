@@ -66,12 +66,12 @@ def test_lanczos_matches_oracle_iterates():
     assert rel2(out.cpu().numpy(), ref) <= 1e-4
 
 
-def test_lanczos_c0_fixed_iterations_matches_oracle():
-    """Config 0 (1,920 blobs): with the iteration count pinned on both sides
+def test_lanczos_1920_fixed_iterations_matches_oracle():
+    """1,920 boomerang blobs: with the iteration count pinned on both sides
     (20 iterations, a tolerance neither side reaches) the FP64 Lanczos of the
     library and of the oracle build the same Krylov space and differ only by
     rounding: <= 1e-12."""
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     prm = oracle_params(s)
     pc = precond.BlockPrecond(r, s.q, s.nper, prm)
@@ -237,7 +237,7 @@ def test_gmres_not_converged_reports_status():
 
 @pytest.mark.parametrize("dtype,delta,bound", [(F64, 1e-6, 1e-9), (F32, 1e-3, 2e-3)])
 def test_rfd_drift_matches_oracle(dtype, delta, bound):
-    s = synth.c0_boomerangs_1920()
+    s = synth.boomerangs_1920()
     r = positions(s)
     W = synth.gaussian(17, (3, s.n))
     ref = rfd.rfd_drift(r, W, delta, oracle_params(s))
@@ -266,10 +266,10 @@ def test_divergence_matches_oracle():
     assert rel2(d, om.divergence(r, oracle_params(s))) <= 1e-11
 
 
-def test_adjoint_c2_sampled_and_fd():
+def test_adjoint_16380_sampled_and_fd():
     """16,380 blobs: oracle gradient on sampled blobs, plus central
     differences of the GPU matvec itself (h = 1e-6 a) on 64 coordinates."""
-    s = synth.c2_blobs_16384()
+    s = synth.blobs_16384()
     r = positions(s)
     rng = np.random.default_rng(21)
     u, F = rng.standard_normal((2, 3, s.n))

@@ -19,7 +19,7 @@ def test_rotation_quarter_turn_about_z():
 
 
 def test_blob_positions_rigid():
-    s = synth.c0_boomerangs_1920(0)
+    s = synth.boomerangs_1920(0)
     r = rigid.blob_positions(s.q, s.theta, s.shape)
     rb = r.T.reshape(s.nb, s.nper, 3)
     d = np.linalg.norm(rb[:, :, None] - rb[:, None], axis=-1)

@@ -34,7 +34,7 @@ def _call(lib, prm, r, F, U, k, n=None):
 
 def test_noalloc_matches_workspace_path_twice():
     lib = _native.load()
-    s = synth.c2_blobs_16384()           # 16,380 blobs, just under the 16,384 limit
+    s = synth.blobs_16384()           # 16,380 blobs, just under the 16,384 limit
     rh = positions(s)
     r = to_dev(rh)
     prm = _native.Params(synth.ETA, s.a, synth.KT, 1, 1e-3)
