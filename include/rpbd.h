@@ -395,7 +395,7 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
  * separation; the default form loses digits in proportion to
  * |R|^2 / (zi zj) (~1e-3 relative for a block 700 a away), which the matvec's
  * rows do not show because such blocks are tiny.  Runs the packed symmetric
- * kernel for every k (groups of up to four right-hand sides), about 9%
+ * kernel for every k (groups of up to four right-hand sides), 5-12%
  * slower per launch; RPBD_BAD_ARG when packing is off.  Batched and adjoint
  * calls keep the default form. */
 #define RPBD_OPT_FARFIELD 6

@@ -741,8 +741,10 @@ __device__ __forceinline__ void pair_apply2_images(float2 dx, float2 dy, float2 
 template <int K, int V, bool PER = false>
 struct Sym2Var {
     static constexpr int HP = V >= 4 ? 2 : 1;
-    static constexpr int UNR = V == 0 ? 2 : (V == 1 ? 1 : (V == 2 ? 2 : (V == 3 ? 4 : (V == 4 ? 1 : 2))));
-    static constexpr int MINB0 = V >= 4 ? (K == 1 ? 8 : (K == 2 ? 6 : 4))
+    // (the periodic cell's nine-image body is unrolled less, to bound the code size)
+    static constexpr int UNR = V == 0 ? 2
+                             : (V == 1 ? 1 : (V == 2 ? 2 : (V == 3 ? (K == 1 && !PER ? 16 : 4) : (V == 4 ? 1 : (PER ? 2 : (K == 1 ? 4 : 8))))));
+    static constexpr int MINB0 = V >= 4 ? (K == 1 ? 8 : (K == 2 ? 5 : 4))
                                         : (K == 1 ? (V == 1 ? 6 : (V == 2 ? 5 : 4))
                                                   : (K == 2 ? (V == 2 ? 3 : 4) : (V == 1 ? 3 : 2)));
     // the image loop of the periodic cell needs more registers
@@ -1195,7 +1197,7 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
         else
             return set_error(h, RPBD_BAD_ARG, "packed symmetric kernel: batches are open in x, y");
     } else if (h->far_field) {  // the cancellation-free block: one compiled variant per k
-        RPBD_SYM2_LAUNCH(K == 1 ? 3 : 5, true, true);
+        RPBD_SYM2_LAUNCH(K == 1 ? 3 : (K == 2 || !PER ? 5 : 3), true, true);  // (k > 2 periodic: no spill)
     } else if (!atom) {  // per-home-tile partials and the fixed-order reduction: the default variant
         RPBD_SYM2_LAUNCH(K == 1 ? 3 : (K == 2 ? 5 : 4), false, false);
     } else {
