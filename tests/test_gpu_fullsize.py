@@ -94,3 +94,65 @@ def test_uneven_batch_471495_lanczos_graph():
         if rank < 3:
             _, it_tol, _ = krylov.lanczos_sqrt(G, W[:, sl], 1e-4, 60)
             assert abs(iters[s] - it_tol) <= 1, s
+
+
+def test_boomerangs_65535_gmres_residual_sampled():
+    """The saddle solve at full size in the bench's configuration (65,535
+    boomerang blobs, FP32 pairs, GMRES tol 1e-6, restart 100, block-diagonal
+    preconditioner), checked on 48 sampled bodies (720 blob rows) with the
+    oracle: the velocity rows M lambda - K U + slip (oracle M lambda in FP64
+    over all sources) and the force and torque balance K^T lambda = F.  The
+    FP32 operator agrees with the oracle to ~1e-6 of |M lambda|, so the first
+    residual is bounded by the FP32 parity tolerance (1e-5 of the sampled
+    |M lambda|) plus GMRES's own 1e-6 |b|; the balance, formed in FP64, by
+    the GMRES tolerance."""
+    from paper_1709_02410_gb300 import F32
+    s = synth.boomerangs_65535()
+    r = rigid.blob_positions(s.q, s.theta, s.shape)
+    h = handle_for(s)
+    FT = synth.gaussian(71, (s.nb, 6)) * 1e-2
+    slip = synth.gaussian(72, (3, s.n)) * 1e-3
+    lam, U, st = h.gmres_rigid_solve(s.nper, to_dev(r), to_dev(s.q), to_dev(slip), to_dev(FT), tol=1e-6,
+                                     max_iter=300, restart=100, dtype=F32)
+    assert st["status"] == 0, st
+    lam, U = lam.cpu().numpy(), U.cpu().numpy()
+    nper = s.nper
+    bodies = np.sort(np.random.default_rng(73).choice(s.nb, 48, replace=False))
+    rows = np.concatenate([np.arange(p * nper, (p + 1) * nper) for p in bodies])
+    Ml = om.apply(r, lam, oracle_params(s), rows=rows)
+    KU = np.concatenate([rigid.K_apply(r[:, p * nper:(p + 1) * nper], s.q[p:p + 1], U[p:p + 1], nper)
+                         for p in bodies], axis=1)
+    b_norm = np.sqrt(np.sum(slip ** 2) + np.sum(FT ** 2))
+    res = Ml - KU + slip[:, rows]
+    print(f"velocity rows: |res| {np.linalg.norm(res):.3e}, bound {1e-5 * np.linalg.norm(Ml) + 1e-6 * b_norm:.3e}")
+    assert np.linalg.norm(res) <= 1e-5 * np.linalg.norm(Ml) + 1e-6 * b_norm
+    KTl = np.concatenate([rigid.KT_apply(r[:, p * nper:(p + 1) * nper], s.q[p:p + 1],
+                                         lam[:, p * nper:(p + 1) * nper], nper) for p in bodies])
+    print(f"balance: |K^T lam - F| {np.linalg.norm(KTl - FT[bodies]):.3e}, bound {1e-5 * b_norm:.3e}")
+    assert np.linalg.norm(KTl - FT[bodies]) <= 1e-5 * b_norm
+
+
+def test_boomerangs_65535_lanczos_norm_identity():
+    """The preconditioned Lanczos at full size in the bench's configuration
+    (65,535 boomerang blobs, FP32 pairs, tol 1e-4): its output y = L G^{1/2} W
+    with G = L^-1 M L^-T must satisfy |L^-1 y|^2 = W^T G W = z^T M z with
+    z = L^-T W, a property that holds at any size.  L from the oracle's
+    block preconditioner, M z from the FP64 matvec (pinned to the oracle at
+    1e-12 elsewhere).  A relative error ~tol in y gives ~2 tol in the squared
+    norm: bound 1e-3; a wrong factor or scale is off by O(1)."""
+    from paper_1709_02410_gb300 import F32
+    s = synth.boomerangs_65535()
+    r = rigid.blob_positions(s.q, s.theta, s.shape)
+    h = handle_for(s)
+    rd = to_dev(r)
+    h.precond_build(s.nper, rd, to_dev(s.q))
+    W = synth.gaussian(74, (3, s.n))
+    y, st = h.lanczos_sqrt_apply(rd, to_dev(W), tol=1e-4, max_iter=60, dtype=F32)
+    assert st["status"] == 0, st
+    pc = precond.BlockPrecond(r, s.q, s.nper, oracle_params(s))
+    u = pc.Linv_apply(y.cpu().numpy())
+    z = pc.LinvT_apply(W)
+    Mz = h.mobility_apply(rd, to_dev(z)).cpu().numpy()
+    zMz = float(np.sum(z * Mz))
+    print(f"|L^-1 y|^2 / z^T M z - 1 = {float(np.sum(u * u)) / zMz - 1:.3e} ({st['iterations']} iterations)")
+    assert abs(float(np.sum(u * u)) - zMz) <= 1e-3 * zMz
