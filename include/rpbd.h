@@ -399,17 +399,20 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
  * slower per launch; RPBD_BAD_ARG when packing is off.  Batched and adjoint
  * calls keep the default form. */
 #define RPBD_OPT_FARFIELD 6
-/* value != 0 (default 0): the packed symmetric kernel of a single system
- * writes one FP32 visitor partial per (256-blob home tile, blob) and reduces
- * them in a fixed order (memory about n^2 / 256 * 3k floats; past 16 GiB the
- * option is ignored).  By default it accumulates in fixed point instead: every
- * contribution to a blob's velocity is scaled by 2^S, rounded to a 64-bit
+/* value != 0 (default 0): the FP32 matvec of a single system keeps partial
+ * sums reduced in a fixed order: the packed symmetric kernel one FP32 visitor
+ * partial per (256-blob home tile, blob) (memory about n^2 / 256 * 3k floats;
+ * past 16 GiB the option is ignored), the one-direction kernel one per
+ * (2048-source chunk, blob) (n^2 / 2048 * 3k floats).  By default both
+ * accumulate in fixed point instead: every contribution to a blob's velocity
+ * (a tile's or a chunk's FP32 sum) is scaled by 2^S, rounded to a 64-bit
  * integer and added atomically, one accumulator per blob and component
  * (memory 3k n integers; S from the largest |force|, so that no sum can
  * overflow; the rounding step is at most 2^-60 of the largest possible sum,
- * 4 n max|F| in units of 1 / (8 pi eta a); any finite FP32 forces).  Integer
- * addition does not depend on its order, so both are deterministic; they
- * differ by FP32 output rounding. */
+ * 4 n max|F| in units of 1 / (8 pi eta a), x 9 in the periodic cell; any
+ * finite FP32 forces).  Integer addition does not depend on its order, so
+ * both are deterministic; they differ by FP32 output rounding.  Batches and
+ * the FP64 kernels always keep their partials. */
 #define RPBD_OPT_SYM_PARTIALS 7
 int rpbd_set_option(rpbd_handle* h, int option, int value);
 

@@ -113,8 +113,9 @@ class Handle:
         self._check(self.lib.rpbd_set_option(self.h, 6, int(bool(on))), "set_option")
 
     def set_sym_partials(self, on: bool):
-        """Packed symmetric kernel of one system: per-home-tile partials with the fixed-order
-        reduction (memory O(n^2)) instead of the default fixed-point accumulation (memory O(n))."""
+        """FP32 matvec of one system: partial sums with the fixed-order reduction (per home tile
+        in the packed symmetric kernel, per source chunk in the one-direction kernel; memory
+        O(n^2)) instead of the default fixed-point accumulation (memory O(n))."""
         self._check(self.lib.rpbd_set_option(self.h, 7, int(bool(on))), "set_option")
 
     def measure_fma_peak(self, dtype=F32):

@@ -15,12 +15,17 @@
 //              in FP64, FP32 partials as compensated float pairs, about
 //              48 bits; the result is deterministic), multiplies by
 //              s_i / (8 pi eta) and writes U in the caller's type.
+// FP32 applies through the handle accumulate in fixed point instead
+// (fixed_point.cuh): each CTA adds its chunk sums to one 64-bit integer per
+// blob and component, so memory is O(n k) rather than O(n^2 k / 2048), and a
+// small kernel finishes U; the result is the same bit for bit on every run.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 
 #include "accum.cuh"
+#include "fixed_point.cuh"
 #include "rpbd_internal.cuh"
 #include "wall_rpy.cuh"
 
@@ -50,6 +55,14 @@ struct Rec<double, K> {
 // partial sums: FP32 kernels store float chunk sums, FP64 kernels double
 template <class R>
 struct PartialT { using type = R; };
+
+// FP32 fixed-point accumulation (acc != nullptr): [3K][n_pad] accumulators and
+// fmax_bits (largest |force|, non-finite flag); cap as in fixed_exponent
+struct FixedAcc {
+    unsigned long long* acc;
+    unsigned* fmax_bits;
+    double cap;
+};
 
 // ---------------------------------------------------------------------------
 // PTX helpers: mbarrier + 1-D TMA bulk copy
@@ -110,7 +123,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
 template <class R, int K, class In>
 __global__ void pack_kernel(int64_t n, int64_t n_pad, int k, const double* __restrict__ r,
                             const In* __restrict__ F, double a, int wall, double s_min,
-                            R* __restrict__ rec, double* __restrict__ scale)
+                            R* __restrict__ rec, double* __restrict__ scale, unsigned* __restrict__ fmax_bits = nullptr)
 {
     const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (i >= n_pad) return;
@@ -146,6 +159,7 @@ __global__ void pack_kernel(int64_t n, int64_t n_pad, int k, const double* __res
         constexpr int TAIL = Rec<R, K>::TAIL;
 #pragma unroll
         for (int q = 1; q < TAIL; ++q) o[4 + q] = 0.0f;
+        float fm = 0.0f;  // largest |stored force| of this blob (+inf: not finite)
         if (i < n)
             for (int m = 0; m < k; ++m)
 #pragma unroll
@@ -153,7 +167,9 @@ __global__ void pack_kernel(int64_t n, int64_t n_pad, int k, const double* __res
                     const float v = (float)(s * (double)F[((int64_t)m * 3 + c) * n + i]);
                     if constexpr (K == 1) o[5 + c] = v;
                     else o[6 + 6 * (m / 2) + 2 * c + (m & 1)] = v;
+                    fm = isfinite(v) ? fmaxf(fm, fabsf(v)) : INFINITY;
                 }
+        if (fmax_bits) fixed_force_max(fmax_bits, fm);
     } else {
         o[0] = x;
         o[1] = y;
@@ -173,7 +189,7 @@ __global__ void pack_kernel(int64_t n, int64_t n_pad, int k, const double* __res
 template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
 __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, int64_t n_pad, int tiles_per_chunk,
                                           int n_tiles, PairConst<R> pc, typename PartialT<R>::type* __restrict__ partial,
-                                          int* __restrict__ err_flag, RingTest rt)
+                                          int* __restrict__ err_flag, RingTest rt, FixedAcc fx)
 {
     constexpr int LEN = Rec<R, K>::LEN;
     constexpr uint32_t TILE_BYTES = TS * LEN * sizeof(R);
@@ -310,7 +326,23 @@ __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, 
         return;
     }
     if (i < n) {
-        if constexpr (PK) {
+        if (sizeof(R) == 4 && fx.acc) {  // FP32: the chunk sums into the fixed-point accumulators
+            const int S = fixed_exponent(__uint_as_float(__ldg(fx.fmax_bits)), n, fx.cap);
+            unsigned* const flag = fx.fmax_bits + 1;
+            if constexpr (PK) {
+#pragma unroll
+                for (int pp = 0; pp < K / 2; ++pp)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        fixed_add(fx.acc + (int64_t)(3 * (2 * pp) + c) * n_pad + i, (float)acc2[3 * pp + c].x, S, flag);
+                        fixed_add(fx.acc + (int64_t)(3 * (2 * pp + 1) + c) * n_pad + i, (float)acc2[3 * pp + c].y, S,
+                                  flag);
+                    }
+            } else {
+#pragma unroll
+                for (int q = 0; q < 3 * K; ++q) fixed_add(fx.acc + (int64_t)q * n_pad + i, (float)acc[q], S, flag);
+            }
+        } else if constexpr (PK) {
 #pragma unroll
             for (int pp = 0; pp < K / 2; ++pp)
 #pragma unroll
@@ -329,9 +361,9 @@ template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
 __global__ void __launch_bounds__(BT) pair_kernel(const R* __restrict__ rec, int64_t n, int64_t n_pad,
                                                   int tiles_per_chunk, int n_tiles, PairConst<R> pc,
                                                   typename PartialT<R>::type* __restrict__ partial,
-                                                  int* __restrict__ err_flag, RingTest rt)
+                                                  int* __restrict__ err_flag, RingTest rt, FixedAcc fx)
 {
-    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag, rt);
+    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag, rt, fx);
 }
 
 // FP32, 16 right-hand sides: registers capped so five CTAs share an SM
@@ -339,9 +371,9 @@ template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
 __global__ void __launch_bounds__(BT, 5) pair_kernel_k16(const R* __restrict__ rec, int64_t n, int64_t n_pad,
                                                          int tiles_per_chunk, int n_tiles, PairConst<R> pc,
                                                          typename PartialT<R>::type* __restrict__ partial,
-                                                         int* __restrict__ err_flag, RingTest rt)
+                                                         int* __restrict__ err_flag, RingTest rt, FixedAcc fx)
 {
-    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag, rt);
+    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag, rt, fx);
 }
 
 template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
@@ -422,14 +454,26 @@ static int apply_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out*
 
     R* rec;
     double* scale;
-    typename PartialT<R>::type* partial;
+    typename PartialT<R>::type* partial = nullptr;
     RPBD_TRY(ensure_t(h, BUF_PACK, (size_t)n_pad * LEN, &rec));
     RPBD_TRY(ensure_t(h, BUF_SCALE, (size_t)n_pad, &scale));
-    RPBD_TRY(ensure_t(h, BUF_PARTIAL, (size_t)n_chunks * 3 * K * n_pad, &partial));
+    // FP32: fixed-point accumulators unless per-chunk partials are requested
+    // (RPBD_OPT_SYM_PARTIALS); block entries are at most 4 / (3 a) (8 pi eta
+    // M in lengths of the caller), nine images in the periodic cell
+    const bool fixed = sizeof(R) == 4 && !h->sym_partials;
+    FixedAcc fx{nullptr, nullptr, (PER ? 36.0 : 4.0) / h->p.a};
+    if (fixed) {
+        RPBD_TRY(ensure_t(h, BUF_PARTIAL, (size_t)3 * K * n_pad + 1, &fx.acc));
+        RPBD_CU(h, cudaMemsetAsync(fx.acc, 0, sizeof(unsigned long long) * (3 * K * n_pad + 1), st));
+        fx.fmax_bits = reinterpret_cast<unsigned*>(fx.acc + 3 * K * n_pad);
+    } else {
+        RPBD_TRY(ensure_t(h, BUF_PARTIAL, (size_t)n_chunks * 3 * K * n_pad, &partial));
+    }
 
     const PairConst<R> pc = PairConst<R>::make(h->p.a, h->p.Lx, h->p.Ly);
     pack_kernel<R, K, In><<<(unsigned)((n_pad + 255) / 256), 256, 0, st>>>(n, n_pad, k, r, F, h->p.a, h->p.wall,
-                                                                           h->p.s_min, rec, scale); count_launch();
+                                                                           h->p.s_min, rec, scale, fx.fmax_bits);
+    count_launch();
     RPBD_LAUNCH_CHECK(h);
     const size_t smem = (size_t)NST * TS * LEN * sizeof(R) + NST * sizeof(uint64_t);
     auto kern = pick_pair_kernel<R, K, BT, TS, NST, WALL, PER>();
@@ -437,13 +481,19 @@ static int apply_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out*
         RPBD_CU(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)tgt_tiles, (unsigned)n_chunks);
     if (h->profile) prof_begin(h, st);
-    kern<<<grid, BT, smem, st>>>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, h->dev_flag, ring_test(h));
+    kern<<<grid, BT, smem, st>>>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, h->dev_flag, ring_test(h),
+                                 fx);
     count_launch();
     if (h->profile) prof_end(h, st, sizeof(R) == 4 ? RPBD_F32 : RPBD_F64, K, (double)n * (double)n);
     RPBD_LAUNCH_CHECK(h);
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta);
-    reduce_kernel<typename PartialT<R>::type, Out><<<dim3((unsigned)((n + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(
-        n, n_pad, k, K, n_chunks, partial, scale, inv8pieta, U); count_launch();
+    const dim3 rgrid((unsigned)((n + 255) / 256), (unsigned)(3 * k));
+    if (fixed)
+        finish_fixed_kernel<Out><<<rgrid, 256, 0, st>>>(n, n_pad, k, fx.cap, fx.acc, fx.fmax_bits, scale, inv8pieta, U);
+    else
+        reduce_kernel<typename PartialT<R>::type, Out><<<rgrid, 256, 0, st>>>(n, n_pad, k, K, n_chunks, partial, scale,
+                                                                              inv8pieta, U);
+    count_launch();
     RPBD_LAUNCH_CHECK(h);
     return RPBD_OK;
 }
@@ -618,7 +668,7 @@ static int apply(int sm_count, const rpbd_params& p, int64_t n, const double* r,
     static_assert((size_t)NST * TS * Rec<float, 16>::LEN * sizeof(float) + NST * sizeof(uint64_t) <= 48 * 1024,
                   "the no-alloc kernels must fit the default dynamic shared memory limit");
     pair_kernel<float, K, BT, TS, NST, WALL, false><<<dim3((unsigned)tgt_tiles, (unsigned)n_chunks), BT, smem, st>>>(
-        rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, flag, RingTest{4000000000LL, 0});
+        rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, flag, RingTest{4000000000LL, 0}, FixedAcc{});
     count_launch();
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * p.eta);
     reduce_kernel<float, float><<<dim3((unsigned)((n + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(

@@ -33,6 +33,7 @@
 #include "accum.cuh"
 #include "rpbd_internal.cuh"
 #include "wall_rpy.cuh"
+#include "fixed_point.cuh"
 #include "wall_rpy_x2.cuh"
 
 namespace rpbd {
@@ -526,40 +527,10 @@ constexpr int HT2 = 256;  // home blobs per CTA, two per thread
 // always takes the fixed-point accumulation below
 constexpr double SYM_PARTIAL_LIMIT = 16.0 * (1ull << 30);
 
-// Fixed-point accumulation of one system's matvec.  Every contribution to a
-// blob's velocity (a visitor tile's sum, an item's home sum) is an FP32 number;
-// it is scaled by 2^S, rounded to a 64-bit integer and added with an integer
-// atomic, so the result does not depend on the order of the additions
-// (integer addition is associative): deterministic with one accumulator per
-// blob and component.  S is the largest exponent for which no sum can leave
-// 2^61: every block entry is at most the self term 4/3 (in units of a; nine
-// images in the periodic cell), so a component is bounded by 4 n max|F|
-// (x 9), and 2^S = 2^61 / (that bound rounded up to a power of two).  The
-// rounding step 2^-S is at most 2^-60 of that bound.
-__device__ __forceinline__ int fixed_exponent(float fmax, int64_t n, bool per)
-{
-    // in FP64, where the bound stays finite for every finite FP32 force (S
-    // then lies within about [-120, 210])
-    const double bound = 4.0 * (double)n * (double)fmax * (per ? 9.0 : 1.0);
-    if (!(bound > 0.0)) return 0;
-    int e;
-    frexp(bound, &e);  // bound < 2^e
-    return 61 - e;
-}
-// adds v 2^S, scaled in two exact FP32 steps 2^h 2^(S-h) so that each factor
-// is a normal FP32 number over the whole range of S; a non-finite v
-// (non-finite positions) raises flag, and the finishing kernel then writes
-// NaN, as the fixed-order reduction would
-__device__ __forceinline__ void fixed_add(unsigned long long* a, float v, int S, unsigned* flag)
-{
-    if (!isfinite(v)) {
-        atomicExch(flag, 1u);
-        return;
-    }
-    const int h = S >> 1;
-    const float s1 = __int_as_float((h + 127) << 23), s2 = __int_as_float((S - h + 127) << 23);
-    atomicAdd(a, (unsigned long long)__float2ll_rn((v * s1) * s2));
-}
+// single-system accumulation in fixed point (fixed_point.cuh): every block
+// entry is at most the self term 4/3 in units of a (nine images in the
+// periodic cell), so a velocity component is at most 4 n max|F| (x 9)
+__host__ __device__ constexpr double fixed_cap(bool per) { return per ? 36.0 : 4.0; }
 
 template <int K>
 struct Rec2 {
@@ -629,17 +600,7 @@ __global__ void pack2_kernel(int n_sys, const SymSys* __restrict__ sys, int64_t 
 #pragma unroll
     for (int c = 0; c < NCH; ++c)
         *reinterpret_cast<float4*>(rec + rec2_off(j, c, LEN)) = make_float4(v[2 * c], v[2 * c], v[2 * c + 1], v[2 * c + 1]);
-    if (fmax_bits) {
-        // fmax_bits[0]: largest finite |force| of the launch (non-negative floats
-        // order like their bits); fmax_bits[1] != 0: some force is not finite
-        const bool bad = isinf(fm);
-        const unsigned b = __reduce_max_sync(__activemask(), bad ? 0u : __float_as_uint(fm));
-        const unsigned anybad = __any_sync(__activemask(), bad);
-        if ((threadIdx.x & 31) == __ffs(__activemask()) - 1) {
-            atomicMax(fmax_bits, b);
-            if (anybad) atomicExch(fmax_bits + 1, 1u);
-        }
-    }
+    if (fmax_bits) fixed_force_max(fmax_bits, fm);  // largest |force| of the launch, non-finite flag
 }
 
 // record j of a staged tile -> packed operands (both lanes equal); value m
@@ -795,7 +756,7 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
     const PairConstX2 pc = PairConstX2::make_unit();
     const float2 m1 = pc.m1;
     // exponent S of the fixed-point scale 2^S (ATOM)
-    const int fexp = ATOM ? fixed_exponent(__uint_as_float(__ldg(fmax_bits)), n, PER) : 0;
+    const int fexp = ATOM ? fixed_exponent(__uint_as_float(__ldg(fmax_bits)), n, fixed_cap(PER)) : 0;
 
     if (tid == 0) {
 #pragma unroll
@@ -1018,21 +979,6 @@ __global__ void reduce2_kernel(int n_sys, const SymSys* __restrict__ sys, int64_
     U[(int64_t)q * n_tot + g] = (Out)(scale[g] * inv8pieta * sum);
 }
 
-// U of one system from its fixed-point accumulators: undo 2^S, scale and write
-template <class Out>
-__global__ void finish_fixed_kernel(int64_t n, int64_t n_pad, int k, bool per, const unsigned long long* __restrict__ acc,
-                                    const unsigned* __restrict__ fmax_bits, const double* __restrict__ scale,
-                                    double inv8pieta, Out* __restrict__ U)
-{
-    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    const int q = blockIdx.y;
-    if (i >= n || q >= 3 * k) return;
-    const int S = fixed_exponent(__uint_as_float(fmax_bits[0]), n, per);
-    const double v = fmax_bits[1] ? __longlong_as_double(0x7ff8000000000000LL)
-                                   : ldexp((double)(long long)acc[(int64_t)q * n_pad + i], -S);
-    U[(int64_t)q * n + i] = (Out)(scale[i] * inv8pieta * v);
-}
-
 }  // namespace sym
 
 // Work list of the packed symmetric kernel for one launch (one system, or a
@@ -1221,7 +1167,8 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta * h->p.a);
     if (atom) {
         finish_fixed_kernel<Out><<<dim3((unsigned)((n_tot + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(
-            n_tot, np1a, k, PER, reinterpret_cast<const unsigned long long*>(partial), fmax_bits, scale, inv8pieta, U);
+            n_tot, np1a, k, sym::fixed_cap(PER), reinterpret_cast<const unsigned long long*>(partial), fmax_bits, scale,
+            inv8pieta, U);
         count_launch();
         RPBD_LAUNCH_CHECK(h);
         return RPBD_OK;

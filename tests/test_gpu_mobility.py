@@ -374,3 +374,51 @@ def test_f32_packed_far_from_origin_and_wide(k):
     rw[1] += shift[body % 16, 1]
     Uw = h.mobility_apply(to_dev(rw), to_dev(F, torch.float32)).cpu().numpy()
     assert rel2(Uw, om.apply(rw, F.astype(np.float64), oracle_params(s))) <= 1e-5
+
+
+@pytest.mark.parametrize("k", [1, 8, 16])
+@pytest.mark.parametrize("n", [1, 700, 4500])
+def test_f32_one_direction_fixed_point_and_partials(k, n):
+    """The one-direction FP32 kernel's two accumulations: fixed point per blob
+    (the default) and per-chunk partials with the fixed-order reduction.  Both
+    against the oracle, against each other (the same FP32 chunk sums), and
+    each bit for bit against a repeat of itself; the fixed point in the
+    periodic cell as well."""
+    rng = np.random.default_rng(17 * n + k)
+    box = max(2.0, np.sqrt(n))
+    r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
+    F = rng.standard_normal((k, 3, n)).astype(np.float32)
+    s = synth.boomerangs_1920()
+    h = handle_for(s)
+    h.set_symmetric(False)
+    rd, Fd = to_dev(r), to_dev(F, torch.float32)
+    Ufx = h.mobility_apply(rd, Fd).cpu().numpy()
+    assert np.array_equal(Ufx, h.mobility_apply(rd, Fd).cpu().numpy())
+    h.set_sym_partials(True)
+    Upt = h.mobility_apply(rd, Fd).cpu().numpy()
+    Uo = om.apply(r, F.astype(np.float64), oracle_params(s))
+    assert rel2(Ufx, Uo) <= 1e-5 and rel2(Upt, Uo) <= 1e-5
+    assert rel2(Ufx, Upt) <= 1e-6
+    if k == 16:
+        from paper_1709_02410_gb300 import Handle
+        L = max(4.0, box)
+        hp = Handle(synth.ETA, s.a, synth.KT, Lx=L, Ly=L)
+        Up = hp.mobility_apply(rd, Fd).cpu().numpy()
+        assert rel2(Up, om.apply(r, F.astype(np.float64), om.Params(synth.ETA, s.a, Lx=L, Ly=L))) <= 1e-5
+
+
+def test_f32_one_direction_fixed_point_extreme_scale_and_nan():
+    """k = 8 (one-direction kernel): forces of 4e33 at 9,000 blobs (4 n max|F|
+    beyond FP32's range) match the oracle; a NaN force gives NaN."""
+    n = 9000
+    rng = np.random.default_rng(979)
+    box = np.sqrt(n)
+    r = np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)])
+    F = (rng.standard_normal((8, 3, n)) * 4e33).astype(np.float32)
+    s = synth.boomerangs_1920()
+    h = handle_for(s)
+    U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(U))
+    assert rel2(U, om.apply(r, F.astype(np.float64), oracle_params(s))) <= 1e-5
+    F[3, 2, 10] = np.nan
+    assert np.isnan(h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()).any()
