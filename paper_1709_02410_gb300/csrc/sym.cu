@@ -726,7 +726,10 @@ struct Sym2Var {
 // thread, 64 threads, so each visitor record loaded and each visitor sum
 // handed on serves twice the pairs).  Warp w owns homes [64 HP w, 64 HP (w+1))
 // of the tile; pair p of a thread holds homes 64 HP w + 64 p + lane (.x) and
-// that + 32 (.y).
+// that + 32 (.y).  FAR: the cancellation-free far-field block.  ATOM (one
+// system): the visitor and home sums go into the fixed-point accumulators
+// (partial = [3K][n_pad] 64-bit integers, fmax_bits after them) instead of
+// the per-home-tile partials.
 template <int K, bool PER, int UNR, int MINB, bool BATCH, int HP = 1, bool FAR = false, bool ATOM = false>
 __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float* __restrict__ rec,
                                                               const SymItem* __restrict__ items, int64_t n,
