@@ -411,8 +411,10 @@ int rpbd_blob_forces(rpbd_handle* h, int64_t n, int nper, const double* r, const
  * overflow; the rounding step is at most 2^-60 of the largest possible sum,
  * 4 n max|F| in units of 1 / (8 pi eta a), x 9 in the periodic cell; any
  * finite FP32 forces).  Integer addition does not depend on its order, so
- * both are deterministic; they differ by FP32 output rounding.  Batches and
- * the FP64 kernels always keep their partials. */
+ * both are deterministic; they differ by FP32 output rounding.  Batches on
+ * the packed symmetric kernel follow the same option (one maximum force per
+ * system); the FP64 kernels and the batched one-direction tiles always keep
+ * their partials. */
 #define RPBD_OPT_SYM_PARTIALS 7
 int rpbd_set_option(rpbd_handle* h, int option, int value);
 

@@ -600,7 +600,9 @@ __global__ void pack2_kernel(int n_sys, const SymSys* __restrict__ sys, int64_t 
 #pragma unroll
     for (int c = 0; c < NCH; ++c)
         *reinterpret_cast<float4*>(rec + rec2_off(j, c, LEN)) = make_float4(v[2 * c], v[2 * c], v[2 * c + 1], v[2 * c + 1]);
-    if (fmax_bits) fixed_force_max(fmax_bits, fm);  // largest |force| of the launch, non-finite flag
+    // largest |force| of the record's system and its non-finite flag (a warp never
+    // straddles two systems: each is padded to whole 256-record home tiles)
+    if (fmax_bits) fixed_force_max(fmax_bits + 2 * sx, fm);
 }
 
 // record j of a staged tile -> packed operands (both lanes equal); value m
@@ -737,7 +739,8 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
                                                               const SymSys* __restrict__ sys,
                                                               const int* __restrict__ active, float Lx, float Ly,
                                                               float* __restrict__ partial, int* __restrict__ err_flag,
-                                                              RingTest rt, const unsigned* __restrict__ fmax_bits = nullptr)
+                                                              RingTest rt, const unsigned* __restrict__ fmax_bits = nullptr,
+                                                              int64_t acc_stride = 0)
 {
     constexpr int NT = HT2 / (2 * HP);  // threads
     constexpr int NW = NT / 32;          // warps
@@ -758,8 +761,10 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
     const int64_t ib = (int64_t)it.home * HT2 + warp * 64 * HP + lane;  // home record of pair 0, lane .x
     const PairConstX2 pc = PairConstX2::make_unit();
     const float2 m1 = pc.m1;
-    // exponent S of the fixed-point scale 2^S (ATOM)
-    const int fexp = ATOM ? fixed_exponent(__uint_as_float(__ldg(fmax_bits)), n, fixed_cap(PER)) : 0;
+    // exponent S of the fixed-point scale 2^S of this item's system (ATOM)
+    const int fexp = ATOM ? fixed_exponent(__uint_as_float(__ldg(fmax_bits + (BATCH ? 2 * it.sys : 0))),
+                                           BATCH ? __ldg(&sd->n) : n, fixed_cap(PER))
+                          : 0;
 
     if (tid == 0) {
 #pragma unroll
@@ -866,9 +871,9 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
                     float sum = rb[vl * 3 * K + q];
 #pragma unroll
                     for (int w = 1; w < NW; ++w) sum += rb[(w * VT + vl) * 3 * K + q];
-                    if constexpr (ATOM)  // one fixed-point accumulator per blob and component
-                        fixed_add(reinterpret_cast<unsigned long long*>(partial) + (int64_t)q * sn_pad + vg, sum,
-                                  fexp, const_cast<unsigned*>(fmax_bits) + 1);
+                    if constexpr (ATOM)  // one fixed-point accumulator per record and component
+                        fixed_add(reinterpret_cast<unsigned long long*>(partial) + (int64_t)q * acc_stride + sB + vg,
+                                  sum, fexp, const_cast<unsigned*>(fmax_bits) + (BATCH ? 2 * it.sys : 0) + 1);
                     else
                         part[(hloc * 3 * K + q) * sn_pad + vg] = sum;
                 }
@@ -898,15 +903,40 @@ __global__ void __launch_bounds__(HT2 / (2 * HP), MINB) sym2_kernel(const float*
 #pragma unroll
         for (int q = 0; q < 3 * K; ++q) {
             if constexpr (ATOM) {
-                unsigned long long* a64 = reinterpret_cast<unsigned long long*>(partial) + (int64_t)q * sn_pad;
-                if (l0 < sn) fixed_add(a64 + l0, acc[p][q].x, fexp, const_cast<unsigned*>(fmax_bits) + 1);
-                if (l1 < sn) fixed_add(a64 + l1, acc[p][q].y, fexp, const_cast<unsigned*>(fmax_bits) + 1);
+                unsigned long long* a64 = reinterpret_cast<unsigned long long*>(partial) + (int64_t)q * acc_stride + sB;
+                unsigned* const flag = const_cast<unsigned*>(fmax_bits) + (BATCH ? 2 * it.sys : 0) + 1;
+                if (l0 < sn) fixed_add(a64 + l0, acc[p][q].x, fexp, flag);
+                if (l1 < sn) fixed_add(a64 + l1, acc[p][q].y, fexp, flag);
             } else {
                 if (l0 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l0] = acc[p][q].x;
                 if (l1 < sn) part[((int64_t)slot * 3 * K + q) * sn_pad + l1] = acc[p][q].y;
             }
         }
     }
+}
+
+// U of a batch from its fixed-point accumulators ([3K][records], then two
+// words per system: largest |force|, non-finite flag): undo the system's 2^S,
+// scale and write; converged systems keep their U.  One thread per (blob,
+// component blockIdx.y).
+template <class Out>
+__global__ void finish_fixed_batch_kernel(int n_sys, const SymSys* __restrict__ sys, int64_t n_tot, int k,
+                                          int64_t acc_stride, const int* __restrict__ active,
+                                          const unsigned long long* __restrict__ acc,
+                                          const unsigned* __restrict__ fmax_bits, const double* __restrict__ scale,
+                                          double inv8pieta, Out* __restrict__ U)
+{
+    const int64_t g = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int q = blockIdx.y;
+    if (g >= n_tot || q >= 3 * k) return;
+    const int sx = sys_of(n_sys, g, [&](int m) { return sys[m].g0; });
+    if (active && !active[sx]) return;
+    const SymSys d = sys[sx];
+    const unsigned* fb = fmax_bits + 2 * sx;
+    const int S = fixed_exponent(__uint_as_float(fb[0]), d.n, fixed_cap(false));
+    const double v = fb[1] ? __longlong_as_double(0x7ff8000000000000LL)
+                           : ldexp((double)(long long)acc[(int64_t)q * acc_stride + d.B + (g - d.g0)], -S);
+    U[(int64_t)q * n_tot + g] = (Out)(scale[g] * inv8pieta * v);
 }
 
 // Reductions of the packed kernel's partials, per system of the launch (the
@@ -1097,22 +1127,25 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     double* scale;
     float* partial;
     double* segsum = nullptr;
-    // one system: fixed-point accumulation, one integer per blob and component
-    // (memory O(n), deterministic); per-home-tile partials with the fixed-order
-    // reduction on request while they stay under SYM_PARTIAL_LIMIT bytes; batches:
-    // per-system partials
-    const bool atom = n_sys == 1 && (!h->sym_partials || h->far_field ||
-                                     (double)pl->part_rows * 3 * K * sizeof(float) > SYM_PARTIAL_LIMIT);
-    const int64_t np1a = pl->sys[0].n_pad;
+    // fixed-point accumulation, one integer per record and component (memory
+    // O(n), deterministic); per-home-tile partials with the fixed-order
+    // reduction on request (RPBD_OPT_SYM_PARTIALS; a single system only while
+    // they stay under SYM_PARTIAL_LIMIT bytes and the far field is off)
+    const bool atom = !h->sym_partials ||
+                      (n_sys == 1 && (h->far_field ||
+                                      (double)pl->part_rows * 3 * K * sizeof(float) > SYM_PARTIAL_LIMIT));
+    const int64_t acc_stride = pl->rec_end;
     unsigned* fmax_bits = nullptr;
     RPBD_TRY(ensure_t(h, b_rec, (size_t)pl->rec_end * LEN, &rec));
     RPBD_TRY(ensure_t(h, b_scale, (size_t)n_tot, &scale));
     if (atom) {
-        unsigned long long* acc;  // [3K][n_pad] accumulators, then the two words of fmax_bits
-        RPBD_TRY(ensure_t(h, b_part, (size_t)3 * K * np1a + 1, &acc));
-        RPBD_CU(h, cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * (3 * K * np1a + 1), st));
+        // [3K][records] accumulators, then two words per system (largest |force|, non-finite flag)
+        unsigned long long* acc;
+        const size_t words = (size_t)3 * K * acc_stride + (size_t)n_sys;
+        RPBD_TRY(ensure_t(h, b_part, words, &acc));
+        RPBD_CU(h, cudaMemsetAsync(acc, 0, sizeof(unsigned long long) * words, st));
         partial = reinterpret_cast<float*>(acc);
-        fmax_bits = reinterpret_cast<unsigned*>(acc + 3 * K * np1a);
+        fmax_bits = reinterpret_cast<unsigned*>(acc + 3 * K * acc_stride);
     } else {
         RPBD_TRY(ensure_t(h, b_part, (size_t)pl->part_rows * 3 * K, &partial));
         RPBD_TRY(ensure_t(h, b_seg, (size_t)std::max<int64_t>(1, pl->seg_rows) * 3 * K, &segsum));
@@ -1136,14 +1169,18 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     sym2_kernel<K, PER, Sym2Var<K, V, PER>::UNR, Sym2Var<K, V, PER>::MINB, false, Sym2Var<K, V, PER>::HP, FARV, ATOMV> \
         <<<ni, Sym2Var<K, V, PER>::NT, Sym2Var<K, V, PER>::smem(LEN), st>>>(rec, items, n1, np1, T1, sys, nullptr,     \
                                                                             Lxa, Lya, partial, h->dev_flag, rt,        \
-                                                                            fmax_bits)
+                                                                            fmax_bits, acc_stride)
     if (n_sys > 1) {  // batches: four home blobs per thread (variant 5's shape; 3-5% faster than two
                       // on 64 uneven suspensions of 480-22,500 blobs)
-        if constexpr (!PER)
-            sym2_kernel<K, false, Sym2Var<K, 5>::UNR, Sym2Var<K, 5>::MINB, true, Sym2Var<K, 5>::HP>
-                <<<ni, Sym2Var<K, 5>::NT, Sym2Var<K, 5>::smem(LEN), st>>>(rec, items, 0, 0, 0, sys, active, Lxa,
-                                                                          Lya, partial, h->dev_flag, rt);
-        else
+        if constexpr (!PER) {
+            using V5 = Sym2Var<K, 5>;
+            if (atom)
+                sym2_kernel<K, false, V5::UNR, V5::MINB, true, V5::HP, false, true><<<ni, V5::NT, V5::smem(LEN), st>>>(
+                    rec, items, 0, 0, 0, sys, active, Lxa, Lya, partial, h->dev_flag, rt, fmax_bits, acc_stride);
+            else
+                sym2_kernel<K, false, V5::UNR, V5::MINB, true, V5::HP><<<ni, V5::NT, V5::smem(LEN), st>>>(
+                    rec, items, 0, 0, 0, sys, active, Lxa, Lya, partial, h->dev_flag, rt);
+        } else
             return set_error(h, RPBD_BAD_ARG, "packed symmetric kernel: batches are open in x, y");
     } else if (h->far_field) {  // the cancellation-free block: one compiled variant per k
         RPBD_SYM2_LAUNCH(K == 1 ? 3 : (K == 2 || !PER ? 5 : 3), true, true);  // (k > 2 periodic: no spill)
@@ -1169,9 +1206,14 @@ static int run2(rpbd_handle* h, int n_sys, const int64_t* off, const double* r, 
     // blocks were formed in units of a: M = M(a = 1) / a
     const double inv8pieta = 1.0 / (8.0 * 3.14159265358979323846 * h->p.eta * h->p.a);
     if (atom) {
-        finish_fixed_kernel<Out><<<dim3((unsigned)((n_tot + 255) / 256), (unsigned)(3 * k)), 256, 0, st>>>(
-            n_tot, np1a, k, sym::fixed_cap(PER), reinterpret_cast<const unsigned long long*>(partial), fmax_bits, scale,
-            inv8pieta, U);
+        const dim3 fgrid((unsigned)((n_tot + 255) / 256), (unsigned)(3 * k));
+        const auto* acc = reinterpret_cast<const unsigned long long*>(partial);
+        if (n_sys == 1)
+            finish_fixed_kernel<Out><<<fgrid, 256, 0, st>>>(n_tot, acc_stride, k, sym::fixed_cap(PER), acc, fmax_bits,
+                                                            scale, inv8pieta, U);
+        else
+            finish_fixed_batch_kernel<Out><<<fgrid, 256, 0, st>>>(n_sys, sys, n_tot, k, acc_stride, active, acc,
+                                                                  fmax_bits, scale, inv8pieta, U);
         count_launch();
         RPBD_LAUNCH_CHECK(h);
         return RPBD_OK;

@@ -26,7 +26,7 @@ def main():
                     help="the uneven batch of 64 boomerang suspensions (one batched launch; --variant: tile variant)")
     ap.add_argument("--adjoint", action="store_true", help="the FP32 adjoint instead of the matvec")
     ap.add_argument("--partials", action="store_true",
-                    help="packed symmetric kernel with per-home-tile partials (not the fixed-point accumulation)")
+                    help="partial sums with the fixed-order reduction (not the fixed-point accumulation)")
     ap.add_argument("--far", action="store_true", help="cancellation-free far field")
     a = ap.parse_args()
     import torch
@@ -70,6 +70,7 @@ def batched(a):
     h = Handle(synth.ETA, systems[0].a, synth.KT)
     if a.variant >= 0:
         h.set_batch_variant(a.variant)
+    h.set_sym_partials(a.partials)
     dev = "cuda:0"
     T = lambda x, dt=torch.float64: torch.as_tensor(np.ascontiguousarray(x), dtype=dt, device=dev)
     shape = T(systems[0].shape)
@@ -89,6 +90,7 @@ def batched(a):
     t = e0.elapsed_time(e1) / 1e3 / a.reps
     pairs = float(sum(float(s.n) ** 2 for s in systems))
     print(json.dumps({"batched": len(systems), "blobs": int(off[-1]), "k": a.k, "variant": a.variant,
+                      "partials": a.partials,
                       "s_per_launch": t, "pairs_per_s": pairs / t}))
 
 

@@ -114,3 +114,36 @@ def test_graph_replay_after_the_single_system_workspace_grows():
     assert it == it_ref
     assert rel2(out.cpu().numpy(), ref.cpu().numpy()) <= 1e-13
     assert rel2(U.cpu().numpy(), Uref.cpu().numpy()) <= 1e-13
+
+
+@pytest.mark.parametrize("k", [1, 2, 3])
+def test_batched_symmetric_fixed_point_and_partials(k):
+    """Batched variant 4 (the packed symmetric kernel over a batch): fixed
+    point with one maximum force per system (the default) against the
+    per-system partials, the oracle per system, and a bitwise repeat; one
+    system's forces 1e6 times larger than the rest, so a shared scale would
+    cost the small systems their accuracy."""
+    rng = np.random.default_rng(600 + k)
+    sizes = [1, 255, 257, 700, 2049, 31]
+    rs, Fs = [], []
+    for i, n in enumerate(sizes):
+        box = max(2.0, np.sqrt(n))
+        rs.append(np.stack([rng.uniform(0, box, n), rng.uniform(0, box, n), rng.uniform(-0.2, 2.5, n)]))
+        Fs.append(rng.standard_normal((k, 3, n)) * (1e6 if i == 3 else 1.0))
+    r = np.concatenate(rs, axis=1)
+    F = np.concatenate(Fs, axis=2).astype(np.float32)
+    off = np.concatenate([[0], np.cumsum(sizes)]).astype(np.int64)
+    s = synth.boomerangs_1920()
+    h = handle_for(s)
+    h.set_batch_variant(4)
+    rd, Fd = to_dev(r), to_dev(F, torch.float32)
+    Ufx = h.mobility_apply_batched(off, rd, Fd).cpu().numpy()
+    assert np.array_equal(Ufx, h.mobility_apply_batched(off, rd, Fd).cpu().numpy())
+    h.set_sym_partials(True)
+    Upt = h.mobility_apply_batched(off, rd, Fd).cpu().numpy()
+    for i in range(len(sizes)):
+        sl = slice(off[i], off[i + 1])
+        Uo = om.apply(rs[i], F[:, :, sl].astype(np.float64), oracle_params(s))
+        assert rel2(Ufx[:, :, sl], Uo) <= 1e-5, i
+        assert rel2(Upt[:, :, sl], Uo) <= 1e-5, i
+        assert rel2(Ufx[:, :, sl], Upt[:, :, sl]) <= 1e-6, i
