@@ -186,7 +186,7 @@ __global__ void pack_kernel(int64_t n, int64_t n_pad, int k, const double* __res
 // ---------------------------------------------------------------------------
 // 2. pair kernel
 
-template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
+template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER, bool FX>
 __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, int64_t n_pad, int tiles_per_chunk,
                                           int n_tiles, PairConst<R> pc, typename PartialT<R>::type* __restrict__ partial,
                                           int* __restrict__ err_flag, RingTest rt, FixedAcc fx)
@@ -326,7 +326,7 @@ __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, 
         return;
     }
     if (i < n) {
-        if (sizeof(R) == 4 && fx.acc) {  // FP32: the chunk sums into the fixed-point accumulators
+        if constexpr (FX) {  // FP32: the chunk sums into the fixed-point accumulators
             const int S = fixed_exponent(__uint_as_float(__ldg(fx.fmax_bits)), n, fx.cap);
             unsigned* const flag = fx.fmax_bits + 1;
             if constexpr (PK) {
@@ -357,30 +357,30 @@ __device__ __forceinline__ void pair_body(const R* __restrict__ rec, int64_t n, 
     }
 }
 
-template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
+template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER, bool FX = false>
 __global__ void __launch_bounds__(BT) pair_kernel(const R* __restrict__ rec, int64_t n, int64_t n_pad,
                                                   int tiles_per_chunk, int n_tiles, PairConst<R> pc,
                                                   typename PartialT<R>::type* __restrict__ partial,
                                                   int* __restrict__ err_flag, RingTest rt, FixedAcc fx)
 {
-    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag, rt, fx);
+    pair_body<R, K, BT, TS, NST, WALL, PER, FX>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag, rt, fx);
 }
 
 // FP32, 16 right-hand sides: registers capped so five CTAs share an SM
-template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
+template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER, bool FX = false>
 __global__ void __launch_bounds__(BT, 5) pair_kernel_k16(const R* __restrict__ rec, int64_t n, int64_t n_pad,
                                                          int tiles_per_chunk, int n_tiles, PairConst<R> pc,
                                                          typename PartialT<R>::type* __restrict__ partial,
                                                          int* __restrict__ err_flag, RingTest rt, FixedAcc fx)
 {
-    pair_body<R, K, BT, TS, NST, WALL, PER>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag, rt, fx);
+    pair_body<R, K, BT, TS, NST, WALL, PER, FX>(rec, n, n_pad, tiles_per_chunk, n_tiles, pc, partial, err_flag, rt, fx);
 }
 
-template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER>
+template <class R, int K, int BT, int TS, int NST, bool WALL, bool PER, bool FX>
 static auto pick_pair_kernel()
 {
-    if constexpr (sizeof(R) == 4 && K == 16) return pair_kernel_k16<R, K, BT, TS, NST, WALL, PER>;
-    else return pair_kernel<R, K, BT, TS, NST, WALL, PER>;
+    if constexpr (sizeof(R) == 4 && K == 16) return pair_kernel_k16<R, K, BT, TS, NST, WALL, PER, FX>;
+    else return pair_kernel<R, K, BT, TS, NST, WALL, PER, FX>;
 }
 
 // ---------------------------------------------------------------------------
@@ -476,7 +476,10 @@ static int apply_k(rpbd_handle* h, int64_t n, const double* r, const In* F, Out*
     count_launch();
     RPBD_LAUNCH_CHECK(h);
     const size_t smem = (size_t)NST * TS * LEN * sizeof(R) + NST * sizeof(uint64_t);
-    auto kern = pick_pair_kernel<R, K, BT, TS, NST, WALL, PER>();
+    // FX: a separate instantiation, so the partials kernel keeps its own register allocation
+    auto kern = pick_pair_kernel<R, K, BT, TS, NST, WALL, PER, false>();
+    if constexpr (sizeof(R) == 4)
+        if (fixed) kern = pick_pair_kernel<R, K, BT, TS, NST, WALL, PER, true>();
     if (once_per_device(h, reinterpret_cast<const void*>(kern)))
         RPBD_CU(h, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid((unsigned)tgt_tiles, (unsigned)n_chunks);
