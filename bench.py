@@ -736,7 +736,9 @@ def run_reference(args, rank, world):
     ro = rigid.blob_positions(s.q, s.theta, s.shape)
     prm = om.Params(synth.ETA, s.a)
     F = synth.gaussian(100, (K_RHS, 3, N), np.float32).astype(np.float64)
-    nrows = 32
+    # enough rows per step that the call's fixed cost (argument conversion,
+    # thread start) stays small next to the pair sums: ~1.5 s per step
+    nrows = 512
 
     def step(i):
         rows = np.arange(i * nrows, (i + 1) * nrows) % N
