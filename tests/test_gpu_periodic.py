@@ -82,3 +82,22 @@ def test_periodic_argument_checks():
     F = torch.zeros((1, 3, s.n), dtype=torch.float32, device=DEV)
     with pytest.raises(RpbdError):
         h.mobility_apply_batched(off, to_dev(r), F)
+
+
+@pytest.mark.parametrize("k", [1, 2])
+def test_periodic_full_size_row_sampled(k):
+    """The periodic cell at full size in the bench's configuration: the
+    65,535-blob boomerang suspension in its own 233.7 um square cell (minimum
+    image + 8 nearest images per pair), packed symmetric kernel with
+    fixed-point accumulation; 64 sampled rows, the first and the last blob
+    included, against the oracle's image sum."""
+    s = synth.boomerangs_65535()
+    Lc = 40.0 * np.sqrt(s.nb / 128)
+    r = positions(s)
+    F = synth.gaussian(510 + k, (k, 3, s.n), np.float32)
+    h = Handle(synth.ETA, s.a, synth.KT, Lx=Lc, Ly=Lc)
+    U = h.mobility_apply(to_dev(r), to_dev(F, torch.float32)).cpu().numpy()
+    rows = np.random.default_rng(512).choice(s.n, 64, replace=False)
+    rows[0], rows[1] = 0, s.n - 1
+    Uo = om.apply(r, F.astype(np.float64), om.Params(synth.ETA, s.a, Lx=Lc, Ly=Lc), rows=rows)
+    assert rel2(U[:, :, rows], Uo) <= 1e-5
